@@ -1,0 +1,216 @@
+"""Seeded synthetic relations for the hash-join workloads.
+
+This module generates inputs only: it holds none of the join's arithmetic, and
+both the CUDA path's tests/bench and the CPU oracle's tests draw their inputs
+from it.  Every value is a pure function of (seed, stream ids, row index), so the
+same call gives identical bytes on a CPU tensor and on a CUDA tensor.
+
+Relations are tensors of shape (n, 2): column 0 the key, column 1 the rid
+(payload), stored as int32 (bit pattern of the unsigned 32-bit value) or int64
+(bit pattern of the unsigned 64-bit value).  The paper's data sets are two
+four-byte integer attributes per tuple, generated synthetically (Sec. 5.1).
+
+Random words come from a counter-based SplitMix64 stream (Steele, Lea, Flood,
+OOPSLA 2014): word i of stream s is the SplitMix64 finaliser of
+s + (i + 1) * 0x9E3779B97F4A7C15, computed with wrapping int64 arithmetic and
+logical shifts.  Permutations are a keyed bijection on [0, 2^k) (odd multiplier,
+xorshift and key XOR rounds) restricted to [0, n) by cycle walking.
+"""
+from __future__ import annotations
+
+import math
+from dataclasses import dataclass
+
+import torch
+
+GAMMA = 0x9E3779B97F4A7C15
+M64 = (1 << 64) - 1
+DEFAULT_SEED = 0x5EED
+
+
+def _s64(v: int) -> int:
+    """Unsigned 64-bit value -> the int64 with the same bit pattern."""
+    v &= M64
+    return v - (1 << 64) if v >= (1 << 63) else v
+
+
+def _srl(x: torch.Tensor, s: int) -> torch.Tensor:
+    """Logical right shift of int64 bit patterns."""
+    return (x >> s) & ((1 << (64 - s)) - 1)
+
+
+def _fin(z: torch.Tensor) -> torch.Tensor:
+    z = (z ^ _srl(z, 30)) * _s64(0xBF58476D1CE4E5B9)
+    z = (z ^ _srl(z, 27)) * _s64(0x94D049BB133111EB)
+    return z ^ _srl(z, 31)
+
+
+def _fin_int(z: int) -> int:
+    z &= M64
+    z = ((z ^ (z >> 30)) * 0xBF58476D1CE4E5B9) & M64
+    z = ((z ^ (z >> 27)) * 0x94D049BB133111EB) & M64
+    return z ^ (z >> 31)
+
+
+def stream_id(seed: int, *ids: int) -> int:
+    """Derive a stream word from the seed and a tuple of small ids (pure Python)."""
+    s = _fin_int(seed)
+    for i in ids:
+        s = _fin_int(s ^ _fin_int(i + 0x632BE59BD9B4E019))
+    return s
+
+
+def words(stream: int, start: int, count: int, device) -> torch.Tensor:
+    """SplitMix64 words start .. start+count-1 of a stream, as int64 bit patterns."""
+    i = torch.arange(start + 1, start + count + 1, dtype=torch.int64, device=device)
+    return _fin(i * _s64(GAMMA) + _s64(stream))
+
+
+def uniform_below(n: int, stream: int, count: int, device, start: int = 0) -> torch.Tensor:
+    """Integers uniform on [0, n), n <= 2^31 (multiply-shift on the high 32 bits)."""
+    if not 1 <= n <= (1 << 31):
+        raise ValueError("n must be in [1, 2^31]")
+    hi = _srl(words(stream, start, count, device), 32)
+    return (hi * n) >> 32
+
+
+def unit_doubles(stream: int, count: int, device) -> torch.Tensor:
+    """Doubles uniform on [0, 1): the top 53 bits of each word times 2^-53 (exact)."""
+    return _srl(words(stream, 0, count, device), 11).to(torch.float64) * (2.0 ** -53)
+
+
+def _bijection(x: torch.Tensor, k: int, keys: list[int]) -> torch.Tensor:
+    mask = (1 << k) - 1
+    s = max(1, (k + 1) // 2)
+    for r, key in enumerate(keys):
+        mult = (0xD1B54A32D192ED03 + 2 * r * 0x2545F4914F6CDD1D) | 1
+        x = (x * _s64(mult)) & mask
+        x = x ^ (x >> s)
+        x = x ^ (key & mask)
+    return x
+
+
+def permutation(n: int, stream: int, device, start: int = 0, count: int | None = None) -> torch.Tensor:
+    """Entries start .. start+count-1 of a seeded permutation of [0, n)."""
+    count = n - start if count is None else count
+    x = torch.arange(start, start + count, dtype=torch.int64, device=device)
+    if n <= 1:
+        return x
+    k = max(2, math.ceil(math.log2(n)))
+    keys = [_fin_int(stream + r + 1) for r in range(4)]
+    y = _bijection(x, k, keys)
+    while True:
+        bad = y >= n
+        if not bool(bad.any()):
+            return y
+        y = torch.where(bad, _bijection(y, k, keys), y)
+
+
+def _u32_bits(v: torch.Tensor) -> torch.Tensor:
+    """Unsigned 32-bit values held in int64 -> int32 with the same bit pattern."""
+    v = v & 0xFFFFFFFF
+    return (v - ((v >> 31) << 32)).to(torch.int32)
+
+
+def make_relation(keys: torch.Tensor, rids: torch.Tensor, width: int) -> torch.Tensor:
+    """Pack key and rid columns (int64 holding unsigned values) into an (n, 2) AoS tensor."""
+    if width == 4:
+        return torch.stack([_u32_bits(keys), _u32_bits(rids)], dim=1).contiguous()
+    if width == 8:
+        return torch.stack([keys, rids], dim=1).contiguous()
+    raise ValueError("width must be 4 or 8")
+
+
+# --------------------------------------------------------------------------- workloads
+
+
+def unique_and_uniform(n_r: int, n_s: int, s_domain: int, seed: int, device, width: int = 4,
+                       ids: tuple = ()):
+    """R keys: a seeded permutation of 1..|R| (unique); R rid = row index.
+    S keys: uniform on [1, s_domain]; S rid = row index.
+
+    With s_domain = |R| every S tuple matches exactly one R tuple; with
+    s_domain = |R| / m a fraction m of S matches (once each)."""
+    pr = stream_id(seed, *ids, 1)
+    ps = stream_id(seed, *ids, 2)
+    rk = permutation(n_r, pr, device) + 1
+    rr = torch.arange(n_r, dtype=torch.int64, device=device)
+    sk = uniform_below(s_domain, ps, n_s, device) + 1 if n_s else torch.zeros(0, dtype=torch.int64, device=device)
+    sr = torch.arange(n_s, dtype=torch.int64, device=device)
+    return make_relation(rk, rr, width), make_relation(sk, sr, width)
+
+
+def zipf_cdf(n_ranks: int, theta: float) -> torch.Tensor:
+    """CPU float64 CDF of P(rank = k) proportional to k^-theta, k = 1..n_ranks (last entry 1.0)."""
+    k = torch.arange(1, n_ranks + 1, dtype=torch.float64)
+    c = torch.cumsum(k.pow(-theta), 0)
+    c = c / c[-1]
+    c[-1] = 1.0
+    return c
+
+
+def zipf_keys(n: int, theta: float, n_ranks: int, stream: int, key_stream: int, device) -> torch.Tensor:
+    """n keys whose ranks are Zipf(theta) over n_ranks values, drawn by inverse CDF;
+    rank k maps to the 64-bit key SplitMix64-finaliser(k + key_stream) (a bijection,
+    so distinct ranks give distinct keys spread over all 64 bits)."""
+    cdf = zipf_cdf(n_ranks, theta).to(device)
+    u = unit_doubles(stream, n, device)
+    rank = torch.searchsorted(cdf, u, right=True) + 1
+    return _fin(rank + _s64(key_stream))
+
+
+def zipf_pair(n_r: int, n_s: int, theta_r: float, theta_s: float, n_ranks: int, seed: int, device,
+              ids: tuple = ()):
+    """Skewed 64-bit workload: R and S keys Zipf over the same n_ranks distinct keys,
+    payload = row index, width 8."""
+    ks = stream_id(seed, *ids, 0)
+    rk = zipf_keys(n_r, theta_r, n_ranks, stream_id(seed, *ids, 1), ks, device)
+    sk = zipf_keys(n_s, theta_s, n_ranks, stream_id(seed, *ids, 2), ks, device)
+    rr = torch.arange(n_r, dtype=torch.int64, device=device)
+    sr = torch.arange(n_s, dtype=torch.int64, device=device)
+    return make_relation(rk, rr, 8), make_relation(sk, sr, 8)
+
+
+@dataclass(frozen=True)
+class JoinSpec:
+    """Sizes of one join of a batch or of a served request."""
+    n_r: int
+    n_s: int
+    s_domain: int
+    arrival_s: float = 0.0
+
+
+def batched_specs(n_joins: int, seed: int, lo_log2: float = 10.0, hi_log2: float = 22.0,
+                  s_factor: int = 4, match_rate: float = 0.75) -> list[JoinSpec]:
+    """|R| = floor(2^U), U ~ Uniform[lo, hi]; |S| = s_factor * |R|;
+    S keys uniform over [1, ceil(|R| / match_rate)] (computed on the CPU)."""
+    u = unit_doubles(stream_id(seed, 4, 0), n_joins, "cpu").tolist()
+    out = []
+    for x in u:
+        n_r = int(math.floor(2.0 ** (lo_log2 + (hi_log2 - lo_log2) * x)))
+        out.append(JoinSpec(n_r, s_factor * n_r, int(math.ceil(n_r / match_rate))))
+    return out
+
+
+def serving_specs(n_req: int, seed: int, rate_per_s: float, lo_log2: float = 12.0, hi_log2: float = 24.0,
+                  max_s_factor_log16: float = 1.0, match_rate: float = 0.5) -> list[JoinSpec]:
+    """Poisson arrivals at rate_per_s; |R| = 2^U, U ~ U[lo, hi] (rounded down);
+    |S| = |R| * 16^V, V ~ U[0, 1]; S keys uniform over [1, ceil(|R| / match_rate)]."""
+    u = unit_doubles(stream_id(seed, 5, 0), 3 * n_req, "cpu").tolist()
+    t = 0.0
+    out = []
+    for i in range(n_req):
+        ua, ur, us = u[3 * i], u[3 * i + 1], u[3 * i + 2]
+        t += -math.log(1.0 - ua) / rate_per_s
+        n_r = int(math.floor(2.0 ** (lo_log2 + (hi_log2 - lo_log2) * ur)))
+        n_s = int(math.floor(n_r * 16.0 ** (max_s_factor_log16 * us)))
+        out.append(JoinSpec(n_r, n_s, int(math.ceil(n_r / match_rate)), t))
+    return out
+
+
+def to_numpy_u(rel: torch.Tensor):
+    """(n, 2) int32/int64 tensor -> numpy uint32/uint64 view of the same bytes (CPU copy)."""
+    import numpy as np
+
+    a = rel.detach().cpu().contiguous().numpy()
+    return a.view(np.uint32 if a.dtype == np.int32 else np.uint64)
