@@ -1,0 +1,392 @@
+#!/usr/bin/env python
+"""Throughput of the GB300 hash-join engine: (|R| + |S|) tuples per second.
+
+Default workload: the radix-partitioned hash join (PHJ) of |R| = 2^24 and
+|S| = 2^28 tuples of (uint32 key, uint32 rid); R keys a seeded permutation of
+1..2^24, S keys uniform over [1, 2^25] (about half of S matches).  One step is a
+whole join through the C ABI (hj_join): partition R and S, join every partition
+pair, materialise the (rid_R, rid_S) pairs.  Inputs (2.28 GB) exceed the 129 MB
+L2, so no flush is needed between steps.
+
+Prints ONE JSON line (rank 0).  `--impl reference` times the CPU oracle instead.
+Under torchrun every rank joins its own seeded relations (independent problems,
+weak scaling, no data-path collective); value = all ranks' tuples / max time.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "(|R|+|S|) tuples/s"
+UNIT = "tuples/s"
+
+WORKLOADS = {
+    "phj_16m_256m": dict(
+        nr=1 << 24, ns=1 << 28, dom=1 << 25, algo=2,
+        desc="PHJ radix-partitioned join, |R|=2^24, |S|=2^28 (uint32 key, uint32 rid); R keys a seeded "
+             "permutation of 1..2^24, S keys uniform over [1, 2^25] (~50% match); pairs materialised"),
+    "shj_1m": dict(
+        nr=1 << 20, ns=1 << 20, dom=1 << 20, algo=1,
+        desc="SHJ, |R|=|S|=2^20 (uint32 key, uint32 rid); R keys a permutation of 1..2^20, S keys drawn "
+             "from R's keys (every probe matches once); pairs materialised"),
+}
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=200)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="hj", choices=["hj", "reference"])
+    ap.add_argument("--workload", default="phj_16m_256m", choices=sorted(WORKLOADS))
+    ap.add_argument("--radix-bits", type=int, default=0)
+    ap.add_argument("--passes", type=int, default=0)
+    ap.add_argument("--e2e-steps", type=int, default=3)
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-clocks", action="store_true")
+    return ap.parse_args()
+
+
+def dist_env():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+# ------------------------------------------------------------------- peaks, clocks
+
+
+def measured_peak():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        with open(path) as f:
+            return float(json.load(f)["hbm_gbs"]), "measured"
+    except Exception:
+        return 6800.0, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi samples of SM clock and throttle reasons while the timed region runs."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, device: int):
+        self.device = device
+        self.proc = None
+        self.lines = []
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits", "-lms", "100",
+                 "-i", str(self.device)], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except Exception:
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if not self.proc:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"], "samples": 0}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        self.t.join(timeout=2)
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            parts = [p.strip() for p in ln.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                smax.append(float(parts[2]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(nm)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(smax) if smax else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+# ------------------------------------------------------------------- roofline
+
+
+def kernel_bytes(name: str, wl: dict, w: int, passes: int, pairs: int) -> float:
+    """Algorithmic bytes one step moves in all launches of kernel `name`."""
+    n = wl["nr"] + wl["ns"]
+    tb = 2 * w
+    if name == "partition_scatter":      # read + write every tuple, each pass
+        return 2.0 * tb * n * passes
+    if name == "partition_hist":         # read every tuple, each pass
+        return 1.0 * tb * n * passes
+    if name == "partition_join":         # read both partitioned relations, write the pairs
+        return tb * n + tb * pairs
+    if name == "table_build":
+        return tb * wl["nr"]
+    if name == "table_probe":
+        return tb * wl["ns"] + tb * pairs
+    return 0.0
+
+
+def traffic_record(kernel: str, workload: str):
+    """DRAM bytes per launch of `kernel` from the committed ncu summary, if the
+    kernel source is unchanged since it was captured (else None)."""
+    path = os.path.join(ROOT, "profiles", "ncu_traffic.json")
+    try:
+        with open(path) as f:
+            rec = json.load(f)[workload][kernel]
+        src = os.path.join(ROOT, "paper_1307_1955_gb300", "csrc", rec["source"])
+        h = hashlib.sha256(open(src, "rb").read()).hexdigest()[:16]
+        return rec["bytes_per_launch"] if h == rec["source_sha"] else None
+    except Exception:
+        return None
+
+
+# ------------------------------------------------------------------- CPU oracle
+
+
+def oracle_rate(R_np, S_np):
+    """Run the oracle's hash join once; return (tuples, seconds)."""
+    import oracle
+
+    t0 = time.perf_counter()
+    rr, ss = oracle.hash_join(R_np, S_np, cap_hint=len(S_np))
+    dt = time.perf_counter() - t0
+    return len(R_np) + len(S_np), dt, len(rr)
+
+
+def make_inputs(wl, rank, device):
+    from paper_1307_1955_gb300 import workload as W
+
+    return W.unique_and_uniform(wl["nr"], wl["ns"], wl["dom"], W.DEFAULT_SEED, device, ids=(2, rank))
+
+
+def cpu_sample(wl, R, S, target_s: float):
+    """Oracle on a bounded sample: all of R and a prefix of S sized to about target_s."""
+    from paper_1307_1955_gb300 import workload as W
+
+    Rn = W.to_numpy_u(R)
+    ns0 = min(len(S), 1 << 20)
+    n, dt, _ = oracle_rate(Rn, W.to_numpy_u(S[:ns0]))
+    # time per S tuple beyond the build, from one calibration run
+    rate = max(n / dt, 1.0)
+    want = int(min(len(S), max(ns0, rate * target_s - len(Rn))))
+    Ss = W.to_numpy_u(S[:want])
+    n, dt, m = oracle_rate(Rn, Ss)
+    return {"value": n / dt, "unit": UNIT, "cores": 1, "kind": "oracle",
+            "sample": f"all |R|={len(Rn)} tuples, first {want} of |S|={len(S)} tuples "
+                      f"({m} pairs materialised), single-threaded C oracle, {dt:.1f} s"}
+
+
+# ------------------------------------------------------------------- arms
+
+
+def run_reference(args, wl, ws, rank):
+    """The CPU oracle on the machine's host cores, one bounded sample per step."""
+    if rank != 0:
+        return
+    import torch
+
+    from paper_1307_1955_gb300 import workload as W
+    import oracle
+
+    oracle.build()
+    total = args.steps + args.warmup
+    per_step = max(0.05, min(20.0, 150.0 / max(total, 1)))
+    # Scale the workload down (|S| / |R| and the key-domain ratio kept) so that one
+    # step takes about per_step seconds: time the oracle at 1/256 and extrapolate.
+    cal = 256
+    R, S = W.unique_and_uniform(wl["nr"] // cal, wl["ns"] // cal, wl["dom"] // cal, W.DEFAULT_SEED, "cpu",
+                                ids=(2, 0))
+    _, dt_cal, _ = oracle_rate(W.to_numpy_u(R), W.to_numpy_u(S))
+    scale = 1
+    while dt_cal * cal / scale > per_step and scale < (1 << 14):
+        scale *= 2
+    R, S = W.unique_and_uniform(wl["nr"] // scale, wl["ns"] // scale, wl["dom"] // scale, W.DEFAULT_SEED, "cpu",
+                                ids=(2, 0))
+    Rn, Sn = W.to_numpy_u(R), W.to_numpy_u(S)
+    for _ in range(args.warmup):
+        oracle_rate(Rn, Sn)
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        oracle_rate(Rn, Sn)
+    dt = time.perf_counter() - t0
+    value = (len(Rn) + len(Sn)) * args.steps / dt
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": 1000 * dt / max(args.steps, 1), "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "u32", "data": "synthetic",
+        "config": {"workload": wl["desc"], "sample_scale": f"1/{scale} of |R| and |S|"},
+        "cpu_baseline": {"value": value, "unit": UNIT, "kind": "oracle", "cores": 1,
+                         "sample": f"|R|={len(Rn)}, |S|={len(Sn)} (the workload scaled by 1/{scale}), "
+                                   f"single-threaded C oracle hash join, pairs materialised"},
+        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+
+
+def run_hj(args, wl, ws, rank, local):
+    import torch
+    import torch.distributed as dist
+
+    import __graft_entry__
+
+    if ws > 1:
+        dist.init_process_group("nccl" if torch.cuda.is_available() else "gloo")
+    torch.cuda.set_device(local)
+    if rank == 0:
+        __graft_entry__.build()
+    if ws > 1:
+        dist.barrier()
+    from paper_1307_1955_gb300 import hj
+
+    dev = torch.device("cuda", local)
+    R, S = make_inputs(wl, rank, dev)
+    stream = torch.cuda.current_stream(dev)
+    ctx = hj.Context(local, stream=stream)
+    kw = dict(algo=wl["algo"], radix_bits=args.radix_bits, passes=args.passes)
+
+    def step():
+        res = hj.hj_join(ctx, R, S, **kw)
+        info = (res.count, res.radix_bits, res.passes, res.algo)
+        res.free()
+        return info
+
+    for _ in range(args.warmup):
+        info = step()
+    torch.cuda.synchronize()
+    sampler = ClockSampler(local)
+    if not args.no_clocks:
+        sampler.start()
+        time.sleep(0.3)
+    if ws > 1:
+        dist.barrier()
+    torch.cuda.synchronize()
+    hj.prof_reset(ctx)
+    hj.prof_enable(ctx, True)
+    l0 = hj.launch_count(ctx)
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    ev0.record(stream)
+    for _ in range(args.steps):
+        info = step()
+    ev1.record(stream)
+    torch.cuda.synchronize()
+    if ws > 1:
+        dist.barrier()
+    launches = hj.launch_count(ctx) - l0
+    ms = ev0.elapsed_time(ev1)
+    prof = hj.prof_read(ctx)
+    hj.prof_enable(ctx, False)
+    clocks = sampler.stop() if not args.no_clocks else None
+    if ws > 1:
+        t = torch.tensor([ms], device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms = float(t.item())
+    count, bits, passes, algo = info
+    tuples = (wl["nr"] + wl["ns"]) * args.steps * ws
+    value = tuples / (ms / 1000.0)
+
+    # roofline of the dominant kernel (algorithmic bytes / its event-timed duration)
+    peak, peak_kind = measured_peak()
+    w = 4
+    dom_name, (dom_launches, dom_ms) = max(prof.items(), key=lambda kv: kv[1][1])
+    g = max(passes, 1) if algo == 2 else 0
+    bytes_k = kernel_bytes(dom_name, wl, w, g, count) * args.steps
+    achieved = bytes_k / (dom_ms / 1000.0) / 1e9 if dom_ms > 0 else 0.0
+    per_launch_bytes = bytes_k / max(dom_launches, 1)
+    roofline = {"bound": "hbm", "kernel": dom_name, "achieved": achieved, "peak": peak, "unit": "GB/s",
+                "frac": achieved / peak, "peak_kind": peak_kind,
+                "bytes_per_launch": per_launch_bytes, "launches": dom_launches,
+                "avg_launch_ms": dom_ms / max(dom_launches, 1),
+                "traffic": traffic_record(dom_name, args.workload)}
+    # whole-join roofline: (2g + 1) w (|R| + |S|) + o M bytes per step (PHJ), w (|R|+|S|) + o M (SHJ)
+    n = wl["nr"] + wl["ns"]
+    join_bytes = ((2 * g + 1) * 8 * n if algo == 2 else 8 * n) + 8 * count
+    join_bytes_g1 = 3 * 8 * n + 8 * count if algo == 2 else join_bytes
+    step_s = ms / 1000.0 / args.steps
+    join_roof = {"bytes_per_step": join_bytes, "achieved_gbs": join_bytes / step_s / 1e9,
+                 "frac": join_bytes / step_s / 1e9 / peak, "frac_vs_g1": join_bytes_g1 / step_s / 1e9 / peak}
+    kernels = {k: {"launches": v[0], "ms": v[1], "share": v[1] / sum(x[1] for x in prof.values())}
+               for k, v in sorted(prof.items(), key=lambda kv: -kv[1][1])}
+
+    # end to end through hj_join_host: host buffers, copies inside the timed region
+    e2e = None
+    if not args.no_e2e:
+        Rh = R.cpu().pin_memory()
+        Sh = S.cpu().pin_memory()
+        out = torch.empty((wl["ns"] + (1 << 20), 2), dtype=torch.int32).pin_memory()
+        res = hj.hj_join_host(ctx, Rh, Sh, out, **kw)
+        m = res.count
+        if ws > 1:
+            dist.barrier()
+        t0 = time.perf_counter()
+        for _ in range(args.e2e_steps):
+            res = hj.hj_join_host(ctx, Rh, Sh, out, **kw)
+        torch.cuda.synchronize()
+        dt = time.perf_counter() - t0
+        if ws > 1:
+            t = torch.tensor([dt], device=dev)
+            dist.all_reduce(t, op=dist.ReduceOp.MAX)
+            dt = float(t.item())
+        e2e = {"value": (wl["nr"] + wl["ns"]) * args.e2e_steps * ws / dt, "unit": UNIT,
+               "h2d_bytes_per_step": 8 * (wl["nr"] + wl["ns"]), "d2h_bytes_per_step": 8 * m + 24,
+               "api": "hj_join_host", "steps": args.e2e_steps}
+        del Rh, Sh, out
+
+    cpu = None
+    if rank == 0 and not args.no_cpu_baseline:
+        cpu = cpu_sample(wl, R, S, target_s=15.0)
+
+    if rank == 0:
+        line = {
+            "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "u32", "data": "synthetic",
+            "config": {"workload": wl["desc"], "algo": {1: "SHJ", 2: "PHJ"}[algo], "radix_bits": bits,
+                       "passes": passes, "pairs_per_step": count, "parallelism": f"replicas x{ws}",
+                       "l2": "inputs 2.28 GB per step exceed the 129 MB L2; no flush"
+                       if wl["ns"] >= (1 << 24) else "inputs smaller than L2; warm L2 across steps"},
+            "roofline": roofline, "join_roofline": join_roof, "kernels": kernels,
+            "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches, "clocks": clocks,
+        }
+        print(json.dumps(line), flush=True)
+    ctx.close()
+    if ws > 1:
+        dist.destroy_process_group()
+
+
+def main():
+    args = parse()
+    ws, rank, local = dist_env()
+    wl = WORKLOADS[args.workload]
+    if args.impl == "reference":
+        run_reference(args, wl, ws, rank)
+    else:
+        run_hj(args, wl, ws, rank, local)
+
+
+if __name__ == "__main__":
+    main()

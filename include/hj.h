@@ -1,0 +1,196 @@
+/*
+ * hj.h -- C ABI of the GB300 hash-join engine (libhj.so).
+ *
+ * The engine computes the equi-join of two relations R and S of <key, rid> tuples:
+ * the multiset of pairs (r.rid, s.rid) with r.key == s.key.  Its two algorithms are
+ * the simple hash join (SHJ: build a table on R, probe it with S -- Sec. 3.1,
+ * Alg. 1) and the radix-partitioned hash join (PHJ: partition R and S on low bits
+ * of the key hash in one or two passes, then run SHJ on every partition pair --
+ * Sec. 3.1, Alg. 2).  Tuples are two integer attributes (Sec. 5.1); here both are
+ * 4 bytes (HJ_U32) or both 8 bytes (HJ_U64).
+ *
+ * Conventions shared by every call:
+ *   - Tuple and offset pointers are DEVICE pointers on the context's device unless
+ *     a call says otherwise.  The caller owns its inputs; the library never frees
+ *     or writes them.  Buffers the library returns (tables, pairs, partitions) are
+ *     library-owned and released with the matching *_free call.
+ *   - Work is ordered on the context's CUDA stream.  Calls that return a count
+ *     (hj_probe, hj_join, hj_join_batch, hj_partition) synchronise that stream
+ *     before returning.
+ *   - Relations are arrays of n tuples, AoS, key first then rid, each field
+ *     `width` bytes, little-endian; `tuples` must be 16-byte aligned (n = 0 allows
+ *     NULL).  No key or rid value is reserved: 0 and 2^(8*width)-1 are ordinary.
+ *   - Every call returns an hj_status; nothing aborts, traps or prints.
+ *     hj_last_error() describes the last failure on a context.
+ *   - The radix digit and the table bucket come from MurmurHash2 (Sec. 5.1) of the
+ *     key's little-endian bytes with seed 0: the 32-bit variant for 4-byte keys,
+ *     MurmurHash64A for 8-byte keys.  The digit of pass one is bits [0, b1) of the
+ *     hash, of pass two bits [b1, b1 + b2) (Alg. 2: "lower bits of the integer hash
+ *     values"); table buckets use the high bits.
+ */
+#ifndef HJ_H
+#define HJ_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef int32_t hj_status;
+#define HJ_OK 0
+#define HJ_E_INVALID 1     /* bad argument: NULL, width, alignment, sizes          */
+#define HJ_E_NOMEM 2       /* device allocation failed or HBM budget exceeded      */
+#define HJ_E_OVERFLOW 3    /* caller capacity too small; the required size is set */
+#define HJ_E_CUDA 4        /* a CUDA runtime call failed                           */
+#define HJ_E_TIMEOUT 5     /* a bounded device-side wait expired                   */
+#define HJ_E_UNSUPPORTED 6 /* valid request this build does not implement         */
+#define HJ_E_PENDING 7     /* serving: request not finished yet                    */
+
+#define HJ_U32 4
+#define HJ_U64 8
+
+/* A relation: n tuples of <key, rid>, both fields `width` bytes (HJ_U32 or HJ_U64). */
+typedef struct hj_rel {
+    const void *tuples;
+    uint64_t n;
+    int32_t width;
+    int32_t reserved;
+} hj_rel;
+
+/* Output modes.  COUNT returns |J|; COUNT_CHECKSUM adds two order-independent sums
+ * over J, c0 = sum A(rid_R) * B(rid_S) and c1 = sum A(rid_R) + B(rid_S) (mod 2^64),
+ * with A(x) the SplitMix64 finaliser of x and B(x) = A(x ^ 0x9E3779B97F4A7C15);
+ * both are computed per key without forming pairs.  MATERIALIZE also returns the
+ * pairs in a device buffer. */
+#define HJ_COUNT 0
+#define HJ_COUNT_CHECKSUM 1
+#define HJ_MATERIALIZE 2
+
+#define HJ_ALGO_AUTO 0
+#define HJ_ALGO_SHJ 1
+#define HJ_ALGO_PHJ 2
+
+/* opts.flags */
+#define HJ_FLAG_CHECKSUM 1u /* MATERIALIZE: also compute c0, c1 over the pairs */
+
+typedef struct hj_opts {
+    int32_t algo;          /* HJ_ALGO_*                                              */
+    int32_t mode;          /* HJ_COUNT, HJ_COUNT_CHECKSUM, HJ_MATERIALIZE            */
+    int32_t radix_bits;    /* PHJ: total radix bits b1 + b2 (0: the tuner chooses)  */
+    int32_t passes;        /* PHJ: 1 or 2 partition passes (0: the tuner chooses)   */
+    uint64_t out_capacity; /* MATERIALIZE: initial pair capacity (0: |S|); a join
+                              with more pairs is re-run once at the exact size     */
+    uint64_t flags;        /* HJ_FLAG_*                                              */
+} hj_opts;
+
+/* Result of a join.  `pairs` holds `count` pairs (rid_R, rid_S), each field `width`
+ * bytes (the relations' width), in no particular order; NULL in the count modes.
+ * It is library-owned: release it with hj_result_free. */
+typedef struct hj_result {
+    uint64_t count;
+    uint64_t checksum[2];
+    void *pairs;
+    uint64_t pairs_cap;
+    int32_t width;
+    int32_t algo;       /* algorithm that ran: HJ_ALGO_SHJ or HJ_ALGO_PHJ */
+    int32_t radix_bits; /* PHJ: total radix bits used                     */
+    int32_t passes;     /* PHJ: partition passes used                     */
+} hj_result;
+
+typedef struct hj_ctx hj_ctx;
+typedef struct hj_table hj_table;
+
+/* Create a context on `device`.  `cuda_stream` is a cudaStream_t to order work on
+ * (NULL: the library creates its own non-blocking stream).  `hbm_budget_bytes`
+ * caps the device memory the library holds at once (0: no cap).  Every later call
+ * on the context must run with that device current or will make it current. */
+hj_status hj_create(hj_ctx **ctx, int device, void *cuda_stream, uint64_t hbm_budget_bytes);
+
+/* Release the context and every buffer it still owns. */
+hj_status hj_destroy(hj_ctx *ctx);
+
+/* Text of the last error on the context ("" if none).  Valid until the next call. */
+const char *hj_last_error(const hj_ctx *ctx);
+
+/* SHJ build phase (Alg. 1, steps b1-b4): a device hash table on R.  For the
+ * MATERIALIZE mode the table holds every R tuple (duplicates kept as separate
+ * entries); for the count modes it holds one entry per distinct key with the
+ * tuple count and the sum of A(rid).  `opts->mode` fixes which; the table is only
+ * valid for probes in a mode of the same family.  R is read during the call's
+ * stream work only; the table does not point into R. */
+hj_status hj_build(hj_ctx *ctx, const hj_rel *R, const hj_opts *opts, hj_table **out);
+
+/* SHJ probe phase (Alg. 1, steps p1-p4): look every S tuple up in `table` and
+ * produce the join result in `out` (count, checksums, pairs as `opts->mode` says).
+ * HJ_E_INVALID if S's width differs from the table's or the modes differ. */
+hj_status hj_probe(hj_ctx *ctx, const hj_table *table, const hj_rel *S, const hj_opts *opts,
+                   hj_result *out);
+
+hj_status hj_table_free(hj_ctx *ctx, hj_table *table);
+
+/* Radix partitioning (Alg. 2, steps n1-n3): split `in` into 2^(b1+b2) partitions,
+ * pass one on hash bits [0, b1), pass two (if b2 > 0) on bits [b1, b1 + b2) within
+ * each pass-one partition.  Partition p = d1 * 2^b2 + d2 is rows
+ * [offsets[p], offsets[p+1]) of `out_tuples`; the order of tuples inside a
+ * partition is unspecified.  b1 in [1, 12], b2 in [0, 12].
+ * `out_tuples->tuples` and `*out_offsets` (2^(b1+b2) + 1 uint64 entries) are
+ * library-owned device buffers; release them with hj_partition_free. */
+hj_status hj_partition(hj_ctx *ctx, const hj_rel *in, int b1, int b2, hj_rel *out_tuples,
+                       uint64_t **out_offsets);
+hj_status hj_partition_free(hj_ctx *ctx, hj_rel *tuples, uint64_t *offsets);
+
+/* The whole join: SHJ or PHJ (opts->algo, HJ_ALGO_AUTO lets the tuner pick), with
+ * partitioning, per-partition build and probe, and output.  `out` as for hj_probe. */
+hj_status hj_join(hj_ctx *ctx, const hj_rel *R, const hj_rel *S, const hj_opts *opts,
+                  hj_result *out);
+
+/* End-to-end join on HOST buffers: copies R and S from host memory (page-locked
+ * memory gives full link speed; pageable works) to device buffers the library
+ * allocates, runs hj_join, and copies the pairs into `pairs_host` (room for
+ * `pairs_host_cap` pairs of 2 * width bytes; may be NULL in the count modes).
+ * `out->pairs` is NULL on return: nothing stays on the device.  If the join has
+ * more pairs than `pairs_host_cap`, the first pairs_host_cap are copied and
+ * HJ_E_OVERFLOW is returned with out->count set to the full count. */
+hj_status hj_join_host(hj_ctx *ctx, const hj_rel *R_host, const hj_rel *S_host, const hj_opts *opts,
+                       void *pairs_host, uint64_t pairs_host_cap, hj_result *out);
+
+/* Release a result's pairs (no-op for the count modes) and zero the struct. */
+hj_status hj_result_free(hj_ctx *ctx, hj_result *res);
+
+/* Wait for all work queued on the context's stream. */
+hj_status hj_sync(hj_ctx *ctx);
+
+/* Copy `bytes` between any two host or device buffers (cudaMemcpyDefault
+ * semantics), ordered on the context's stream; returns after the copy is done.
+ * Used to read library-owned results (pairs, offsets) into caller memory. */
+hj_status hj_copy(hj_ctx *ctx, void *dst, const void *src, uint64_t bytes);
+
+/* Per-kernel timing on the context's stream.  While enabled, every kernel launch
+ * is bracketed by CUDA events; hj_prof_read synchronises, then reports, for up to
+ * `cap` distinct kernel names, the name (NUL-terminated, at most 47 chars), the
+ * number of launches and the summed device milliseconds, and returns how many
+ * names exist in *n_out.  hj_prof_reset clears the record.  hj_launch_count returns
+ * the number of kernels this context has launched since creation. */
+typedef struct hj_prof_entry {
+    char name[48];
+    uint64_t launches;
+    double ms;
+} hj_prof_entry;
+hj_status hj_prof_enable(hj_ctx *ctx, int on);
+hj_status hj_prof_reset(hj_ctx *ctx);
+hj_status hj_prof_read(hj_ctx *ctx, hj_prof_entry *entries, int cap, int *n_out);
+uint64_t hj_launch_count(const hj_ctx *ctx);
+
+/* Host-side fault injection for tests (no GPU fault is involved):
+ * hj_debug_fail_alloc makes the n-th device allocation from now fail with
+ * HJ_E_NOMEM (n < 0 disarms); hj_debug_bytes_in_use reports the device bytes the
+ * context currently holds (0 after every buffer has been released). */
+hj_status hj_debug_fail_alloc(hj_ctx *ctx, int64_t n);
+uint64_t hj_debug_bytes_in_use(const hj_ctx *ctx);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* HJ_H */

@@ -115,15 +115,20 @@ def key_hash(key: int, width: int, seed: int = HASH_SEED) -> int:
     return int(_load().oracle_key_hash(key, width, seed))
 
 
-def _join(fn_name: str, R: np.ndarray, S: np.ndarray):
+def _join(fn_name: str, R: np.ndarray, S: np.ndarray, cap_hint: int | None = None):
     R, w = _rel(R)
     S, w2 = _rel(S)
     if w != w2:
         raise ValueError("R and S must have the same width")
     fn = getattr(_load(), fn_name)
-    n = fn(w, _ptr(R), len(R), _ptr(S), len(S), None, None, 0)
+    cap = 0 if cap_hint is None else int(cap_hint)
+    rr = np.empty(cap, np.uint64)
+    ss = np.empty(cap, np.uint64)
+    n = fn(w, _ptr(R), len(R), _ptr(S), len(S), _ptr(rr), _ptr(ss), cap)
     if n < 0:
         raise MemoryError(fn_name)
+    if n <= cap:
+        return rr[:n], ss[:n]
     rr = np.empty(n, np.uint64)
     ss = np.empty(n, np.uint64)
     n2 = fn(w, _ptr(R), len(R), _ptr(S), len(S), _ptr(rr), _ptr(ss), n)
@@ -131,9 +136,10 @@ def _join(fn_name: str, R: np.ndarray, S: np.ndarray):
     return rr, ss
 
 
-def hash_join(R: np.ndarray, S: np.ndarray):
-    """Pairs (rid_R, rid_S) of R join S on key, in probe order (two uint64 arrays)."""
-    return _join("oracle_hash_join", R, S)
+def hash_join(R: np.ndarray, S: np.ndarray, cap_hint: int | None = None):
+    """Pairs (rid_R, rid_S) of R join S on key, in probe order (two uint64 arrays).
+    With cap_hint >= the pair count the join runs once; otherwise it counts first."""
+    return _join("oracle_hash_join", R, S, cap_hint)
 
 
 def nested_loop_join(R: np.ndarray, S: np.ndarray):

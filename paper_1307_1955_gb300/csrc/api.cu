@@ -1,0 +1,366 @@
+// api.cu -- the C ABI of include/hj.h: argument checks, plan choice, and the
+// SHJ / PHJ drivers that sequence the kernels of join.cu and partition.cu.
+#include <algorithm>
+#include <cmath>
+#include <vector>
+
+#include "common.cuh"
+#include "engine.cuh"
+
+using namespace hj;
+
+namespace {
+
+hj_status check_rel(hj_ctx *c, const hj_rel *r, const char *name) {
+    if (!r) return set_err(c, HJ_E_INVALID, "%s is NULL", name);
+    if (r->width != HJ_U32 && r->width != HJ_U64)
+        return set_err(c, HJ_E_INVALID, "%s width %d is not 4 or 8", name, r->width);
+    if (r->n && !r->tuples) return set_err(c, HJ_E_INVALID, "%s has %llu tuples but a NULL pointer", name,
+                                           (unsigned long long)r->n);
+    if (r->n && ((uintptr_t)r->tuples & 15))
+        return set_err(c, HJ_E_INVALID, "%s tuples are not 16-byte aligned", name);
+    if (r->width == HJ_U32 && r->n >= 0xFFFFFFFFull)
+        return set_err(c, HJ_E_INVALID, "%s: 4-byte relations hold fewer than 2^32 - 1 tuples", name);
+    return HJ_OK;
+}
+
+hj_status check_ctx(hj_ctx *c) {
+    if (!c) return HJ_E_INVALID;
+    c->err.clear();
+    if (cudaSetDevice(c->device) != cudaSuccess) return cuda_err(c, cudaGetLastError(), "cudaSetDevice");
+    return HJ_OK;
+}
+
+hj_opts default_opts() {
+    hj_opts o;
+    o.algo = HJ_ALGO_AUTO;
+    o.mode = HJ_MATERIALIZE;
+    o.radix_bits = 0;
+    o.passes = 0;
+    o.out_capacity = 0;
+    o.flags = 0;
+    return o;
+}
+
+bool is_agg(int mode) { return mode == HJ_COUNT || mode == HJ_COUNT_CHECKSUM; }
+bool wants_checksum(const hj_opts &o) {
+    return o.mode == HJ_COUNT_CHECKSUM || (o.mode == HJ_MATERIALIZE && (o.flags & HJ_FLAG_CHECKSUM));
+}
+
+uint64_t slot_bytes(int width, bool agg) {
+    if (!agg) return 2ull * width;
+    return width == 4 ? sizeof(AggSlot<4>) : sizeof(AggSlot<8>);
+}
+
+// Plan choice (the cost model's GPU-only case, Sec. 4 Eq. 1-2 with every step on
+// the GPU): SHJ while its table is small enough to stay in L2; otherwise PHJ with
+// enough radix bits that a partition of R holds about 4096 tuples (a shared-memory
+// table), in one pass up to 12 bits and two passes beyond.
+void plan(const hj_rel *R, const hj_opts &o, int *algo, int *bits, int *passes) {
+    uint64_t nR = R->n;
+    int a = o.algo;
+    if (a == HJ_ALGO_AUTO) {
+        uint64_t cap = 64;
+        while (cap < 2 * nR + 1) cap <<= 1;
+        a = cap * slot_bytes(R->width, is_agg(o.mode)) <= (32ull << 20) ? HJ_ALGO_SHJ : HJ_ALGO_PHJ;
+    }
+    *algo = a;
+    int b = o.radix_bits;
+    if (b <= 0) {
+        b = 1;
+        while (b < 24 && (nR >> b) > 4096) b++;
+    }
+    *bits = b;
+    int p = o.passes;
+    if (p <= 0) p = b <= 12 ? 1 : 2;
+    *passes = p;
+}
+
+hj_status upload_u64(hj_ctx *c, const std::vector<uint64_t> &v, DevBuf &out) {
+    HJ_TRY(out.alloc(v.size() * 8));
+    HJ_CUDA(c, cudaMemcpyAsync(out.p, v.data(), v.size() * 8, cudaMemcpyHostToDevice, c->stream));
+    HJ_CUDA(c, cudaStreamSynchronize(c->stream));  // v is a host temporary
+    return HJ_OK;
+}
+
+// Partition a whole relation in one or two passes (Alg. 2); on success `tuples`
+// (padded by 64 bytes) and `offsets` (2^(b1+b2) + 1 entries) hold the result.
+hj_status partition_rel(hj_ctx *c, const hj_rel *in, int b1, int b2, DevBuf &tuples, DevBuf &offsets) {
+    const uint64_t n = in->n, tb = tuple_bytes(in->width);
+    DevBuf seg(c), A(c), off1(c);
+    HJ_TRY(upload_u64(c, {0ull, n}, seg));
+    HJ_TRY(A.alloc(n * tb + 64));
+    HJ_TRY(off1.alloc(((1ull << b1) + 1) * 8));
+    HJ_TRY(partition_pass(c, in->width, in->tuples, n, seg.as<uint64_t>(), 1, 0, b1, A.p, off1.as<uint64_t>()));
+    if (b2 == 0) {
+        tuples.reset();
+        offsets.reset();
+        tuples.p = A.release();
+        offsets.p = off1.release();
+        return HJ_OK;
+    }
+    DevBuf B(c), off2(c);
+    HJ_TRY(B.alloc(n * tb + 64));
+    HJ_TRY(off2.alloc(((1ull << (b1 + b2)) + 1) * 8));
+    HJ_TRY(partition_pass(c, in->width, A.p, n, off1.as<uint64_t>(), 1ull << b1, b1, b2, B.p, off2.as<uint64_t>()));
+    tuples.reset();
+    offsets.reset();
+    tuples.p = B.release();
+    offsets.p = off2.release();
+    return HJ_OK;
+}
+
+void fill_result(hj_ctx *c, hj_result *res, int width, int algo, int bits, int passes) {
+    res->count = c->h_ctr->count;
+    res->checksum[0] = c->h_ctr->c0;
+    res->checksum[1] = c->h_ctr->c1;
+    res->width = width;
+    res->algo = algo;
+    res->radix_bits = algo == HJ_ALGO_PHJ ? bits : 0;
+    res->passes = algo == HJ_ALGO_PHJ ? passes : 0;
+}
+
+struct TableGuard {
+    hj_ctx *c;
+    hj_table *t = nullptr;
+    ~TableGuard() { table_destroy(c, t); }
+};
+
+// ----------------------------------------------------------------------- SHJ
+hj_status join_shj(hj_ctx *c, const hj_rel *R, const hj_rel *S, const hj_opts &o, hj_result *res) {
+    const bool agg = is_agg(o.mode), mat = o.mode == HJ_MATERIALIZE, chk = wants_checksum(o);
+    TableGuard tg{c};
+    HJ_TRY(zero_counters(c));
+    HJ_TRY(table_create(c, R->width, agg, R->n, &tg.t));
+    HJ_TRY(table_build(c, tg.t, R->tuples, 0, R->n, R->n));
+    uint64_t cap = mat ? (o.out_capacity ? o.out_capacity : S->n) : 0;
+    DevBuf pairs(c);
+    if (mat) HJ_TRY(pairs.alloc(std::max<uint64_t>(cap, 1) * tuple_bytes(R->width)));
+    for (int attempt = 0; attempt < 2; ++attempt) {
+        HJ_TRY(table_probe(c, tg.t, S->tuples, 0, S->n, S->n, pairs.p, cap, chk));
+        HJ_TRY(read_counters(c));
+        if (c->h_ctr->status & kStatusTableFull) return set_err(c, HJ_E_CUDA, "hash table unexpectedly full");
+        if (!mat || c->h_ctr->count <= cap) break;
+        // more pairs than the capacity: re-run the probe at the exact size
+        cap = c->h_ctr->count;
+        HJ_TRY(pairs.alloc(cap * tuple_bytes(R->width)));
+        HJ_TRY(zero_counters(c));
+    }
+    fill_result(c, res, R->width, HJ_ALGO_SHJ, 0, 0);
+    res->pairs = mat ? pairs.release() : nullptr;
+    res->pairs_cap = mat ? cap : 0;
+    return HJ_OK;
+}
+
+// ----------------------------------------------------------------------- PHJ
+hj_status run_partition_join(hj_ctx *c, const hj_rel *R, const hj_rel *S, const hj_opts &o, const void *Rp,
+                             const uint64_t *roff, const void *Sp, const uint64_t *soff, uint64_t NP, void *pairs,
+                             uint64_t cap, uint32_t *oversize) {
+    const bool agg = is_agg(o.mode), chk = wants_checksum(o);
+    const int W = R->width;
+    HJ_TRY(zero_counters(c));
+    uint64_t expect = NP ? (R->n + NP - 1) / NP : 0;
+    HJ_TRY(partition_join(c, W, agg, Rp, roff, R->n, Sp, soff, S->n, NP, expect, pairs, cap, chk, oversize));
+    HJ_TRY(read_counters(c));
+    uint64_t nov = c->h_ctr->n_oversize;
+    if (nov == 0) return HJ_OK;
+    // Partitions whose table did not fit in shared memory: SHJ with a global table.
+    std::vector<uint32_t> list(nov);
+    std::vector<uint64_t> hr(NP + 1), hs(NP + 1);
+    HJ_CUDA(c, cudaMemcpyAsync(list.data(), oversize, nov * 4, cudaMemcpyDeviceToHost, c->stream));
+    HJ_CUDA(c, cudaMemcpyAsync(hr.data(), roff, (NP + 1) * 8, cudaMemcpyDeviceToHost, c->stream));
+    HJ_CUDA(c, cudaMemcpyAsync(hs.data(), soff, (NP + 1) * 8, cudaMemcpyDeviceToHost, c->stream));
+    HJ_CUDA(c, cudaStreamSynchronize(c->stream));
+    for (uint32_t p : list) {
+        TableGuard tg{c};
+        HJ_TRY(table_create(c, W, agg, hr[p + 1] - hr[p], &tg.t));
+        HJ_TRY(table_build(c, tg.t, Rp, hr[p], hr[p + 1], R->n));
+        HJ_TRY(table_probe(c, tg.t, Sp, hs[p], hs[p + 1], S->n, pairs, cap, chk));
+    }
+    HJ_TRY(read_counters(c));
+    if (c->h_ctr->status & kStatusTableFull) return set_err(c, HJ_E_CUDA, "hash table unexpectedly full");
+    return HJ_OK;
+}
+
+hj_status join_phj(hj_ctx *c, const hj_rel *R, const hj_rel *S, const hj_opts &o, int bits, int passes,
+                   hj_result *res) {
+    const bool mat = o.mode == HJ_MATERIALIZE;
+    const int b1 = passes == 2 ? bits - bits / 2 : bits, b2 = passes == 2 ? bits / 2 : 0;
+    if (b1 < 1 || b1 > 12 || b2 < 0 || b2 > 12)
+        return set_err(c, HJ_E_INVALID, "radix bits %d in %d passes: each pass takes 1..12 bits", bits, passes);
+    const uint64_t NP = 1ull << bits;
+    DevBuf Rp(c), Sp(c), roff(c), soff(c), oversize(c), pairs(c);
+    HJ_TRY(partition_rel(c, R, b1, b2, Rp, roff));
+    HJ_TRY(partition_rel(c, S, b1, b2, Sp, soff));
+    HJ_TRY(oversize.alloc(NP * 4));
+    uint64_t cap = mat ? (o.out_capacity ? o.out_capacity : S->n) : 0;
+    if (mat) HJ_TRY(pairs.alloc(std::max<uint64_t>(cap, 1) * tuple_bytes(R->width)));
+    for (int attempt = 0; attempt < 2; ++attempt) {
+        HJ_TRY(run_partition_join(c, R, S, o, Rp.p, roff.as<uint64_t>(), Sp.p, soff.as<uint64_t>(), NP, pairs.p,
+                                  cap, oversize.as<uint32_t>()));
+        if (!mat || c->h_ctr->count <= cap) break;
+        cap = c->h_ctr->count;
+        HJ_TRY(pairs.alloc(cap * tuple_bytes(R->width)));
+    }
+    fill_result(c, res, R->width, HJ_ALGO_PHJ, bits, passes);
+    res->pairs = mat ? pairs.release() : nullptr;
+    res->pairs_cap = mat ? cap : 0;
+    return HJ_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+hj_status hj_build(hj_ctx *c, const hj_rel *R, const hj_opts *opts, hj_table **out) {
+    HJ_TRY(check_ctx(c));
+    if (!out) return set_err(c, HJ_E_INVALID, "out is NULL");
+    *out = nullptr;
+    HJ_TRY(check_rel(c, R, "R"));
+    hj_opts o = opts ? *opts : default_opts();
+    if (o.mode < HJ_COUNT || o.mode > HJ_MATERIALIZE) return set_err(c, HJ_E_INVALID, "bad mode %d", o.mode);
+    TableGuard tg{c};
+    HJ_TRY(zero_counters(c));
+    HJ_TRY(table_create(c, R->width, is_agg(o.mode), R->n, &tg.t));
+    HJ_TRY(table_build(c, tg.t, R->tuples, 0, R->n, R->n));
+    HJ_TRY(read_counters(c));
+    if (c->h_ctr->status & kStatusTableFull) return set_err(c, HJ_E_CUDA, "hash table unexpectedly full");
+    *out = tg.t;
+    tg.t = nullptr;
+    return HJ_OK;
+}
+
+hj_status hj_probe(hj_ctx *c, const hj_table *t, const hj_rel *S, const hj_opts *opts, hj_result *res) {
+    HJ_TRY(check_ctx(c));
+    if (!t || !res) return set_err(c, HJ_E_INVALID, "table or result is NULL");
+    HJ_TRY(check_rel(c, S, "S"));
+    hj_opts o = opts ? *opts : default_opts();
+    if (S->width != t->width) return set_err(c, HJ_E_INVALID, "S width %d differs from the table's %d", S->width, t->width);
+    if (is_agg(o.mode) != (t->agg != 0))
+        return set_err(c, HJ_E_INVALID, "probe mode %d does not match the table's build mode", o.mode);
+    *res = hj_result{};
+    const bool mat = o.mode == HJ_MATERIALIZE, chk = wants_checksum(o);
+    uint64_t cap = mat ? (o.out_capacity ? o.out_capacity : S->n) : 0;
+    DevBuf pairs(c);
+    if (mat) HJ_TRY(pairs.alloc(std::max<uint64_t>(cap, 1) * tuple_bytes(t->width)));
+    for (int attempt = 0; attempt < 2; ++attempt) {
+        HJ_TRY(zero_counters(c));
+        HJ_TRY(table_probe(c, t, S->tuples, 0, S->n, S->n, pairs.p, cap, chk));
+        HJ_TRY(read_counters(c));
+        if (!mat || c->h_ctr->count <= cap) break;
+        cap = c->h_ctr->count;
+        HJ_TRY(pairs.alloc(cap * tuple_bytes(t->width)));
+    }
+    fill_result(c, res, t->width, HJ_ALGO_SHJ, 0, 0);
+    res->pairs = mat ? pairs.release() : nullptr;
+    res->pairs_cap = mat ? cap : 0;
+    return HJ_OK;
+}
+
+hj_status hj_table_free(hj_ctx *c, hj_table *t) {
+    if (!c || !t) return HJ_E_INVALID;
+    cudaSetDevice(c->device);
+    table_destroy(c, t);
+    return HJ_OK;
+}
+
+hj_status hj_partition(hj_ctx *c, const hj_rel *in, int b1, int b2, hj_rel *out_tuples, uint64_t **out_offsets) {
+    HJ_TRY(check_ctx(c));
+    HJ_TRY(check_rel(c, in, "in"));
+    if (!out_tuples || !out_offsets) return set_err(c, HJ_E_INVALID, "output pointers are NULL");
+    if (b1 < 1 || b1 > 12 || b2 < 0 || b2 > 12)
+        return set_err(c, HJ_E_INVALID, "bits (%d, %d): pass one takes 1..12 bits, pass two 0..12", b1, b2);
+    DevBuf tup(c), off(c);
+    HJ_TRY(partition_rel(c, in, b1, b2, tup, off));
+    HJ_CUDA(c, cudaStreamSynchronize(c->stream));
+    out_tuples->tuples = tup.release();
+    out_tuples->n = in->n;
+    out_tuples->width = in->width;
+    out_tuples->reserved = 0;
+    *out_offsets = off.as<uint64_t>();
+    off.release();
+    return HJ_OK;
+}
+
+hj_status hj_partition_free(hj_ctx *c, hj_rel *tuples, uint64_t *offsets) {
+    if (!c) return HJ_E_INVALID;
+    cudaSetDevice(c->device);
+    if (tuples) {
+        dfree(c, (void *)tuples->tuples);
+        tuples->tuples = nullptr;
+        tuples->n = 0;
+    }
+    dfree(c, offsets);
+    return HJ_OK;
+}
+
+hj_status hj_join(hj_ctx *c, const hj_rel *R, const hj_rel *S, const hj_opts *opts, hj_result *res) {
+    HJ_TRY(check_ctx(c));
+    if (!res) return set_err(c, HJ_E_INVALID, "result is NULL");
+    HJ_TRY(check_rel(c, R, "R"));
+    HJ_TRY(check_rel(c, S, "S"));
+    if (R->width != S->width) return set_err(c, HJ_E_INVALID, "R and S widths differ (%d, %d)", R->width, S->width);
+    hj_opts o = opts ? *opts : default_opts();
+    if (o.mode < HJ_COUNT || o.mode > HJ_MATERIALIZE) return set_err(c, HJ_E_INVALID, "bad mode %d", o.mode);
+    if (o.algo < HJ_ALGO_AUTO || o.algo > HJ_ALGO_PHJ) return set_err(c, HJ_E_INVALID, "bad algo %d", o.algo);
+    if (o.passes < 0 || o.passes > 2) return set_err(c, HJ_E_INVALID, "passes %d not in {1, 2}", o.passes);
+    if (o.radix_bits < 0 || o.radix_bits > 24) return set_err(c, HJ_E_INVALID, "radix bits %d > 24", o.radix_bits);
+    *res = hj_result{};
+    int algo, bits, passes;
+    plan(R, o, &algo, &bits, &passes);
+    hj_status st = algo == HJ_ALGO_SHJ ? join_shj(c, R, S, o, res) : join_phj(c, R, S, o, bits, passes, res);
+    return st;
+}
+
+hj_status hj_copy(hj_ctx *c, void *dst, const void *src, uint64_t bytes) {
+    HJ_TRY(check_ctx(c));
+    if (!bytes) return HJ_OK;
+    if (!dst || !src) return set_err(c, HJ_E_INVALID, "copy with a NULL pointer");
+    HJ_CUDA(c, cudaMemcpyAsync(dst, src, bytes, cudaMemcpyDefault, c->stream));
+    HJ_CUDA(c, cudaStreamSynchronize(c->stream));
+    return HJ_OK;
+}
+
+hj_status hj_join_host(hj_ctx *c, const hj_rel *Rh, const hj_rel *Sh, const hj_opts *opts, void *pairs_host,
+                       uint64_t pairs_host_cap, hj_result *res) {
+    HJ_TRY(check_ctx(c));
+    if (!res) return set_err(c, HJ_E_INVALID, "result is NULL");
+    if (!Rh || !Sh) return set_err(c, HJ_E_INVALID, "relation is NULL");
+    if (Rh->width != HJ_U32 && Rh->width != HJ_U64) return set_err(c, HJ_E_INVALID, "bad width %d", Rh->width);
+    if (Rh->width != Sh->width) return set_err(c, HJ_E_INVALID, "R and S widths differ");
+    if ((Rh->n && !Rh->tuples) || (Sh->n && !Sh->tuples)) return set_err(c, HJ_E_INVALID, "NULL host tuples");
+    const uint64_t tb = tuple_bytes(Rh->width);
+    DevBuf dR(c), dS(c);
+    HJ_TRY(dR.alloc(Rh->n * tb + 64));
+    HJ_TRY(dS.alloc(Sh->n * tb + 64));
+    if (Rh->n) HJ_CUDA(c, cudaMemcpyAsync(dR.p, Rh->tuples, Rh->n * tb, cudaMemcpyHostToDevice, c->stream));
+    if (Sh->n) HJ_CUDA(c, cudaMemcpyAsync(dS.p, Sh->tuples, Sh->n * tb, cudaMemcpyHostToDevice, c->stream));
+    hj_rel R = *Rh, S = *Sh;
+    R.tuples = dR.p;
+    S.tuples = dS.p;
+    HJ_TRY(hj_join(c, &R, &S, opts, res));
+    DevBuf pairs(c);
+    pairs.p = res->pairs;  // released below whatever happens
+    res->pairs = nullptr;
+    res->pairs_cap = 0;
+    if (pairs.p && res->count) {
+        if (!pairs_host) return set_err(c, HJ_E_INVALID, "pairs_host is NULL but the join produced pairs");
+        uint64_t n = std::min(res->count, pairs_host_cap);
+        if (n) HJ_CUDA(c, cudaMemcpyAsync(pairs_host, pairs.p, n * tb, cudaMemcpyDeviceToHost, c->stream));
+        HJ_CUDA(c, cudaStreamSynchronize(c->stream));
+        if (n < res->count)
+            return set_err(c, HJ_E_OVERFLOW, "%llu pairs do not fit in %llu", (unsigned long long)res->count,
+                           (unsigned long long)pairs_host_cap);
+    }
+    return HJ_OK;
+}
+
+hj_status hj_result_free(hj_ctx *c, hj_result *res) {
+    if (!c || !res) return HJ_E_INVALID;
+    cudaSetDevice(c->device);
+    dfree(c, res->pairs);
+    *res = hj_result{};
+    return HJ_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,253 @@
+// ctx.cu -- context lifetime, memory pool with HBM budget, errors, profiling.
+#include <cstring>
+
+#include "ctx.cuh"
+
+namespace hj {
+
+hj_status set_err(hj_ctx *c, hj_status code, const char *fmt, ...) {
+    if (c) {
+        char buf[512];
+        va_list ap;
+        va_start(ap, fmt);
+        vsnprintf(buf, sizeof buf, fmt, ap);
+        va_end(ap);
+        c->err = buf;
+    }
+    return code;
+}
+
+hj_status cuda_err(hj_ctx *c, cudaError_t e, const char *what) {
+    return set_err(c, HJ_E_CUDA, "%s: %s", what, cudaGetErrorString(e));
+}
+
+void *dalloc(hj_ctx *c, uint64_t bytes, hj_status *st) {
+    *st = HJ_OK;
+    if (bytes == 0) bytes = 16;
+    bytes = (bytes + 255) & ~uint64_t(255);
+    if (c->fail_alloc_after == 0) {
+        c->fail_alloc_after = -1;
+        *st = set_err(c, HJ_E_NOMEM, "injected allocation failure (%llu bytes)", (unsigned long long)bytes);
+        return nullptr;
+    }
+    if (c->fail_alloc_after > 0) c->fail_alloc_after--;
+    if (c->budget && c->in_use + bytes > c->budget) {
+        *st = set_err(c, HJ_E_NOMEM, "HBM budget exceeded: %llu in use + %llu requested > %llu",
+                      (unsigned long long)c->in_use, (unsigned long long)bytes,
+                      (unsigned long long)c->budget);
+        return nullptr;
+    }
+    void *p = nullptr;
+    cudaError_t e = cudaMallocFromPoolAsync(&p, bytes, c->pool, c->stream);
+    if (e != cudaSuccess || !p) {
+        cudaGetLastError();
+        *st = set_err(c, HJ_E_NOMEM, "device allocation of %llu bytes failed: %s",
+                      (unsigned long long)bytes, cudaGetErrorString(e));
+        return nullptr;
+    }
+    c->allocs[p] = bytes;
+    c->in_use += bytes;
+    if (c->in_use > c->peak) c->peak = c->in_use;
+    return p;
+}
+
+void dfree(hj_ctx *c, void *p) {
+    if (!p) return;
+    auto it = c->allocs.find(p);
+    if (it == c->allocs.end()) return;
+    c->in_use -= it->second;
+    c->allocs.erase(it);
+    cudaFreeAsync(p, c->stream);
+}
+
+static cudaEvent_t take_event(hj_ctx *c) {
+    if (!c->spare_events.empty()) {
+        cudaEvent_t e = c->spare_events.back();
+        c->spare_events.pop_back();
+        return e;
+    }
+    cudaEvent_t e;
+    cudaEventCreate(&e);
+    return e;
+}
+
+void prof_begin(hj_ctx *c, const char *name) {
+    c->launches++;
+    if (!c->prof) return;
+    hj_ctx::Rec r;
+    r.name = name;
+    r.a = take_event(c);
+    r.b = take_event(c);
+    cudaEventRecord(r.a, c->stream);
+    c->recs.push_back(r);
+}
+
+void prof_end(hj_ctx *c) {
+    if (!c->prof || c->recs.empty()) return;
+    cudaEventRecord(c->recs.back().b, c->stream);
+}
+
+hj_status check_launch(hj_ctx *c, const char *name) {
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return set_err(c, HJ_E_CUDA, "launch of %s failed: %s", name, cudaGetErrorString(e));
+    return HJ_OK;
+}
+
+static void prof_collect(hj_ctx *c) {
+    for (auto &r : c->recs) {
+        float ms = 0.f;
+        cudaEventElapsedTime(&ms, r.a, r.b);
+        auto &acc = c->prof_acc[r.name];
+        acc.first += 1;
+        acc.second += ms;
+        c->spare_events.push_back(r.a);
+        c->spare_events.push_back(r.b);
+    }
+    c->recs.clear();
+}
+
+hj_status read_counters(hj_ctx *c) {
+    HJ_CUDA(c, cudaMemcpyAsync(c->h_ctr, c->d_ctr, sizeof(hj_counters), cudaMemcpyDeviceToHost, c->stream));
+    HJ_CUDA(c, cudaStreamSynchronize(c->stream));
+    if (c->h_ctr->status & 2ull) return set_err(c, HJ_E_TIMEOUT, "a bounded device wait expired");
+    if (c->h_ctr->status & 4ull) return set_err(c, HJ_E_INVALID, "a kernel rejected its input");
+    return HJ_OK;
+}
+
+hj_status zero_counters(hj_ctx *c) {
+    HJ_CUDA(c, cudaMemsetAsync(c->d_ctr, 0, sizeof(hj_counters), c->stream));
+    return HJ_OK;
+}
+
+int num_sms(hj_ctx *c) {
+    int n = 0;
+    cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, c->device);
+    return n > 0 ? n : 1;
+}
+
+}  // namespace hj
+
+using namespace hj;
+
+extern "C" {
+
+hj_status hj_create(hj_ctx **out, int device, void *cuda_stream, uint64_t budget) {
+    if (!out) return HJ_E_INVALID;
+    *out = nullptr;
+    int ndev = 0;
+    if (cudaGetDeviceCount(&ndev) != cudaSuccess || device < 0 || device >= ndev) {
+        cudaGetLastError();
+        return HJ_E_INVALID;
+    }
+    hj_ctx *c = new hj_ctx();
+    c->device = device;
+    c->budget = budget;
+    cudaError_t e = cudaSetDevice(device);
+    if (e == cudaSuccess) {
+        if (cuda_stream) {
+            c->stream = (cudaStream_t)cuda_stream;
+        } else {
+            e = cudaStreamCreateWithFlags(&c->stream, cudaStreamNonBlocking);
+            c->own_stream = true;
+        }
+    }
+    if (e == cudaSuccess) {
+        cudaMemPoolProps props;
+        memset(&props, 0, sizeof props);
+        props.allocType = cudaMemAllocationTypePinned;
+        props.location.type = cudaMemLocationTypeDevice;
+        props.location.id = device;
+        e = cudaMemPoolCreate(&c->pool, &props);
+    }
+    if (e == cudaSuccess) {
+        uint64_t keep = ~0ull;  // keep freed blocks for reuse by later joins
+        e = cudaMemPoolSetAttribute(c->pool, cudaMemPoolAttrReleaseThreshold, &keep);
+    }
+    if (e == cudaSuccess) e = cudaMalloc(&c->d_ctr, sizeof(hj_counters));
+    if (e == cudaSuccess) e = cudaMallocHost(&c->h_ctr, sizeof(hj_counters));
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        if (c->d_ctr) cudaFree(c->d_ctr);
+        if (c->pool) cudaMemPoolDestroy(c->pool);
+        if (c->own_stream && c->stream) cudaStreamDestroy(c->stream);
+        delete c;
+        return HJ_E_CUDA;
+    }
+    *out = c;
+    return HJ_OK;
+}
+
+hj_status hj_destroy(hj_ctx *c) {
+    if (!c) return HJ_E_INVALID;
+    cudaSetDevice(c->device);
+    cudaStreamSynchronize(c->stream);
+    for (auto &kv : c->allocs) cudaFreeAsync(kv.first, c->stream);
+    cudaStreamSynchronize(c->stream);
+    c->allocs.clear();
+    for (auto &r : c->recs) {
+        cudaEventDestroy(r.a);
+        cudaEventDestroy(r.b);
+    }
+    for (auto e : c->spare_events) cudaEventDestroy(e);
+    if (c->d_ctr) cudaFree(c->d_ctr);
+    if (c->h_ctr) cudaFreeHost(c->h_ctr);
+    if (c->pool) cudaMemPoolDestroy(c->pool);
+    if (c->own_stream) cudaStreamDestroy(c->stream);
+    delete c;
+    return HJ_OK;
+}
+
+const char *hj_last_error(const hj_ctx *c) { return c ? c->err.c_str() : "null context"; }
+
+hj_status hj_sync(hj_ctx *c) {
+    if (!c) return HJ_E_INVALID;
+    cudaSetDevice(c->device);
+    HJ_CUDA(c, cudaStreamSynchronize(c->stream));
+    return HJ_OK;
+}
+
+hj_status hj_prof_enable(hj_ctx *c, int on) {
+    if (!c) return HJ_E_INVALID;
+    c->prof = on != 0;
+    return HJ_OK;
+}
+
+hj_status hj_prof_reset(hj_ctx *c) {
+    if (!c) return HJ_E_INVALID;
+    cudaStreamSynchronize(c->stream);
+    prof_collect(c);
+    c->prof_acc.clear();
+    return HJ_OK;
+}
+
+hj_status hj_prof_read(hj_ctx *c, hj_prof_entry *ent, int cap, int *n_out) {
+    if (!c || !n_out || (cap > 0 && !ent)) return HJ_E_INVALID;
+    HJ_CUDA(c, cudaStreamSynchronize(c->stream));
+    prof_collect(c);
+    int i = 0;
+    for (auto &kv : c->prof_acc) {
+        if (i < cap) {
+            memset(ent[i].name, 0, sizeof ent[i].name);
+            strncpy(ent[i].name, kv.first.c_str(), sizeof ent[i].name - 1);
+            ent[i].launches = kv.second.first;
+            ent[i].ms = kv.second.second;
+        }
+        i++;
+    }
+    *n_out = i;
+    return HJ_OK;
+}
+
+uint64_t hj_launch_count(const hj_ctx *c) { return c ? c->launches : 0; }
+
+/* Test hook: make the n-th device allocation from now fail with HJ_E_NOMEM
+ * (n < 0 disarms).  Host-side fault injection; no GPU fault is involved. */
+hj_status hj_debug_fail_alloc(hj_ctx *c, int64_t n) {
+    if (!c) return HJ_E_INVALID;
+    c->fail_alloc_after = n;
+    return HJ_OK;
+}
+
+uint64_t hj_debug_bytes_in_use(const hj_ctx *c) { return c ? c->in_use : 0; }
+
+}  // extern "C"

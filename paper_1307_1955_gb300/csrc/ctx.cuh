@@ -1,0 +1,127 @@
+// ctx.cuh -- host-side engine state behind an hj_ctx: the device, the stream, a
+// stream-ordered memory pool with an HBM budget, the last error text, a small
+// device counter block, and optional per-kernel event timing.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <cstdarg>
+#include <cstdio>
+#include <map>
+#include <string>
+#include <unordered_map>
+#include <vector>
+
+#include "../../include/hj.h"
+
+// Counters every join kernel accumulates into (device, zeroed per join).
+struct hj_counters {
+    unsigned long long count;      // pairs found (also the output cursor)
+    unsigned long long c0, c1;     // checksums
+    unsigned long long n_oversize; // partitions left to the global-table fallback
+    unsigned long long status;     // kStatus* bits
+    unsigned long long pad[3];
+};
+
+struct hj_ctx {
+    int device = 0;
+    cudaStream_t stream = nullptr;
+    bool own_stream = false;
+    uint64_t budget = 0;  // 0 = unlimited
+    uint64_t in_use = 0;
+    uint64_t peak = 0;
+    std::unordered_map<void *, uint64_t> allocs;
+    cudaMemPool_t pool = nullptr;
+    std::string err;
+    hj_counters *d_ctr = nullptr;      // device counters
+    hj_counters *h_ctr = nullptr;      // pinned host mirror
+    // profiling
+    bool prof = false;
+    struct Rec {
+        const char *name;
+        cudaEvent_t a, b;
+    };
+    std::vector<Rec> recs;
+    std::vector<cudaEvent_t> spare_events;
+    std::map<std::string, std::pair<uint64_t, double>> prof_acc;
+    uint64_t launches = 0;
+    // test hooks (host-side fault injection)
+    int64_t fail_alloc_after = -1;  // fail the N-th allocation from now (0 = next)
+};
+
+struct hj_table {
+    int width = 4;
+    int agg = 0;          // 1: aggregate table (count modes), 0: pair table
+    void *slots = nullptr;
+    uint64_t cap = 0;
+    void *side = nullptr; // hj::TableSide on the device
+};
+
+namespace hj {
+
+hj_status set_err(hj_ctx *c, hj_status code, const char *fmt, ...);
+hj_status cuda_err(hj_ctx *c, cudaError_t e, const char *what);
+void *dalloc(hj_ctx *c, uint64_t bytes, hj_status *st);
+void dfree(hj_ctx *c, void *p);
+
+// Kernel launch bracketed by profiling events when enabled.
+void prof_begin(hj_ctx *c, const char *name);
+void prof_end(hj_ctx *c);
+hj_status check_launch(hj_ctx *c, const char *name);
+
+// Read the counter block back (synchronises the stream).
+hj_status read_counters(hj_ctx *c);
+hj_status zero_counters(hj_ctx *c);
+
+int num_sms(hj_ctx *c);
+
+// A device buffer from the context's pool, released when the guard goes out of
+// scope unless ownership is taken with release().
+struct DevBuf {
+    hj_ctx *c;
+    void *p = nullptr;
+    explicit DevBuf(hj_ctx *ctx) : c(ctx) {}
+    DevBuf(const DevBuf &) = delete;
+    DevBuf &operator=(const DevBuf &) = delete;
+    ~DevBuf() { reset(); }
+    hj_status alloc(uint64_t bytes) {
+        reset();
+        hj_status st;
+        p = dalloc(c, bytes, &st);
+        return st;
+    }
+    void reset() {
+        if (p) dfree(c, p);
+        p = nullptr;
+    }
+    void *release() {
+        void *q = p;
+        p = nullptr;
+        return q;
+    }
+    template <class T> T *as() const { return (T *)p; }
+};
+
+}  // namespace hj
+
+#define HJ_LAUNCH(ctx, name, kernel, grid, block, smem, ...)                 \
+    do {                                                                     \
+        hj::prof_begin((ctx), (name));                                       \
+        kernel<<<(grid), (block), (smem), (ctx)->stream>>>(__VA_ARGS__);    \
+        hj::prof_end(ctx);                                                   \
+        hj_status _st = hj::check_launch((ctx), (name));                     \
+        if (_st != HJ_OK) return _st;                                        \
+    } while (0)
+
+#define HJ_CUDA(ctx, call)                                                   \
+    do {                                                                     \
+        cudaError_t _e = (call);                                             \
+        if (_e != cudaSuccess) return hj::cuda_err((ctx), _e, #call);       \
+    } while (0)
+
+#define HJ_TRY(expr)                                                         \
+    do {                                                                     \
+        hj_status _s = (expr);                                               \
+        if (_s != HJ_OK) return _s;                                          \
+    } while (0)

@@ -1,0 +1,298 @@
+"""Thin Python binding of libhj (include/hj.h): argument marshalling only.
+
+Every step of the join runs in the library's CUDA kernels; this module turns
+torch tensors into ``hj_rel`` structs (device pointer, length, width), calls the C
+entry point of the same name and turns the result struct back into Python values.
+PyTorch provides the device memory of the inputs and the stream.  There is no CPU
+fallback: if the library cannot be loaded every call raises.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+from dataclasses import dataclass
+
+import torch
+
+HJ_OK, HJ_E_INVALID, HJ_E_NOMEM, HJ_E_OVERFLOW, HJ_E_CUDA, HJ_E_TIMEOUT, HJ_E_UNSUPPORTED, HJ_E_PENDING = range(8)
+HJ_COUNT, HJ_COUNT_CHECKSUM, HJ_MATERIALIZE = 0, 1, 2
+HJ_ALGO_AUTO, HJ_ALGO_SHJ, HJ_ALGO_PHJ = 0, 1, 2
+HJ_FLAG_CHECKSUM = 1
+
+_STATUS = {0: "HJ_OK", 1: "HJ_E_INVALID", 2: "HJ_E_NOMEM", 3: "HJ_E_OVERFLOW", 4: "HJ_E_CUDA",
+           5: "HJ_E_TIMEOUT", 6: "HJ_E_UNSUPPORTED", 7: "HJ_E_PENDING"}
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "_build", "libhj.so")
+
+
+class HJError(RuntimeError):
+    def __init__(self, status: int, msg: str):
+        super().__init__(f"{_STATUS.get(status, status)}: {msg}")
+        self.status = status
+
+
+class hj_rel(ctypes.Structure):
+    _fields_ = [("tuples", ctypes.c_void_p), ("n", ctypes.c_uint64), ("width", ctypes.c_int32),
+                ("reserved", ctypes.c_int32)]
+
+
+class hj_opts(ctypes.Structure):
+    _fields_ = [("algo", ctypes.c_int32), ("mode", ctypes.c_int32), ("radix_bits", ctypes.c_int32),
+                ("passes", ctypes.c_int32), ("out_capacity", ctypes.c_uint64), ("flags", ctypes.c_uint64)]
+
+
+class hj_result(ctypes.Structure):
+    _fields_ = [("count", ctypes.c_uint64), ("checksum", ctypes.c_uint64 * 2), ("pairs", ctypes.c_void_p),
+                ("pairs_cap", ctypes.c_uint64), ("width", ctypes.c_int32), ("algo", ctypes.c_int32),
+                ("radix_bits", ctypes.c_int32), ("passes", ctypes.c_int32)]
+
+
+class hj_prof_entry(ctypes.Structure):
+    _fields_ = [("name", ctypes.c_char * 48), ("launches", ctypes.c_uint64), ("ms", ctypes.c_double)]
+
+
+_lib = None
+
+
+def load_library(path: str = LIB_PATH):
+    """Load libhj.so (build it first with paper_1307_1955_gb300.build.build())."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(path):
+        raise RuntimeError(f"libhj not built: {path} is missing (run __graft_entry__.build())")
+    lib = ctypes.CDLL(path)
+    P, V, I32, U64 = ctypes.POINTER, ctypes.c_void_p, ctypes.c_int32, ctypes.c_uint64
+    sig = {
+        "hj_create": (I32, [P(V), ctypes.c_int, V, U64]),
+        "hj_destroy": (I32, [V]),
+        "hj_last_error": (ctypes.c_char_p, [V]),
+        "hj_build": (I32, [V, P(hj_rel), P(hj_opts), P(V)]),
+        "hj_probe": (I32, [V, V, P(hj_rel), P(hj_opts), P(hj_result)]),
+        "hj_table_free": (I32, [V, V]),
+        "hj_partition": (I32, [V, P(hj_rel), ctypes.c_int, ctypes.c_int, P(hj_rel), P(V)]),
+        "hj_partition_free": (I32, [V, P(hj_rel), V]),
+        "hj_join": (I32, [V, P(hj_rel), P(hj_rel), P(hj_opts), P(hj_result)]),
+        "hj_result_free": (I32, [V, P(hj_result)]),
+        "hj_join_host": (I32, [V, P(hj_rel), P(hj_rel), P(hj_opts), V, U64, P(hj_result)]),
+        "hj_sync": (I32, [V]),
+        "hj_copy": (I32, [V, V, V, U64]),
+        "hj_prof_enable": (I32, [V, ctypes.c_int]),
+        "hj_prof_reset": (I32, [V]),
+        "hj_prof_read": (I32, [V, P(hj_prof_entry), ctypes.c_int, P(ctypes.c_int)]),
+        "hj_launch_count": (U64, [V]),
+        "hj_debug_fail_alloc": (I32, [V, ctypes.c_int64]),
+        "hj_debug_bytes_in_use": (U64, [V]),
+    }
+    for name, (res, args) in sig.items():
+        f = getattr(lib, name)
+        f.restype = res
+        f.argtypes = args
+    _lib = lib
+    return lib
+
+
+def _check(ctx, st: int):
+    if st != HJ_OK:
+        msg = load_library().hj_last_error(ctx.handle if ctx is not None else None)
+        raise HJError(st, msg.decode() if msg else "")
+
+
+def rel_of(t: torch.Tensor) -> hj_rel:
+    """An (n, 2) int32/int64 CUDA tensor (key, rid columns) as an hj_rel."""
+    if t.dim() != 2 or t.shape[1] != 2 or t.dtype not in (torch.int32, torch.int64):
+        raise ValueError("relation must be an (n, 2) int32 or int64 tensor")
+    if not t.is_contiguous():
+        raise ValueError("relation must be contiguous")
+    width = 4 if t.dtype == torch.int32 else 8
+    return hj_rel(t.data_ptr() if t.numel() else None, t.shape[0], width, 0)
+
+
+@dataclass
+class Result:
+    count: int
+    checksum: tuple
+    pairs_ptr: int
+    pairs_cap: int
+    width: int
+    algo: int
+    radix_bits: int
+    passes: int
+    _raw: hj_result
+    _ctx: "Context"
+
+    def pairs_numpy(self):
+        """Copy the pairs to host: (count, 2) uint32/uint64 array of (rid_R, rid_S)."""
+        import numpy as np
+
+        dt = np.uint32 if self.width == 4 else np.uint64
+        out = np.empty((self.count, 2), dt)
+        if self.count and self.pairs_ptr:
+            _check(self._ctx, load_library().hj_copy(self._ctx.handle, out.ctypes.data, self.pairs_ptr,
+                                                     out.nbytes))
+        return out
+
+    def free(self):
+        if self._raw is not None and self._ctx.handle:
+            _check(self._ctx, load_library().hj_result_free(self._ctx.handle, ctypes.byref(self._raw)))
+        self._raw = None
+        self.pairs_ptr = 0
+
+
+def _result(ctx, r: hj_result) -> Result:
+    return Result(int(r.count), (int(r.checksum[0]), int(r.checksum[1])), int(r.pairs or 0), int(r.pairs_cap),
+                  int(r.width), int(r.algo), int(r.radix_bits), int(r.passes), r, ctx)
+
+
+class Context:
+    """An hj_ctx bound to a CUDA device and stream."""
+
+    def __init__(self, device: int = 0, stream: torch.cuda.Stream | None = None, budget: int = 0):
+        lib = load_library()
+        h = ctypes.c_void_p()
+        s = stream.cuda_stream if stream is not None else None
+        st = lib.hj_create(ctypes.byref(h), device, s, budget)
+        if st != HJ_OK:
+            raise HJError(st, "hj_create failed")
+        self.handle = h
+        self.device = device
+
+    def close(self):
+        if self.handle:
+            load_library().hj_destroy(self.handle)
+            self.handle = None
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def _opts(algo=HJ_ALGO_AUTO, mode=HJ_MATERIALIZE, radix_bits=0, passes=0, out_capacity=0, checksum=False):
+    return hj_opts(algo, mode, radix_bits, passes, out_capacity, HJ_FLAG_CHECKSUM if checksum else 0)
+
+
+def hj_create(device: int = 0, stream=None, budget: int = 0) -> Context:
+    return Context(device, stream, budget)
+
+
+def hj_destroy(ctx: Context):
+    ctx.close()
+
+
+class Table:
+    def __init__(self, ctx, handle, width, agg):
+        self.ctx, self.handle, self.width, self.agg = ctx, handle, width, agg
+
+    def free(self):
+        if self.handle:
+            _check(self.ctx, load_library().hj_table_free(self.ctx.handle, self.handle))
+            self.handle = None
+
+
+def hj_build(ctx: Context, R: torch.Tensor, mode: int = HJ_MATERIALIZE) -> Table:
+    r = rel_of(R)
+    h = ctypes.c_void_p()
+    o = _opts(mode=mode)
+    _check(ctx, load_library().hj_build(ctx.handle, ctypes.byref(r), ctypes.byref(o), ctypes.byref(h)))
+    return Table(ctx, h, r.width, mode != HJ_MATERIALIZE)
+
+
+def hj_probe(ctx: Context, table: Table, S: torch.Tensor, mode: int = HJ_MATERIALIZE, out_capacity: int = 0,
+             checksum: bool = False) -> Result:
+    s = rel_of(S)
+    o = _opts(mode=mode, out_capacity=out_capacity, checksum=checksum)
+    res = hj_result()
+    _check(ctx, load_library().hj_probe(ctx.handle, table.handle, ctypes.byref(s), ctypes.byref(o),
+                                        ctypes.byref(res)))
+    return _result(ctx, res)
+
+
+def hj_table_free(ctx: Context, table: Table):
+    table.free()
+
+
+def hj_join(ctx: Context, R: torch.Tensor, S: torch.Tensor, algo: int = HJ_ALGO_AUTO, mode: int = HJ_MATERIALIZE,
+            radix_bits: int = 0, passes: int = 0, out_capacity: int = 0, checksum: bool = False) -> Result:
+    r, s = rel_of(R), rel_of(S)
+    o = _opts(algo, mode, radix_bits, passes, out_capacity, checksum)
+    res = hj_result()
+    _check(ctx, load_library().hj_join(ctx.handle, ctypes.byref(r), ctypes.byref(s), ctypes.byref(o),
+                                       ctypes.byref(res)))
+    return _result(ctx, res)
+
+
+def hj_join_host(ctx: Context, R: torch.Tensor, S: torch.Tensor, pairs_out: torch.Tensor | None = None,
+                 algo: int = HJ_ALGO_AUTO, mode: int = HJ_MATERIALIZE, radix_bits: int = 0, passes: int = 0,
+                 out_capacity: int = 0, checksum: bool = False) -> Result:
+    """hj_join on CPU tensors (pinned for full speed): pairs land in `pairs_out`,
+    an (m, 2) CPU tensor of R's dtype with m >= the pair count."""
+    if R.device.type != "cpu" or S.device.type != "cpu":
+        raise ValueError("hj_join_host takes CPU tensors")
+    r, s = rel_of(R), rel_of(S)
+    o = _opts(algo, mode, radix_bits, passes, out_capacity, checksum)
+    res = hj_result()
+    ptr = pairs_out.data_ptr() if pairs_out is not None and pairs_out.numel() else None
+    cap = pairs_out.shape[0] if pairs_out is not None else 0
+    _check(ctx, load_library().hj_join_host(ctx.handle, ctypes.byref(r), ctypes.byref(s), ctypes.byref(o), ptr,
+                                            cap, ctypes.byref(res)))
+    return _result(ctx, res)
+
+
+def hj_result_free(ctx: Context, res: Result):
+    res.free()
+
+
+def hj_partition(ctx: Context, rel: torch.Tensor, b1: int, b2: int = 0):
+    """Radix-partition a relation; returns (tuples as numpy (n, 2) array, offsets numpy)."""
+    import numpy as np
+
+    r = rel_of(rel)
+    out = hj_rel()
+    off = ctypes.c_void_p()
+    lib = load_library()
+    _check(ctx, lib.hj_partition(ctx.handle, ctypes.byref(r), b1, b2, ctypes.byref(out), ctypes.byref(off)))
+    try:
+        dt = np.uint32 if r.width == 4 else np.uint64
+        tup = np.empty((r.n, 2), dt)
+        offs = np.empty((1 << (b1 + b2)) + 1, np.uint64)
+        if r.n:
+            _check(ctx, lib.hj_copy(ctx.handle, tup.ctypes.data, out.tuples, tup.nbytes))
+        _check(ctx, lib.hj_copy(ctx.handle, offs.ctypes.data, off, offs.nbytes))
+    finally:
+        lib.hj_partition_free(ctx.handle, ctypes.byref(out), off)
+    return tup, offs
+
+
+def hj_sync(ctx: Context):
+    _check(ctx, load_library().hj_sync(ctx.handle))
+
+
+def prof_enable(ctx: Context, on: bool = True):
+    _check(ctx, load_library().hj_prof_enable(ctx.handle, 1 if on else 0))
+
+
+def prof_reset(ctx: Context):
+    _check(ctx, load_library().hj_prof_reset(ctx.handle))
+
+
+def prof_read(ctx: Context) -> dict:
+    """{kernel name: (launches, total device ms)} since the last reset."""
+    lib = load_library()
+    n = ctypes.c_int()
+    _check(ctx, lib.hj_prof_read(ctx.handle, None, 0, ctypes.byref(n)))
+    arr = (hj_prof_entry * max(n.value, 1))()
+    _check(ctx, lib.hj_prof_read(ctx.handle, arr, n.value, ctypes.byref(n)))
+    return {arr[i].name.decode(): (int(arr[i].launches), float(arr[i].ms)) for i in range(n.value)}
+
+
+def launch_count(ctx: Context) -> int:
+    return int(load_library().hj_launch_count(ctx.handle))

@@ -1,0 +1,62 @@
+"""The C-ABI library builds for sm_103a, loads, and exports every function that
+include/hj.h declares.  No kernel runs here (CPU only)."""
+import ctypes
+import os
+import re
+
+import pytest
+
+from paper_1307_1955_gb300 import build as B
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def _declared():
+    names = set()
+    for f in os.listdir(os.path.join(ROOT, "include")):
+        if f.endswith(".h"):
+            txt = open(os.path.join(ROOT, "include", f)).read()
+            txt = re.sub(r"/\*.*?\*/", "", txt, flags=re.S)
+            names |= set(re.findall(r"\b(hj_[a-z0-9_]+)\s*\(", txt))
+    return names
+
+
+@pytest.fixture(scope="module")
+def lib():
+    return ctypes.CDLL(B.build())
+
+
+def test_header_declares_the_boundary():
+    d = _declared()
+    for name in ("hj_create", "hj_destroy", "hj_build", "hj_probe", "hj_partition", "hj_join", "hj_result_free",
+                 "hj_sync", "hj_last_error"):
+        assert name in d
+
+
+def test_library_exports_every_declared_symbol(lib):
+    missing = [n for n in sorted(_declared()) if not hasattr(lib, n)]
+    assert not missing, missing
+
+
+def test_null_context_is_rejected_without_a_gpu(lib):
+    lib.hj_join.restype = ctypes.c_int32
+    assert lib.hj_join(None, None, None, None, None) == 1  # HJ_E_INVALID
+    lib.hj_last_error.restype = ctypes.c_char_p
+    assert lib.hj_last_error(None) == b"null context"
+
+
+def test_binding_names_match_the_abi():
+    from paper_1307_1955_gb300 import hj
+
+    for name in ("hj_create", "hj_destroy", "hj_build", "hj_probe", "hj_table_free", "hj_partition", "hj_join",
+                 "hj_result_free", "hj_sync"):
+        assert callable(getattr(hj, name))
+
+
+def test_product_path_does_not_import_the_oracle():
+    pkg = os.path.join(ROOT, "paper_1307_1955_gb300")
+    for dirpath, _, files in os.walk(pkg):
+        for f in files:
+            if f.endswith((".py", ".cu", ".cuh", ".h", ".cpp")):
+                txt = open(os.path.join(dirpath, f)).read()
+                assert "import oracle" not in txt and "from oracle" not in txt and "hj_oracle" not in txt, f
