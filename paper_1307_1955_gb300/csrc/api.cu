@@ -5,6 +5,7 @@
 #include <vector>
 
 #include "common.cuh"
+#include "emit.cuh"
 #include "engine.cuh"
 
 using namespace hj;
@@ -54,7 +55,7 @@ uint64_t slot_bytes(int width, bool agg) {
 
 // Plan choice (the cost model's GPU-only case, Sec. 4 Eq. 1-2 with every step on
 // the GPU): SHJ while its table is small enough to stay in L2; otherwise PHJ with
-// enough radix bits that a partition of R holds about 4096 tuples (a shared-memory
+// enough radix bits that a partition of R holds about 8192 tuples (a shared-memory
 // table), in one pass up to 12 bits and two passes beyond.
 void plan(const hj_rel *R, const hj_opts &o, int *algo, int *bits, int *passes) {
     uint64_t nR = R->n;
@@ -68,7 +69,7 @@ void plan(const hj_rel *R, const hj_opts &o, int *algo, int *bits, int *passes) 
     int b = o.radix_bits;
     if (b <= 0) {
         b = 1;
-        while (b < 24 && (nR >> b) > 4096) b++;
+        while (b < 24 && (nR >> b) > 8192) b++;
     }
     *bits = b;
     int p = o.passes;
@@ -76,37 +77,49 @@ void plan(const hj_rel *R, const hj_opts &o, int *algo, int *bits, int *passes) 
     *passes = p;
 }
 
-hj_status upload_u64(hj_ctx *c, const std::vector<uint64_t> &v, DevBuf &out) {
-    HJ_TRY(out.alloc(v.size() * 8));
-    HJ_CUDA(c, cudaMemcpyAsync(out.p, v.data(), v.size() * 8, cudaMemcpyHostToDevice, c->stream));
-    HJ_CUDA(c, cudaStreamSynchronize(c->stream));  // v is a host temporary
+__global__ void set_pair_kernel(uint64_t *p, uint64_t a, uint64_t b) {
+    p[0] = a;
+    p[1] = b;
+}
+
+// Device array {a, b}, written by a one-thread kernel so that the host need not wait.
+hj_status device_pair(hj_ctx *c, uint64_t a, uint64_t b, DevBuf &out) {
+    HJ_TRY(out.alloc(16));
+    HJ_LAUNCH(c, "set_pair", set_pair_kernel, 1, 1, 0, out.as<uint64_t>(), a, b);
     return HJ_OK;
 }
 
 // Partition a whole relation in one or two passes (Alg. 2); on success `tuples`
-// (padded by 64 bytes) and `offsets` (2^(b1+b2) + 1 entries) hold the result.
-hj_status partition_rel(hj_ctx *c, const hj_rel *in, int b1, int b2, DevBuf &tuples, DevBuf &offsets) {
+// and `offsets` (2^(b1+b2) + 1 entries) hold the result and *rows the number of
+// rows allocated for the tuples (more than in->n when padded).
+hj_status partition_rel(hj_ctx *c, const hj_rel *in, int b1, int b2, int pad, DevBuf &tuples, DevBuf &offsets,
+                        uint64_t *rows) {
     const uint64_t n = in->n, tb = tuple_bytes(in->width);
     DevBuf seg(c), A(c), off1(c);
-    HJ_TRY(upload_u64(c, {0ull, n}, seg));
-    HJ_TRY(A.alloc(n * tb + 64));
+    HJ_TRY(device_pair(c, 0ull, n, seg));
+    const uint64_t rows1 = partition_out_rows(c, in->width, n, 1, b1, pad);
+    HJ_TRY(A.alloc(rows1 * tb + 64));
     HJ_TRY(off1.alloc(((1ull << b1) + 1) * 8));
-    HJ_TRY(partition_pass(c, in->width, in->tuples, n, seg.as<uint64_t>(), 1, 0, b1, A.p, off1.as<uint64_t>()));
+    HJ_TRY(partition_pass(c, in->width, in->tuples, n, seg.as<uint64_t>(), 1, 0, b1, A.p, off1.as<uint64_t>(), pad));
     if (b2 == 0) {
         tuples.reset();
         offsets.reset();
         tuples.p = A.release();
         offsets.p = off1.release();
+        *rows = rows1;
         return HJ_OK;
     }
     DevBuf B(c), off2(c);
-    HJ_TRY(B.alloc(n * tb + 64));
+    const uint64_t rows2 = partition_out_rows(c, in->width, rows1, 1ull << b1, b2, pad);
+    HJ_TRY(B.alloc(rows2 * tb + 64));
     HJ_TRY(off2.alloc(((1ull << (b1 + b2)) + 1) * 8));
-    HJ_TRY(partition_pass(c, in->width, A.p, n, off1.as<uint64_t>(), 1ull << b1, b1, b2, B.p, off2.as<uint64_t>()));
+    HJ_TRY(partition_pass(c, in->width, A.p, rows1, off1.as<uint64_t>(), 1ull << b1, b1, b2, B.p,
+                          off2.as<uint64_t>(), pad));
     tuples.reset();
     offsets.reset();
     tuples.p = B.release();
     offsets.p = off2.release();
+    *rows = rows2;
     return HJ_OK;
 }
 
@@ -126,41 +139,68 @@ struct TableGuard {
     ~TableGuard() { table_destroy(c, t); }
 };
 
+// Initial pair capacity: the caller's hint, else |S| (every probe tuple matching
+// once), plus one chunk per emitting warp for the holes of partly filled chunks.
+uint64_t first_capacity(const hj_opts &o, uint64_t nS, uint64_t warps) {
+    uint64_t want = o.out_capacity ? o.out_capacity : nS;
+    return want + warps * kChunkPairs;
+}
+
 // ----------------------------------------------------------------------- SHJ
+hj_status probe_into(hj_ctx *c, const hj_table *t, const hj_rel *S, const hj_opts &o, hj_result *res) {
+    const bool mat = o.mode == HJ_MATERIALIZE, chk = wants_checksum(o);
+    const uint64_t warps = table_probe_warps(c, S->n);
+    PairSink sink(c, t->width);
+    uint64_t cap = mat ? first_capacity(o, S->n, warps) : 0;
+    for (int attempt = 0; attempt < 2; ++attempt) {
+        RecArea ra{nullptr, nullptr, 0};
+        if (mat) {
+            HJ_TRY(sink.reset(cap));
+            HJ_TRY(sink.new_area(warps, &ra));
+        }
+        HJ_TRY(zero_counters(c));
+        HJ_TRY(table_probe(c, t, S->tuples, 0, S->n, S->n, sink.pairs.p, sink.pcap, chk, ra, PartFilter{0, 0, 0, 0}));
+        HJ_TRY(read_counters(c));
+        if (c->h_ctr->status & 8ull) return set_err(c, HJ_E_CUDA, "output record area overflow");
+        if (!mat) break;
+        if (c->h_ctr->cursor <= sink.pcap) {
+            HJ_TRY(sink.finalize(c->h_ctr->count, c->h_ctr->cursor));
+            break;
+        }
+        // more pairs than the capacity: run the probe again at the exact size
+        cap = c->h_ctr->cursor + warps * kChunkPairs;
+        if (attempt == 1) return set_err(c, HJ_E_CUDA, "pair capacity still too small after resizing");
+    }
+    fill_result(c, res, t->width, HJ_ALGO_SHJ, 0, 0);
+    res->pairs = mat ? sink.pairs.release() : nullptr;
+    res->pairs_cap = mat ? sink.pcap : 0;
+    return HJ_OK;
+}
+
 hj_status join_shj(hj_ctx *c, const hj_rel *R, const hj_rel *S, const hj_opts &o, hj_result *res) {
-    const bool agg = is_agg(o.mode), mat = o.mode == HJ_MATERIALIZE, chk = wants_checksum(o);
     TableGuard tg{c};
     HJ_TRY(zero_counters(c));
-    HJ_TRY(table_create(c, R->width, agg, R->n, &tg.t));
-    HJ_TRY(table_build(c, tg.t, R->tuples, 0, R->n, R->n));
-    uint64_t cap = mat ? (o.out_capacity ? o.out_capacity : S->n) : 0;
-    DevBuf pairs(c);
-    if (mat) HJ_TRY(pairs.alloc(std::max<uint64_t>(cap, 1) * tuple_bytes(R->width)));
-    for (int attempt = 0; attempt < 2; ++attempt) {
-        HJ_TRY(table_probe(c, tg.t, S->tuples, 0, S->n, S->n, pairs.p, cap, chk));
-        HJ_TRY(read_counters(c));
-        if (c->h_ctr->status & kStatusTableFull) return set_err(c, HJ_E_CUDA, "hash table unexpectedly full");
-        if (!mat || c->h_ctr->count <= cap) break;
-        // more pairs than the capacity: re-run the probe at the exact size
-        cap = c->h_ctr->count;
-        HJ_TRY(pairs.alloc(cap * tuple_bytes(R->width)));
-        HJ_TRY(zero_counters(c));
-    }
-    fill_result(c, res, R->width, HJ_ALGO_SHJ, 0, 0);
-    res->pairs = mat ? pairs.release() : nullptr;
-    res->pairs_cap = mat ? cap : 0;
-    return HJ_OK;
+    HJ_TRY(table_create(c, R->width, is_agg(o.mode), R->n, &tg.t));
+    HJ_TRY(table_build(c, tg.t, R->tuples, 0, R->n, R->n, PartFilter{0, 0, 0, 0}));
+    HJ_TRY(read_counters(c));
+    if (c->h_ctr->status & kStatusTableFull) return set_err(c, HJ_E_CUDA, "hash table unexpectedly full");
+    return probe_into(c, tg.t, S, o, res);
 }
 
 // ----------------------------------------------------------------------- PHJ
 hj_status run_partition_join(hj_ctx *c, const hj_rel *R, const hj_rel *S, const hj_opts &o, const void *Rp,
-                             const uint64_t *roff, const void *Sp, const uint64_t *soff, uint64_t NP, void *pairs,
-                             uint64_t cap, uint32_t *oversize) {
-    const bool agg = is_agg(o.mode), chk = wants_checksum(o);
+                             const uint64_t *roff, uint64_t r_rows, const void *Sp, const uint64_t *soff,
+                             uint64_t s_rows, uint64_t NP, int b1, int b2, PairSink *sink, uint32_t *oversize) {
+    const bool agg = is_agg(o.mode), chk = wants_checksum(o), mat = o.mode == HJ_MATERIALIZE;
     const int W = R->width;
+    RecArea ra{nullptr, nullptr, 0};
+    if (mat) HJ_TRY(sink->new_area(partition_join_warps(c), &ra));
     HJ_TRY(zero_counters(c));
     uint64_t expect = NP ? (R->n + NP - 1) / NP : 0;
-    HJ_TRY(partition_join(c, W, agg, Rp, roff, R->n, Sp, soff, S->n, NP, expect, pairs, cap, chk, oversize));
+    void *pairs = mat ? sink->pairs.p : nullptr;
+    uint64_t pcap = mat ? sink->pcap : 0;
+    HJ_TRY(partition_join(c, W, agg, Rp, roff, r_rows, Sp, soff, s_rows, NP, expect, pairs, pcap, chk, oversize, ra,
+                          b1, b2, 1));
     HJ_TRY(read_counters(c));
     uint64_t nov = c->h_ctr->n_oversize;
     if (nov == 0) return HJ_OK;
@@ -173,9 +213,12 @@ hj_status run_partition_join(hj_ctx *c, const hj_rel *R, const hj_rel *S, const 
     HJ_CUDA(c, cudaStreamSynchronize(c->stream));
     for (uint32_t p : list) {
         TableGuard tg{c};
+        const PartFilter pf{p, b1, b2, 1};
         HJ_TRY(table_create(c, W, agg, hr[p + 1] - hr[p], &tg.t));
-        HJ_TRY(table_build(c, tg.t, Rp, hr[p], hr[p + 1], R->n));
-        HJ_TRY(table_probe(c, tg.t, Sp, hs[p], hs[p + 1], S->n, pairs, cap, chk));
+        HJ_TRY(table_build(c, tg.t, Rp, hr[p], hr[p + 1], r_rows, pf));
+        RecArea ra2{nullptr, nullptr, 0};
+        if (mat) HJ_TRY(sink->new_area(table_probe_warps(c, hs[p + 1] - hs[p]), &ra2));
+        HJ_TRY(table_probe(c, tg.t, Sp, hs[p], hs[p + 1], s_rows, pairs, pcap, chk, ra2, pf));
     }
     HJ_TRY(read_counters(c));
     if (c->h_ctr->status & kStatusTableFull) return set_err(c, HJ_E_CUDA, "hash table unexpectedly full");
@@ -189,22 +232,32 @@ hj_status join_phj(hj_ctx *c, const hj_rel *R, const hj_rel *S, const hj_opts &o
     if (b1 < 1 || b1 > 12 || b2 < 0 || b2 > 12)
         return set_err(c, HJ_E_INVALID, "radix bits %d in %d passes: each pass takes 1..12 bits", bits, passes);
     const uint64_t NP = 1ull << bits;
-    DevBuf Rp(c), Sp(c), roff(c), soff(c), oversize(c), pairs(c);
-    HJ_TRY(partition_rel(c, R, b1, b2, Rp, roff));
-    HJ_TRY(partition_rel(c, S, b1, b2, Sp, soff));
+    DevBuf Rp(c), Sp(c), roff(c), soff(c), oversize(c);
+    PairSink sink(c, R->width);
+    uint64_t r_rows = 0, s_rows = 0;
+    HJ_TRY(partition_rel(c, R, b1, b2, 1, Rp, roff, &r_rows));
+    HJ_TRY(partition_rel(c, S, b1, b2, 1, Sp, soff, &s_rows));
     HJ_TRY(oversize.alloc(NP * 4));
-    uint64_t cap = mat ? (o.out_capacity ? o.out_capacity : S->n) : 0;
-    if (mat) HJ_TRY(pairs.alloc(std::max<uint64_t>(cap, 1) * tuple_bytes(R->width)));
+    const uint64_t warps = partition_join_warps(c);
+    uint64_t cap = mat ? first_capacity(o, S->n, warps) : 0;
     for (int attempt = 0; attempt < 2; ++attempt) {
-        HJ_TRY(run_partition_join(c, R, S, o, Rp.p, roff.as<uint64_t>(), Sp.p, soff.as<uint64_t>(), NP, pairs.p,
-                                  cap, oversize.as<uint32_t>()));
-        if (!mat || c->h_ctr->count <= cap) break;
-        cap = c->h_ctr->count;
-        HJ_TRY(pairs.alloc(cap * tuple_bytes(R->width)));
+        if (mat) HJ_TRY(sink.reset(cap));
+        HJ_TRY(run_partition_join(c, R, S, o, Rp.p, roff.as<uint64_t>(), r_rows, Sp.p, soff.as<uint64_t>(), s_rows, NP,
+                                  b1, b2, &sink, oversize.as<uint32_t>()));
+        if (c->h_ctr->status & 8ull) return set_err(c, HJ_E_CUDA, "output record area overflow");
+        if (!mat) break;
+        if (c->h_ctr->cursor <= sink.pcap) {
+            HJ_TRY(sink.finalize(c->h_ctr->count, c->h_ctr->cursor));
+            break;
+        }
+        uint64_t extra = 0;
+        for (auto cp : sink.caps) extra += cp;
+        cap = c->h_ctr->cursor + extra * kChunkPairs;
+        if (attempt == 1) return set_err(c, HJ_E_CUDA, "pair capacity still too small after resizing");
     }
     fill_result(c, res, R->width, HJ_ALGO_PHJ, bits, passes);
-    res->pairs = mat ? pairs.release() : nullptr;
-    res->pairs_cap = mat ? cap : 0;
+    res->pairs = mat ? sink.pairs.release() : nullptr;
+    res->pairs_cap = mat ? sink.pcap : 0;
     return HJ_OK;
 }
 
@@ -222,7 +275,7 @@ hj_status hj_build(hj_ctx *c, const hj_rel *R, const hj_opts *opts, hj_table **o
     TableGuard tg{c};
     HJ_TRY(zero_counters(c));
     HJ_TRY(table_create(c, R->width, is_agg(o.mode), R->n, &tg.t));
-    HJ_TRY(table_build(c, tg.t, R->tuples, 0, R->n, R->n));
+    HJ_TRY(table_build(c, tg.t, R->tuples, 0, R->n, R->n, PartFilter{0, 0, 0, 0}));
     HJ_TRY(read_counters(c));
     if (c->h_ctr->status & kStatusTableFull) return set_err(c, HJ_E_CUDA, "hash table unexpectedly full");
     *out = tg.t;
@@ -239,22 +292,7 @@ hj_status hj_probe(hj_ctx *c, const hj_table *t, const hj_rel *S, const hj_opts 
     if (is_agg(o.mode) != (t->agg != 0))
         return set_err(c, HJ_E_INVALID, "probe mode %d does not match the table's build mode", o.mode);
     *res = hj_result{};
-    const bool mat = o.mode == HJ_MATERIALIZE, chk = wants_checksum(o);
-    uint64_t cap = mat ? (o.out_capacity ? o.out_capacity : S->n) : 0;
-    DevBuf pairs(c);
-    if (mat) HJ_TRY(pairs.alloc(std::max<uint64_t>(cap, 1) * tuple_bytes(t->width)));
-    for (int attempt = 0; attempt < 2; ++attempt) {
-        HJ_TRY(zero_counters(c));
-        HJ_TRY(table_probe(c, t, S->tuples, 0, S->n, S->n, pairs.p, cap, chk));
-        HJ_TRY(read_counters(c));
-        if (!mat || c->h_ctr->count <= cap) break;
-        cap = c->h_ctr->count;
-        HJ_TRY(pairs.alloc(cap * tuple_bytes(t->width)));
-    }
-    fill_result(c, res, t->width, HJ_ALGO_SHJ, 0, 0);
-    res->pairs = mat ? pairs.release() : nullptr;
-    res->pairs_cap = mat ? cap : 0;
-    return HJ_OK;
+    return probe_into(c, t, S, o, res);
 }
 
 hj_status hj_table_free(hj_ctx *c, hj_table *t) {
@@ -271,7 +309,8 @@ hj_status hj_partition(hj_ctx *c, const hj_rel *in, int b1, int b2, hj_rel *out_
     if (b1 < 1 || b1 > 12 || b2 < 0 || b2 > 12)
         return set_err(c, HJ_E_INVALID, "bits (%d, %d): pass one takes 1..12 bits, pass two 0..12", b1, b2);
     DevBuf tup(c), off(c);
-    HJ_TRY(partition_rel(c, in, b1, b2, tup, off));
+    uint64_t rows = 0;
+    HJ_TRY(partition_rel(c, in, b1, b2, 0, tup, off, &rows));
     HJ_CUDA(c, cudaStreamSynchronize(c->stream));
     out_tuples->tuples = tup.release();
     out_tuples->n = in->n;

@@ -96,6 +96,21 @@ __device__ __forceinline__ uint32_t digit_of(uint64_t h, int shift, int bits) {
     return (uint32_t)(h >> shift) & ((1u << bits) - 1u);
 }
 
+// Membership of a hash in partition p of a PHJ with pass bits (b1, b2): the
+// partition index is ((h mod 2^b1) << b2) | ((h >> b1) mod 2^b2) (Alg. 2's nested
+// passes).  Inside the join, partitions may hold padding tuples whose key hashes
+// elsewhere; build and probe drop every tuple this test rejects.
+struct PartFilter {
+    uint32_t p;
+    int b1, b2, on;
+    __device__ __forceinline__ bool keep(uint64_t h) const {
+        if (!on) return true;
+        const uint32_t d1 = (uint32_t)h & ((1u << b1) - 1u);
+        const uint32_t d2 = b2 ? ((uint32_t)(h >> b1) & ((1u << b2) - 1u)) : 0u;
+        return ((d1 << b2) | d2) == p;
+    }
+};
+
 // Table bucket in [0, cap): the high 32 bits of the hash scaled to cap
 // (multiply-shift range reduction), independent of the low radix bits.
 template <int W> __device__ __forceinline__ uint64_t bucket_of(uint64_t h, uint64_t cap);
@@ -220,14 +235,15 @@ __device__ __forceinline__ bool pair_insert(typename PairSlot<W>::S *slots, uint
     return false;
 }
 
-// Visit every build rid whose key equals k: f(rid).  Terminates at the first empty
-// slot (a table always keeps at least one) and at most after cap slots.
+// Visit every build rid whose key equals k: f(rid).  The key's run starts at its
+// home slot bucket_of(h, cap / group) * group and ends at the first empty slot (a
+// table always keeps at least one), after at most cap slots.
 template <int W, class F>
 __device__ __forceinline__ void pair_lookup(const typename PairSlot<W>::S *slots, uint64_t cap,
                                             unsigned long long n_allones, typename Tup<W>::U k, uint64_t h,
-                                            F &&f) {
+                                            uint32_t group, F &&f) {
     using PS = PairSlot<W>;
-    uint64_t b = bucket_of<W>(h, cap);
+    uint64_t b = bucket_of<W>(h, cap / group) * group;
     for (uint64_t it = 0; it < cap; ++it) {
         typename PS::S s = slots[b];
         if (PS::is_empty(s)) break;

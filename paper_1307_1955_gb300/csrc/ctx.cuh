@@ -17,11 +17,13 @@
 
 // Counters every join kernel accumulates into (device, zeroed per join).
 struct hj_counters {
-    unsigned long long count;      // pairs found (also the output cursor)
+    unsigned long long count;      // pairs found
     unsigned long long c0, c1;     // checksums
     unsigned long long n_oversize; // partitions left to the global-table fallback
     unsigned long long status;     // kStatus* bits
-    unsigned long long pad[3];
+    unsigned long long cursor;     // output slots handed out in whole chunks (pairs + holes)
+    unsigned long long work;       // next partition for the persistent join kernel
+    unsigned long long pad;
 };
 
 struct hj_ctx {

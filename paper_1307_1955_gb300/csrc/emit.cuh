@@ -1,0 +1,102 @@
+// emit.cuh -- dense output of join pairs with few global atomics.
+//
+// GPU form of the block allocator of Sec. 3.3 (a work group takes a block from a
+// global pointer, its threads sub-allocate from the block): here every WARP takes
+// a chunk of kChunkPairs output slots from the global cursor with one atomicAdd
+// and appends the pairs its lanes find with ballot/popc offsets -- no block-wide
+// barrier, one global atomic per kChunkPairs pairs.  A warp's last chunk is
+// usually partly filled; the warp records (base, used) so that the host can plan a
+// small move of pairs from the tail into those holes, after which pairs[0, count)
+// is dense.
+#pragma once
+
+#include "common.cuh"
+#include "ctx.cuh"
+
+namespace hj {
+
+constexpr unsigned kChunkPairs = 1024;
+
+struct ChunkRec {
+    unsigned long long base, used;
+};
+
+// Where the warps of one launch record their partly filled chunks.
+struct RecArea {
+    unsigned long long *n;  // number of records written
+    ChunkRec *rec;
+    unsigned long long cap;
+};
+
+template <int W> struct PairOut;
+template <> struct PairOut<4> {
+    static __device__ __forceinline__ void put(void *p, uint64_t i, uint32_t a, uint32_t b) {
+        ((uint2 *)p)[i] = make_uint2(a, b);
+    }
+};
+template <> struct PairOut<8> {
+    static __device__ __forceinline__ void put(void *p, uint64_t i, uint64_t a, uint64_t b) {
+        ((ulonglong2 *)p)[i] = make_ulonglong2(a, b);
+    }
+};
+
+// Output context of a launch.
+struct OutCtx {
+    void *pairs;
+    uint64_t pcap;
+    hj_counters *ctr;
+};
+
+// Warp-uniform state of a warp's current chunk.
+struct OutState {
+    unsigned long long base = 0;
+    unsigned used = kChunkPairs;  // no chunk open yet
+    bool claimed = false;
+    unsigned long long pairs = 0;
+};
+
+// Append one pair per lane whose `has` is set.  All 32 lanes must call.
+template <int W>
+__device__ __forceinline__ void warp_append(OutState &st, const OutCtx &oc, bool has, typename Tup<W>::U a,
+                                            typename Tup<W>::U b) {
+    const unsigned mask = __ballot_sync(0xffffffffu, has);
+    if (!mask) return;
+    const unsigned lane = threadIdx.x & 31;
+    const unsigned k = __popc(mask);
+    const unsigned rank = __popc(mask & ((1u << lane) - 1u));
+    const unsigned room = kChunkPairs - st.used;
+    unsigned long long nb = 0;
+    if (k > room) {
+        if (lane == 0) nb = atomicAdd(&oc.ctr->cursor, (unsigned long long)kChunkPairs);
+        nb = __shfl_sync(0xffffffffu, nb, 0);
+    }
+    if (has) {
+        unsigned long long pos = rank < room ? st.base + st.used + rank : nb + (rank - room);
+        if (pos < oc.pcap) PairOut<W>::put(oc.pairs, pos, a, b);
+    }
+    if (k > room) {
+        st.base = nb;
+        st.used = k - room;
+        st.claimed = true;
+    } else {
+        st.used += k;
+    }
+    st.pairs += k;
+}
+
+// Record the warp's partly filled chunk and add its pair count.  All lanes call.
+__device__ __forceinline__ void warp_finish(const OutState &st, const OutCtx &oc, const RecArea &ra) {
+    if ((threadIdx.x & 31) != 0) return;
+    if (st.claimed && st.used < kChunkPairs) {
+        unsigned long long i = atomicAdd(ra.n, 1ull);
+        if (i < ra.cap) {
+            ra.rec[i].base = st.base;
+            ra.rec[i].used = st.used;
+        } else {
+            atomicOr(&oc.ctr->status, 8ull);  // record area too small
+        }
+    }
+    if (st.pairs) atomicAdd(&oc.ctr->count, st.pairs);
+}
+
+}  // namespace hj

@@ -1,25 +1,26 @@
 // join.cu -- build and probe kernels (Alg. 1 steps b1-b4 and p1-p4).
 //
-//   * table_* : the simple hash join's table in global memory (SHJ), shared by all
-//     CTAs (Sec. 3.3: one shared table rather than one per processor).
-//   * partition_join : Alg. 2's per-partition SHJ with the table in shared memory,
-//     one CTA per partition pair.
+//   * table_* : the simple hash join's table in global memory (SHJ), one table
+//     shared by all CTAs (Sec. 3.3 prefers one shared table to one per processor).
+//   * partition_join : Alg. 2's "apply SHJ on each partition pair" with the table
+//     in shared memory; persistent CTAs take partition pairs from a work counter.
 //
-// Output placement for the pairs (Sec. 3.3's block allocator, GPU form): a CTA
-// probes a tile of S, counts the matches of each thread, scans the counts across
-// the block, reserves the tile's whole range with ONE atomicAdd on the global
-// cursor, and threads write their pairs densely into it.  The common case of one
-// match per tuple keeps the build rid from the first walk; only tuples with
-// several matches walk their bucket run a second time.
+// Probing is warp-level: each warp streams its share of S in groups of 16-byte
+// vectors (the next group is loaded before the current one is probed), looks
+// every tuple up, and appends pairs through emit.cuh (no block barrier in the
+// probe loop).  A probe key with several build matches (duplicate R keys) is
+// walked by the whole warp, 32 consecutive slots at a time -- the GPU answer to
+// the divergence that skew causes in steps b3/p3 (Sec. 3.3, workload divergence).
 #include "common.cuh"
+#include "emit.cuh"
 #include "engine.cuh"
 
 namespace hj {
 
 // ------------------------------------------------------------------ tuple loads
-// Tuples of a range are visited by 16-byte vectors: vector v holds tuples
-// v*PV .. v*PV+PV-1.  The last vector of a 4-byte relation with an odd number of
-// tuples is read with one 8-byte load so no read passes the array end.
+// Vector v of a tuple array holds tuples v*PV .. v*PV+PV-1.  The last vector of a
+// 4-byte relation with an odd number of tuples is read with one 8-byte load so
+// that no read passes the array end.
 template <int W>
 __device__ __forceinline__ void load_vec(const void *base, uint64_t v, uint64_t n_total, typename Tup<W>::U *k,
                                          typename Tup<W>::U *r) {
@@ -44,29 +45,69 @@ __device__ __forceinline__ void load_vec(const void *base, uint64_t v, uint64_t 
     }
 }
 
-template <int W> struct PairOut;
-template <> struct PairOut<4> {
-    static __device__ __forceinline__ void put(void *p, uint64_t i, uint32_t a, uint32_t b) {
-        ((uint2 *)p)[i] = make_uint2(a, b);
-    }
-};
-template <> struct PairOut<8> {
-    static __device__ __forceinline__ void put(void *p, uint64_t i, uint64_t a, uint64_t b) {
-        ((ulonglong2 *)p)[i] = make_ulonglong2(a, b);
+// A warp's group: U vectors per lane, lane-interleaved (vector g + u*32 + lane).
+template <int W, int U> struct Group {
+    static constexpr int PV = Tup<W>::kPerVec;
+    static constexpr int IT = U * PV;
+    typename Tup<W>::U k[IT], r[IT];
+    bool valid[IT];
+    __device__ __forceinline__ void load(const void *S, uint64_t g, uint64_t lo, uint64_t hi, uint64_t vb,
+                                         uint64_t n_total) {
+        const unsigned lane = threadIdx.x & 31;
+#pragma unroll
+        for (int u = 0; u < U; ++u) {
+            uint64_t v = g + (uint64_t)u * 32 + lane;
+            typename Tup<W>::U kk[2] = {0, 0}, rr[2] = {0, 0};
+            if (v < vb) load_vec<W>(S, v, n_total, kk, rr);
+#pragma unroll
+            for (int e = 0; e < PV; ++e) {
+                uint64_t t = v * PV + e;
+                k[u * PV + e] = kk[e];
+                r[u * PV + e] = rr[e];
+                valid[u * PV + e] = v < vb && t >= lo && t < hi;
+            }
+        }
     }
 };
 
 // ----------------------------------------------------------------- table views
-template <int W> struct PairView {
+// Pair table: slots in shared or global memory (generic addressing).
+// A key's probe run starts at its home slot, bucket_of(h, cap / group) * group:
+// group 1 for the global table, a bucket of `group` slots read together for the
+// shared-memory tables.  Runs continue linearly (with wrap) to the first empty slot.
+template <int W> struct PairTab {
     using U = typename Tup<W>::U;
-    const typename PairSlot<W>::S *slots;
+    using PS = PairSlot<W>;
+    const typename PS::S *slots;
     uint64_t cap;
     unsigned long long n_allones;
+    uint32_t group;
+
     template <class F> __device__ __forceinline__ void lookup(U k, uint64_t h, F &&f) const {
-        pair_lookup<W>(slots, cap, n_allones, k, h, f);
+        pair_lookup<W>(slots, cap, n_allones, k, h, group, f);
+    }
+    // The whole warp emits every build match of probe key kk (probe rid ss).
+    __device__ __forceinline__ void coop_emit(U kk, U ss, OutState &st, const OutCtx &oc) const {
+        const unsigned lane = threadIdx.x & 31;
+        const uint64_t b = bucket_of<W>(key_hash<W>(kk), cap / group) * group;
+        for (uint64_t off = 0; off < cap; off += 32) {
+            const bool inr = off + lane < cap;
+            uint64_t idx = b + off + lane;
+            if (idx >= cap) idx -= cap;
+            typename PS::S s = inr ? slots[idx] : PS::empty();
+            const unsigned emp = __ballot_sync(0xffffffffu, !inr || PS::is_empty(s));
+            const unsigned before = emp ? ((emp & (0u - emp)) - 1u) : 0xffffffffu;
+            const bool m = ((before >> lane) & 1u) && PS::key(s) == kk;
+            warp_append<W>(st, oc, m, PS::rid(s), ss);
+            if (emp) break;
+        }
+        if (kk == Tup<W>::kAllOnes)
+            for (unsigned long long i = 0; i < n_allones; i += 32)
+                warp_append<W>(st, oc, i + lane < n_allones, Tup<W>::kAllOnes, ss);
     }
 };
-template <int W> struct AggView {
+
+template <int W> struct AggTab {
     using U = typename Tup<W>::U;
     const AggSlot<W> *slots;
     uint64_t cap;
@@ -76,97 +117,100 @@ template <int W> struct AggView {
     }
 };
 
-// Shared scratch for the tile emission (block scan + reserved base).
-struct EmitShared {
-    unsigned long long scan[33];
-    unsigned long long base;
+// Per-lane accumulators of a probing warp.
+struct ProbeAcc {
+    unsigned long long cnt = 0, c0 = 0, c1 = 0;
 };
 
-// Probe IT tuples per thread against a pair table and place their pairs.
-// All threads of the block must call this (it contains barriers).
-template <int W, int IT, class View>
-__device__ __forceinline__ void probe_tile_pairs(const View &tab, const typename Tup<W>::U *k,
-                                                 const typename Tup<W>::U *r, const bool *valid, void *pairs,
-                                                 uint64_t pcap, hj_counters *ctr, bool chk, uint64_t &c0,
-                                                 uint64_t &c1, EmitShared &es) {
-    using U = typename Tup<W>::U;
+// Probe one group against a pair table and append its pairs.
+template <int W, int U>
+__device__ __forceinline__ void probe_group_pairs(const PairTab<W> &tab, const Group<W, U> &g, const PartFilter &pf,
+                                                  bool chk, OutState &st, const OutCtx &oc, ProbeAcc &acc) {
+    using T = typename Tup<W>::U;
+    constexpr int IT = Group<W, U>::IT;
     uint32_t cnt[IT];
-    U first[IT];
-    uint64_t mine = 0;
+    T first[IT];
 #pragma unroll
     for (int i = 0; i < IT; ++i) {
-        cnt[i] = 0;
-        first[i] = 0;
-        if (valid[i]) {
-            uint64_t h = key_hash<W>(k[i]);
-            uint64_t bs = chk ? mix_b(r[i]) : 0;
-            uint32_t c = 0;
-            U f = 0;
-            tab.lookup(k[i], h, [&](U rid) {
+        uint32_t c = 0;
+        T f = 0;
+        const uint64_t h = key_hash<W>(g.k[i]);
+        if (g.valid[i] && pf.keep(h)) {
+            const uint64_t bs = chk ? mix_b(g.r[i]) : 0;
+            tab.lookup(g.k[i], h, [&](T rid) {
                 if (c == 0) f = rid;
                 ++c;
                 if (chk) {
                     uint64_t a = mix_a(rid);
-                    c0 += a * bs;
-                    c1 += a + bs;
+                    acc.c0 += a * bs;
+                    acc.c1 += a + bs;
                 }
             });
-            cnt[i] = c;
-            first[i] = f;
-            mine += c;
         }
+        cnt[i] = c;
+        first[i] = f;
     }
-    unsigned long long total;
-    unsigned long long off = block_exclusive_scan<unsigned long long>(mine, es.scan, &total);
-    if (threadIdx.x == 0) es.base = total ? atomicAdd(&ctr->count, total) : 0ull;
-    __syncthreads();
-    uint64_t pos = es.base + off;
-    __syncthreads();
-    if (mine) {
 #pragma unroll
-        for (int i = 0; i < IT; ++i) {
-            if (cnt[i] == 1) {
-                if (pos < pcap) PairOut<W>::put(pairs, pos, first[i], r[i]);
-                ++pos;
-            } else if (cnt[i] > 1) {
-                uint64_t h = key_hash<W>(k[i]);
-                U s = r[i];
-                tab.lookup(k[i], h, [&](U rid) {
-                    if (pos < pcap) PairOut<W>::put(pairs, pos, rid, s);
-                    ++pos;
-                });
-            }
-        }
-    }
-}
-
-// Probe IT tuples per thread against an aggregate table (count modes).
-template <int W, int IT>
-__device__ __forceinline__ void probe_tile_agg(const AggView<W> &tab, const typename Tup<W>::U *k,
-                                               const typename Tup<W>::U *r, const bool *valid, bool chk,
-                                               uint64_t &cnt, uint64_t &c0, uint64_t &c1) {
+    for (int i = 0; i < IT; ++i) warp_append<W>(st, oc, cnt[i] == 1, first[i], g.r[i]);
 #pragma unroll
     for (int i = 0; i < IT; ++i) {
-        if (!valid[i]) continue;
-        uint64_t n, sa;
-        tab.lookup(k[i], key_hash<W>(k[i]), &n, &sa);
-        cnt += n;
-        if (chk && n) {
-            uint64_t b = mix_b(r[i]);
-            c0 += sa * b;
-            c1 += sa + n * b;
+        unsigned multi = __ballot_sync(0xffffffffu, cnt[i] > 1);
+        while (multi) {
+            const int L = __ffs(multi) - 1;
+            multi &= multi - 1;
+            T kk = __shfl_sync(0xffffffffu, g.k[i], L);
+            T ss = __shfl_sync(0xffffffffu, g.r[i], L);
+            tab.coop_emit(kk, ss, st, oc);
         }
     }
 }
 
-__device__ __forceinline__ void flush_sums(hj_counters *ctr, uint64_t cnt, uint64_t c0, uint64_t c1, bool with_cnt) {
-    cnt = warp_sum(cnt);
-    c0 = warp_sum(c0);
-    c1 = warp_sum(c1);
+template <int W, int U>
+__device__ __forceinline__ void probe_group_agg(const AggTab<W> &tab, const Group<W, U> &g, const PartFilter &pf,
+                                                bool chk, ProbeAcc &acc) {
+    constexpr int IT = Group<W, U>::IT;
+#pragma unroll
+    for (int i = 0; i < IT; ++i) {
+        const uint64_t h = key_hash<W>(g.k[i]);
+        if (!g.valid[i] || !pf.keep(h)) continue;
+        uint64_t n, sa;
+        tab.lookup(g.k[i], h, &n, &sa);
+        acc.cnt += n;
+        if (chk && n) {
+            const uint64_t b = mix_b(g.r[i]);
+            acc.c0 += sa * b;
+            acc.c1 += sa + n * b;
+        }
+    }
+}
+
+// Stream S rows [lo, hi) through one warp: groups g = g0, g0 + gstride, ...
+template <int W, int U, bool AGG, class Tab>
+__device__ __forceinline__ void warp_probe(const Tab &tab, const void *S, uint64_t lo, uint64_t hi, uint64_t n_total,
+                                           uint64_t g0, uint64_t gstride, const PartFilter &pf, bool chk,
+                                           OutState &st, const OutCtx &oc, ProbeAcc &acc) {
+    constexpr int PV = Tup<W>::kPerVec;
+    const uint64_t vb = (hi + PV - 1) / PV;
+    if (g0 >= vb) return;
+    Group<W, U> cur, nxt;
+    cur.load(S, g0, lo, hi, vb, n_total);
+    for (uint64_t g = g0; g < vb; g += gstride) {
+        const uint64_t gn = g + gstride;
+        if (gn < vb) nxt.load(S, gn, lo, hi, vb, n_total);
+        if constexpr (AGG) probe_group_agg<W, U>(tab, cur, pf, chk, acc);
+        else probe_group_pairs<W, U>(tab, cur, pf, chk, st, oc, acc);
+        cur = nxt;
+    }
+}
+
+__device__ __forceinline__ void flush_acc(hj_counters *ctr, ProbeAcc acc, bool with_cnt) {
+    acc.cnt = warp_sum(acc.cnt);
+    acc.c0 = warp_sum(acc.c0);
+    acc.c1 = warp_sum(acc.c1);
     if ((threadIdx.x & 31) == 0) {
-        if (with_cnt && cnt) atomicAdd(&ctr->count, (unsigned long long)cnt);
-        if (c0) atomicAdd(&ctr->c0, (unsigned long long)c0);
-        if (c1) atomicAdd(&ctr->c1, (unsigned long long)c1);
+        if (with_cnt && acc.cnt) atomicAdd(&ctr->count, acc.cnt);
+        if (acc.c0) atomicAdd(&ctr->c0, acc.c0);
+        if (acc.c1) atomicAdd(&ctr->c1, acc.c1);
     }
 }
 
@@ -187,7 +231,7 @@ __global__ void agg_table_init(AggSlot<W> *slots, uint64_t cap) {
 template <int W, bool AGG>
 __global__ void __launch_bounds__(256) table_build_kernel(const void *R, uint64_t lo, uint64_t hi, uint64_t n_total,
                                                           void *slots, uint64_t cap, TableSide *side,
-                                                          hj_counters *ctr) {
+                                                          hj_counters *ctr, PartFilter pf) {
     using U = typename Tup<W>::U;
     constexpr int PV = Tup<W>::kPerVec;
     uint64_t va = lo / PV, vb = (hi + PV - 1) / PV;
@@ -200,6 +244,7 @@ __global__ void __launch_bounds__(256) table_build_kernel(const void *R, uint64_
             uint64_t t = v * PV + e;
             if (t < lo || t >= hi) continue;
             uint64_t h = key_hash<W>(k[e]);
+            if (!pf.keep(h)) continue;
             bool ok = AGG ? agg_insert<W>((AggSlot<W> *)slots, cap, side, k[e], mix_a(r[e]), h)
                           : pair_insert<W>((typename PairSlot<W>::S *)slots, cap, side, k[e], r[e], h);
             if (!ok) atomicOr(&ctr->status, (unsigned long long)kStatusTableFull);
@@ -207,84 +252,60 @@ __global__ void __launch_bounds__(256) table_build_kernel(const void *R, uint64_
     }
 }
 
-// Tuples per thread per tile: 4 (two 16-byte vectors of 4-byte tuples, or four
-// vectors of 8-byte tuples).
-template <int W> struct ProbeShape {
-    static constexpr int PV = Tup<W>::kPerVec;
-    static constexpr int VPT = 4 / PV;
-    static constexpr int IT = 4;
+// Vectors per lane per probe group.
+template <int W> struct ProbeU {
+    static constexpr int value = 2;
 };
 
 template <int W, bool AGG>
-__global__ void __launch_bounds__(512) table_probe_kernel(const void *S, uint64_t lo, uint64_t hi, uint64_t n_total,
+__global__ void __launch_bounds__(256) table_probe_kernel(const void *S, uint64_t lo, uint64_t hi, uint64_t n_total,
                                                           const void *slots, uint64_t cap, const TableSide *side,
-                                                          void *pairs, uint64_t pcap, hj_counters *ctr, int chk) {
-    using U = typename Tup<W>::U;
-    using PSh = ProbeShape<W>;
-    constexpr int PV = PSh::PV, VPT = PSh::VPT, IT = PSh::IT;
-    __shared__ EmitShared es;
-    uint64_t va = lo / PV, vb = (hi + PV - 1) / PV;
-    uint64_t tile_vecs = (uint64_t)blockDim.x * VPT;
-    uint64_t ntiles = (vb - va + tile_vecs - 1) / tile_vecs;
-    uint64_t cnt = 0, c0 = 0, c1 = 0;
-    PairView<W> pv{(const typename PairSlot<W>::S *)slots, cap, AGG ? 0ull : side->n_allones};
-    AggView<W> av{(const AggSlot<W> *)slots, cap, side};
-    for (uint64_t tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
-        U k[IT], r[IT];
-        bool valid[IT];
-#pragma unroll
-        for (int j = 0; j < VPT; ++j) {
-            uint64_t v = va + tile * tile_vecs + (uint64_t)j * blockDim.x + threadIdx.x;
-            U kk[2] = {0, 0}, rr[2] = {0, 0};
-            if (v < vb) load_vec<W>(S, v, n_total, kk, rr);
-#pragma unroll
-            for (int e = 0; e < PV; ++e) {
-                uint64_t t = v * PV + e;
-                k[j * PV + e] = kk[e];
-                r[j * PV + e] = rr[e];
-                valid[j * PV + e] = v < vb && t >= lo && t < hi;
-            }
-        }
-        if constexpr (AGG) {
-            probe_tile_agg<W, IT>(av, k, r, valid, chk != 0, cnt, c0, c1);
-        } else {
-            probe_tile_pairs<W, IT>(pv, k, r, valid, pairs, pcap, ctr, chk != 0, c0, c1, es);
-        }
+                                                          void *pairs, uint64_t pcap, RecArea ra, hj_counters *ctr,
+                                                          int chk, PartFilter pf) {
+    constexpr int PV = Tup<W>::kPerVec, U = ProbeU<W>::value;
+    const unsigned warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const unsigned nwarps = (gridDim.x * blockDim.x) >> 5;
+    const uint64_t va = lo / PV;
+    OutState st;
+    OutCtx oc{pairs, pcap, ctr};
+    ProbeAcc acc;
+    if constexpr (AGG) {
+        AggTab<W> tab{(const AggSlot<W> *)slots, cap, side};
+        warp_probe<W, U, true>(tab, S, lo, hi, n_total, va + (uint64_t)warp * 32 * U, (uint64_t)nwarps * 32 * U,
+                               pf, chk != 0, st, oc, acc);
+    } else {
+        PairTab<W> tab{(const typename PairSlot<W>::S *)slots, cap, side->n_allones, 1u};
+        warp_probe<W, U, false>(tab, S, lo, hi, n_total, va + (uint64_t)warp * 32 * U, (uint64_t)nwarps * 32 * U,
+                                pf, chk != 0, st, oc, acc);
+        warp_finish(st, oc, ra);
     }
-    flush_sums(ctr, cnt, c0, c1, AGG);
+    flush_acc(ctr, acc, AGG);
 }
 
 hj_status table_create(hj_ctx *c, int width, int agg, uint64_t n_build, hj_table **out) {
     *out = nullptr;
-    hj_table *t = new hj_table();
-    t->width = width;
-    t->agg = agg;
     // Capacity: a power of two at least twice the build size (load factor <= 0.5).
     uint64_t cap = 64;
     while (cap < 2 * n_build + 1) cap <<= 1;
-    t->cap = cap;
     uint64_t slot_bytes = agg ? (width == 4 ? sizeof(AggSlot<4>) : sizeof(AggSlot<8>)) : 2ull * width;
-    hj_status st;
-    t->slots = dalloc(c, cap * slot_bytes, &st);
-    if (st != HJ_OK) {
-        delete t;
-        return st;
-    }
-    t->side = dalloc(c, sizeof(TableSide), &st);
-    if (st != HJ_OK) {
-        dfree(c, t->slots);
-        delete t;
-        return st;
-    }
-    cudaMemsetAsync(t->side, 0, sizeof(TableSide), c->stream);
+    DevBuf slots(c), side(c);
+    HJ_TRY(slots.alloc(cap * slot_bytes));
+    HJ_TRY(side.alloc(sizeof(TableSide)));
+    HJ_CUDA(c, cudaMemsetAsync(side.p, 0, sizeof(TableSide), c->stream));
     int grid = num_sms(c) * 4;
     if (!agg) {
-        HJ_CUDA(c, cudaMemsetAsync(t->slots, 0xFF, cap * slot_bytes, c->stream));
+        HJ_CUDA(c, cudaMemsetAsync(slots.p, 0xFF, cap * slot_bytes, c->stream));
     } else if (width == 4) {
-        HJ_LAUNCH(c, "agg_table_init", agg_table_init<4>, grid, 256, 0, (AggSlot<4> *)t->slots, cap);
+        HJ_LAUNCH(c, "agg_table_init", agg_table_init<4>, grid, 256, 0, slots.as<AggSlot<4>>(), cap);
     } else {
-        HJ_LAUNCH(c, "agg_table_init", agg_table_init<8>, grid, 256, 0, (AggSlot<8> *)t->slots, cap);
+        HJ_LAUNCH(c, "agg_table_init", agg_table_init<8>, grid, 256, 0, slots.as<AggSlot<8>>(), cap);
     }
+    hj_table *t = new hj_table();
+    t->width = width;
+    t->agg = agg;
+    t->cap = cap;
+    t->slots = slots.release();
+    t->side = side.release();
     *out = t;
     return HJ_OK;
 }
@@ -296,185 +317,452 @@ void table_destroy(hj_ctx *c, hj_table *t) {
     delete t;
 }
 
-hj_status table_build(hj_ctx *c, hj_table *t, const void *R, uint64_t lo, uint64_t hi, uint64_t n_total) {
+hj_status table_build(hj_ctx *c, hj_table *t, const void *R, uint64_t lo, uint64_t hi, uint64_t n_total,
+                      PartFilter pf) {
     if (hi <= lo) return HJ_OK;
     uint64_t nvec = (hi - lo) / (t->width == 4 ? 2 : 1) + 2;
     uint64_t want = (nvec + 255) / 256;
     int grid = (int)(want < (uint64_t)num_sms(c) * 8 ? (want ? want : 1) : (uint64_t)num_sms(c) * 8);
     TableSide *side = (TableSide *)t->side;
+#define HJ_TB(WW, AA) HJ_LAUNCH(c, "table_build", (table_build_kernel<WW, AA>), grid, 256, 0, R, lo, hi, n_total, t->slots, t->cap, side, c->d_ctr, pf)
     if (t->width == 4) {
-        if (t->agg)
-            HJ_LAUNCH(c, "table_build", (table_build_kernel<4, true>), grid, 256, 0, R, lo, hi, n_total, t->slots, t->cap, side, c->d_ctr);
-        else
-            HJ_LAUNCH(c, "table_build", (table_build_kernel<4, false>), grid, 256, 0, R, lo, hi, n_total, t->slots, t->cap, side, c->d_ctr);
+        if (t->agg) HJ_TB(4, true); else HJ_TB(4, false);
     } else {
-        if (t->agg)
-            HJ_LAUNCH(c, "table_build", (table_build_kernel<8, true>), grid, 256, 0, R, lo, hi, n_total, t->slots, t->cap, side, c->d_ctr);
-        else
-            HJ_LAUNCH(c, "table_build", (table_build_kernel<8, false>), grid, 256, 0, R, lo, hi, n_total, t->slots, t->cap, side, c->d_ctr);
+        if (t->agg) HJ_TB(8, true); else HJ_TB(8, false);
     }
+#undef HJ_TB
     return HJ_OK;
 }
 
+uint64_t table_probe_warps(hj_ctx *c, uint64_t n) {
+    const uint64_t per_cta_tuples = 8 * 32 * 8;  // 8 warps, 32 lanes, 8 tuples per lane group
+    uint64_t want = (n + per_cta_tuples - 1) / per_cta_tuples;
+    uint64_t maxg = (uint64_t)num_sms(c) * 8;
+    uint64_t grid = want < maxg ? (want ? want : 1) : maxg;
+    return grid * 8;
+}
+
 hj_status table_probe(hj_ctx *c, const hj_table *t, const void *S, uint64_t lo, uint64_t hi, uint64_t n_total,
-                      void *pairs, uint64_t pcap, int checksum) {
+                      void *pairs, uint64_t pcap, int checksum, RecArea ra, PartFilter pf) {
     if (hi <= lo) return HJ_OK;
-    const int block = 512;
-    uint64_t tile_tuples = (uint64_t)block * 4;
-    uint64_t want = (hi - lo + tile_tuples - 1) / tile_tuples + 1;
-    uint64_t maxg = (uint64_t)num_sms(c) * 4;
-    int grid = (int)(want < maxg ? want : maxg);
+    const unsigned grid = (unsigned)(table_probe_warps(c, hi - lo) / 8);
     const TableSide *side = (const TableSide *)t->side;
+#define HJ_TP(WW, AA) HJ_LAUNCH(c, "table_probe", (table_probe_kernel<WW, AA>), grid, 256, 0, S, lo, hi, n_total, t->slots, t->cap, side, pairs, pcap, ra, c->d_ctr, checksum, pf)
     if (t->width == 4) {
-        if (t->agg)
-            HJ_LAUNCH(c, "table_probe", (table_probe_kernel<4, true>), grid, block, 0, S, lo, hi, n_total, t->slots, t->cap, side, pairs, pcap, c->d_ctr, checksum);
-        else
-            HJ_LAUNCH(c, "table_probe", (table_probe_kernel<4, false>), grid, block, 0, S, lo, hi, n_total, t->slots, t->cap, side, pairs, pcap, c->d_ctr, checksum);
+        if (t->agg) HJ_TP(4, true); else HJ_TP(4, false);
     } else {
-        if (t->agg)
-            HJ_LAUNCH(c, "table_probe", (table_probe_kernel<8, true>), grid, block, 0, S, lo, hi, n_total, t->slots, t->cap, side, pairs, pcap, c->d_ctr, checksum);
-        else
-            HJ_LAUNCH(c, "table_probe", (table_probe_kernel<8, false>), grid, block, 0, S, lo, hi, n_total, t->slots, t->cap, side, pairs, pcap, c->d_ctr, checksum);
+        if (t->agg) HJ_TP(8, true); else HJ_TP(8, false);
     }
+#undef HJ_TP
     return HJ_OK;
 }
 
 // ================================================== per-partition join (PHJ)
 //
-// CTA p joins partition pair (R_p, S_p): it builds a table over R_p in shared
-// memory (capacity about twice |R_p|, multiply-shift buckets so any capacity
-// works), then streams S_p tile by tile.  A partition whose table cannot fit
-// (|R_p| too large for a pair table, or more distinct keys than slots for an
-// aggregate table) is handed to the global-table fallback.
+// Persistent CTAs take partition pairs (R_p, S_p) from ctr->work.  For each, the
+// CTA builds a table over R_p in shared memory (capacity about twice |R_p|,
+// multiply-shift buckets so any capacity works), then its warps stream S_p.
+// Partitions come from the padded partitioner: every partition starts and ends on
+// a 32-byte sector, so whole 16-byte vectors can be loaded without bounds checks
+// on tuples, and padding tuples are dropped by the partition test (PartFilter).
+// A partition whose table cannot fit (|R_p| too large for a pair table, or more
+// distinct keys than slots for an aggregate table) goes to the host's
+// global-table fallback list.
 
-template <int W, bool AGG>
-__global__ void __launch_bounds__(512) partition_join_kernel(const void *Rp, const uint64_t *roff, uint64_t nR_total,
-                                                             const void *Sp, const uint64_t *soff, uint64_t nS_total,
-                                                             uint64_t cap_max, void *pairs, uint64_t pcap,
-                                                             hj_counters *ctr, uint32_t *oversize, int chk) {
-    using U = typename Tup<W>::U;
-    using PSh = ProbeShape<W>;
-    constexpr int PV = PSh::PV, VPT = PSh::VPT, IT = PSh::IT;
+template <int W> struct HashT { using type = uint32_t; };
+template <> struct HashT<8> { using type = uint64_t; };
+
+// Bucket of a shared-memory table; equal to bucket_of<W> for cap < 2^32.
+template <int W> __device__ __forceinline__ uint32_t sbucket(typename HashT<W>::type h, uint32_t cap);
+template <> __device__ __forceinline__ uint32_t sbucket<4>(uint32_t h, uint32_t cap) { return __umulhi(h, cap); }
+template <> __device__ __forceinline__ uint32_t sbucket<8>(uint64_t h, uint32_t cap) {
+    return (uint32_t)__umul64hi(h, (uint64_t)cap);
+}
+
+// A shared-memory table bucket: 32 aligned bytes, read with two 16-byte loads --
+// four slots of 4-byte tuples or two slots of 8-byte tuples.
+template <int W> struct SmemBucket {
+    static constexpr uint32_t kSlots = 32 / (2 * W);
+    ulonglong2 a, b;
+    __device__ __forceinline__ void load(uint32_t base, uint32_t bkt) {
+        const uint32_t addr = base + bkt * 32u;
+        asm volatile("ld.shared.v2.u64 {%0, %1}, [%2];" : "=l"(a.x), "=l"(a.y) : "r"(addr));
+        asm volatile("ld.shared.v2.u64 {%0, %1}, [%2];" : "=l"(b.x), "=l"(b.y) : "r"(addr + 16u));
+    }
+};
+
+template <int W> struct SmemPair;
+template <> struct SmemPair<4> {
+    static __device__ __forceinline__ unsigned long long ld(uint32_t base, uint32_t i) {
+        unsigned long long v;
+        asm volatile("ld.shared.u64 %0, [%1];" : "=l"(v) : "r"(base + i * 8u));
+        return v;
+    }
+    static __device__ __forceinline__ bool empty(unsigned long long s) { return s == ~0ull; }
+    static __device__ __forceinline__ uint32_t key(unsigned long long s) { return (uint32_t)s; }
+    static __device__ __forceinline__ uint32_t rid(unsigned long long s) { return (uint32_t)(s >> 32); }
+};
+template <> struct SmemPair<8> {
+    static __device__ __forceinline__ ulonglong2 ld(uint32_t base, uint32_t i) {
+        ulonglong2 v;
+        asm volatile("ld.shared.v2.u64 {%0, %1}, [%2];" : "=l"(v.x), "=l"(v.y) : "r"(base + i * 16u));
+        return v;
+    }
+    static __device__ __forceinline__ bool empty(ulonglong2 s) { return (s.x & s.y) == ~0ull; }
+    static __device__ __forceinline__ uint64_t key(ulonglong2 s) { return s.x; }
+    static __device__ __forceinline__ uint64_t rid(ulonglong2 s) { return s.y; }
+};
+
+template <int W>
+__device__ __forceinline__ typename HashT<W>::type hashw(typename Tup<W>::U k) {
+    if constexpr (W == 4) return murmur2_u32(k);
+    else return murmur2_u64(k);
+}
+
+// Probe of a 4-byte key against one shared-memory bucket of four slots, without
+// branches: match mask, count, first matching rid, whether the run ends here.
+struct Bucket4 {
+    uint32_t cnt, first;
+    bool end;
+};
+__device__ __forceinline__ Bucket4 probe_bucket4(uint32_t sbase, uint32_t bkt, uint32_t k, const uint32_t *ovf) {
+    ulonglong2 a, b;
+    const uint32_t addr = sbase + bkt * 32u;
+    asm volatile("ld.shared.v2.u64 {%0, %1}, [%2];" : "=l"(a.x), "=l"(a.y) : "r"(addr));
+    asm volatile("ld.shared.v2.u64 {%0, %1}, [%2];" : "=l"(b.x), "=l"(b.y) : "r"(addr + 16u));
+    const uint32_t k0 = (uint32_t)a.x, k1 = (uint32_t)a.y, k2 = (uint32_t)b.x, k3 = (uint32_t)b.y;
+    const uint32_t r0 = (uint32_t)(a.x >> 32), r1 = (uint32_t)(a.y >> 32), r2 = (uint32_t)(b.x >> 32),
+                   r3 = (uint32_t)(b.y >> 32);
+    // a slot is empty iff key and rid are all ones
+    const bool e0 = (k0 & r0) == 0xFFFFFFFFu, e1 = (k1 & r1) == 0xFFFFFFFFu, e2 = (k2 & r2) == 0xFFFFFFFFu,
+               e3 = (k3 & r3) == 0xFFFFFFFFu;
+    const bool m0 = k0 == k && !e0, m1 = k1 == k && !e1, m2 = k2 == k && !e2, m3 = k3 == k && !e3;
+    Bucket4 o;
+    o.cnt = (uint32_t)m0 + (uint32_t)m1 + (uint32_t)m2 + (uint32_t)m3;
+    o.first = m0 ? r0 : m1 ? r1 : m2 ? r2 : r3;
+    // the run of this key ends in this bucket if the bucket has an empty slot or
+    // no insert ever moved past it
+    o.end = e0 | e1 | e2 | e3;
+    if (!o.end) o.end = !((ovf[bkt >> 5] >> (bkt & 31)) & 1u);
+    return o;
+}
+
+template <int W, bool AGG, int NT>
+__global__ void __launch_bounds__(NT, 2048 / NT / 2) partition_join_kernel(
+    const void *Rp, const uint64_t *roff, const void *Sp, const uint64_t *soff, uint64_t NP, uint32_t cap_max,
+    void *pairs, uint64_t pcap, RecArea ra, hj_counters *ctr, uint32_t *oversize, int chk, int b1, int b2) {
+    using T = typename Tup<W>::U;
+    using Vec = typename Tup<W>::Vec;
+    using Hh = typename HashT<W>::type;
+    using SP = SmemPair<W>;
+    constexpr int PV = Tup<W>::kPerVec, U = 2, IT = U * PV;
+    constexpr uint32_t G = SmemBucket<W>::kSlots;
     extern __shared__ __align__(16) unsigned char smem[];
-    __shared__ EmitShared es;
     __shared__ TableSide side;
     __shared__ int s_full;
+    __shared__ unsigned long long s_p;
+    const uint32_t sbase = (uint32_t)__cvta_generic_to_shared(smem);
+    const unsigned lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
+    const unsigned lt = (1u << lane) - 1u;
 
-    const uint32_t p = blockIdx.x;
-    const uint64_t r0 = roff[p], r1 = roff[p + 1], s0 = soff[p], s1 = soff[p + 1];
-    const uint64_t nr = r1 - r0;
-    if (s1 <= s0 || nr == 0) return;  // no probe tuples or no build tuples: no pairs
-
-    uint64_t cap;
-    if (AGG) {
-        cap = 2 * nr + 32;
-        cap = cap < cap_max ? cap : cap_max;
-    } else {
-        cap = ((2 * nr + 31) / 32) * 32;
-        if (cap > cap_max) cap = cap_max;
-        if (nr >= cap - cap / 4) {  // load factor above 3/4: leave to the fallback
-            if (threadIdx.x == 0) oversize[atomicAdd(&ctr->n_oversize, 1ull)] = p;
-            return;
-        }
-    }
-    // initialise the table
-    if (AGG) {
-        AggSlot<W> *sl = (AggSlot<W> *)smem;
-        for (uint64_t i = threadIdx.x; i < cap; i += blockDim.x) {
-            sl[i].key = Tup<W>::kAllOnes;
-            sl[i].cnt = 0;
-            sl[i].suma = 0;
-        }
-    } else {
-        using S = typename PairSlot<W>::S;
-        S *sl = (S *)smem;
-        for (uint64_t i = threadIdx.x; i < cap; i += blockDim.x) sl[i] = PairSlot<W>::empty();
-    }
-    if (threadIdx.x == 0) {
-        side.n_allones = side.agg_cnt = side.agg_suma = side.full = 0;
-        s_full = 0;
-    }
-    __syncthreads();
-    // build over R_p
-    {
-        uint64_t va = r0 / PV, vb = (r1 + PV - 1) / PV;
-        for (uint64_t v = va + threadIdx.x; v < vb; v += blockDim.x) {
-            U k[2], r[2];
-            load_vec<W>(Rp, v, nR_total, k, r);
-#pragma unroll
-            for (int e = 0; e < PV; ++e) {
-                uint64_t t = v * PV + e;
-                if (t < r0 || t >= r1) continue;
-                uint64_t h = key_hash<W>(k[e]);
-                bool ok = AGG ? agg_insert<W>((AggSlot<W> *)smem, cap, &side, k[e], mix_a(r[e]), h)
-                              : pair_insert<W>((typename PairSlot<W>::S *)smem, cap, &side, k[e], r[e], h);
-                if (!ok) s_full = 1;
+    OutState st;
+    OutCtx oc{pairs, pcap, ctr};
+    ProbeAcc acc;
+    for (;;) {
+        if (threadIdx.x == 0) s_p = atomicAdd(&ctr->work, 1ull);
+        __syncthreads();
+        const uint64_t p = s_p;
+        if (p >= NP) break;
+        const uint64_t r0 = roff[p], r1 = roff[p + 1], s0 = soff[p], s1 = soff[p + 1];
+        const uint32_t nrv = (uint32_t)((r1 - r0) / PV), nsv = (uint32_t)((s1 - s0) / PV);
+        const Vec *Rv = (const Vec *)Rp + r0 / PV;
+        const Vec *Sv = (const Vec *)Sp + s0 / PV;
+        const uint64_t nr = r1 - r0;  // build rows, padding included
+        const PartFilter pf{(uint32_t)p, b1, b2, 1};
+        bool work = nsv > 0 && nrv > 0;
+        uint32_t cap = 0;
+        if (work) {
+            if (AGG) {
+                const uint64_t want = 2 * nr + 32;
+                cap = want < cap_max ? (uint32_t)want : cap_max;
+            } else {
+                // about three slots per build row (load factor 1/3), whole buckets
+                const uint64_t want = (3 * nr + 127) / 128 * 128;
+                cap = want < cap_max ? (uint32_t)want : cap_max;
+                if (nr >= cap - cap / 4) {  // load factor above 3/4: leave to the fallback
+                    if (threadIdx.x == 0) oversize[atomicAdd(&ctr->n_oversize, 1ull)] = (uint32_t)p;
+                    work = false;
+                }
             }
         }
-    }
-    __syncthreads();
-    if (s_full) {
-        if (threadIdx.x == 0) oversize[atomicAdd(&ctr->n_oversize, 1ull)] = p;
-        return;
-    }
-    // probe S_p
-    PairView<W> pv{(const typename PairSlot<W>::S *)smem, cap, side.n_allones};
-    AggView<W> av{(const AggSlot<W> *)smem, cap, &side};
-    uint64_t cnt = 0, c0 = 0, c1 = 0;
-    uint64_t va = s0 / PV, vb = (s1 + PV - 1) / PV;
-    uint64_t tile_vecs = (uint64_t)blockDim.x * VPT;
-    for (uint64_t base = va; base < vb; base += tile_vecs) {
-        U k[IT], r[IT];
-        bool valid[IT];
+        // overflow bitmap (one bit per bucket) after the slots
+        uint32_t *ovf = (uint32_t *)(smem + (size_t)cap_max * (AGG ? sizeof(AggSlot<W>) : 2 * W));
+        if (work) {
+            if (AGG) {
+                AggSlot<W> *sl = (AggSlot<W> *)smem;
+                for (uint32_t i = threadIdx.x; i < cap; i += blockDim.x) {
+                    sl[i].key = Tup<W>::kAllOnes;
+                    sl[i].cnt = 0;
+                    sl[i].suma = 0;
+                }
+            } else {
+                typename PairSlot<W>::S *sl = (typename PairSlot<W>::S *)smem;
+                for (uint32_t i = threadIdx.x; i < cap; i += blockDim.x) sl[i] = PairSlot<W>::empty();
+                for (uint32_t i = threadIdx.x; i < (cap / G + 31) / 32; i += blockDim.x) ovf[i] = 0;
+            }
+            if (threadIdx.x == 0) {
+                side.n_allones = side.agg_cnt = side.agg_suma = side.full = 0;
+                s_full = 0;
+            }
+            __syncthreads();
+            // build over R_p
+            for (uint32_t v = threadIdx.x; v < nrv; v += blockDim.x) {
+                const Vec x = ld_stream(Rv + v);
+                T k[2], r[2];
+                if constexpr (W == 4) {
+                    k[0] = x.x; r[0] = x.y; k[1] = x.z; r[1] = x.w;
+                } else {
+                    k[0] = x.x; r[0] = x.y;
+                }
 #pragma unroll
-        for (int j = 0; j < VPT; ++j) {
-            uint64_t v = base + (uint64_t)j * blockDim.x + threadIdx.x;
-            U kk[2] = {0, 0}, rr[2] = {0, 0};
-            if (v < vb) load_vec<W>(Sp, v, nS_total, kk, rr);
+                for (int e = 0; e < PV; ++e) {
+                    const Hh h = hashw<W>(k[e]);
+                    if (!pf.keep(h)) continue;
+                    bool ok;
+                    if constexpr (AGG) {
+                        ok = agg_insert<W>((AggSlot<W> *)smem, cap, &side, k[e], mix_a(r[e]), h);
+                    } else if (k[e] == Tup<W>::kAllOnes && r[e] == Tup<W>::kAllOnes) {
+                        atomicAdd(&side.n_allones, 1ull);
+                        ok = true;
+                    } else {
+                        typename PairSlot<W>::S *sl = (typename PairSlot<W>::S *)smem;
+                        const typename PairSlot<W>::S val = PairSlot<W>::pack(k[e], r[e]);
+                        const uint32_t nb = cap / G;
+                        uint32_t bkt = sbucket<W>(h, nb);
+                        ok = false;
+                        for (uint32_t it = 0; it < nb && !ok; ++it) {
+                            for (uint32_t q = 0; q < G; ++q) {
+                                if (PairSlot<W>::try_claim(&sl[bkt * G + q], val)) {
+                                    ok = true;
+                                    break;
+                                }
+                            }
+                            if (!ok) {  // moving past a full bucket: mark it
+                                atomicOr(&ovf[bkt >> 5], 1u << (bkt & 31));
+                                bkt = bkt + 1 == nb ? 0 : bkt + 1;
+                            }
+                        }
+                    }
+                    if (!ok) s_full = 1;
+                }
+            }
+            __syncthreads();
+            if (s_full) {
+                if (threadIdx.x == 0) oversize[atomicAdd(&ctr->n_oversize, 1ull)] = (uint32_t)p;
+            } else {
+                const unsigned long long nall = side.n_allones;
+                PairTab<W> ptab{(const typename PairSlot<W>::S *)smem, cap, nall, G};
+                AggTab<W> atab{(const AggSlot<W> *)smem, cap, &side};
+                const uint32_t nb = cap / G;
+                const uint32_t gstride = nwarps * 32 * U;
+                Vec cur[U], nxt[U];
+                uint32_t g = warp * 32 * U;
 #pragma unroll
-            for (int e = 0; e < PV; ++e) {
-                uint64_t t = v * PV + e;
-                k[j * PV + e] = kk[e];
-                r[j * PV + e] = rr[e];
-                valid[j * PV + e] = v < vb && t >= s0 && t < s1;
+                for (int u = 0; u < U; ++u) {
+                    const uint32_t rel = g + u * 32 + lane;
+                    if (rel < nsv) cur[u] = ld_stream(Sv + rel);
+                }
+                for (; g < nsv; g += gstride) {
+#pragma unroll
+                    for (int u = 0; u < U; ++u) {
+                        const uint32_t rel = g + gstride + u * 32 + lane;
+                        if (rel < nsv) nxt[u] = ld_stream(Sv + rel);
+                    }
+                    T k[IT], r[IT];
+                    bool val[IT];
+#pragma unroll
+                    for (int u = 0; u < U; ++u) {
+                        const bool in = g + u * 32 + lane < nsv;
+                        if constexpr (W == 4) {
+                            k[2 * u] = cur[u].x; r[2 * u] = cur[u].y; k[2 * u + 1] = cur[u].z; r[2 * u + 1] = cur[u].w;
+                            val[2 * u] = in;
+                            val[2 * u + 1] = in;
+                        } else {
+                            k[u] = cur[u].x; r[u] = cur[u].y;
+                            val[u] = in;
+                        }
+                    }
+                    if constexpr (AGG) {
+#pragma unroll
+                        for (int i = 0; i < IT; ++i) {
+                            const Hh h = hashw<W>(k[i]);
+                            if (!val[i] || !pf.keep(h)) continue;
+                            uint64_t n, sa;
+                            atab.lookup(k[i], h, &n, &sa);
+                            acc.cnt += n;
+                            if (chk && n) {
+                                const uint64_t bb = mix_b(r[i]);
+                                acc.c0 += sa * bb;
+                                acc.c1 += sa + n * bb;
+                            }
+                        }
+                    } else {
+                        uint32_t cnt[IT];
+                        T first[IT];
+#pragma unroll
+                        for (int i = 0; i < IT; ++i) {
+                            const Hh h = hashw<W>(k[i]);
+                            uint32_t c = 0;
+                            T f = 0;
+                            if (val[i] && pf.keep(h)) {
+                                uint32_t bkt = sbucket<W>(h, nb);
+                                if constexpr (W == 4) {
+                                    for (uint32_t it = 0; it < nb; ++it) {
+                                        const Bucket4 o = probe_bucket4(sbase, bkt, k[i], ovf);
+                                        if (c == 0) f = o.first;
+                                        c += o.cnt;
+                                        if (o.end) break;
+                                        bkt = bkt + 1 == nb ? 0 : bkt + 1;
+                                    }
+                                } else {
+                                    for (uint32_t it = 0; it < nb; ++it) {
+                                        SmemBucket<W> bk;
+                                        bk.load(sbase, bkt);
+                                        const bool e0 = SP::empty(bk.a), e1 = SP::empty(bk.b);
+                                        const bool m0 = !e0 && SP::key(bk.a) == k[i], m1 = !e1 && SP::key(bk.b) == k[i];
+                                        if (c == 0) f = m0 ? SP::rid(bk.a) : SP::rid(bk.b);
+                                        c += (uint32_t)m0 + (uint32_t)m1;
+                                        bool end = e0 | e1;
+                                        if (!end) end = !((ovf[bkt >> 5] >> (bkt & 31)) & 1u);
+                                        if (end) break;
+                                        bkt = bkt + 1 == nb ? 0 : bkt + 1;
+                                    }
+                                }
+                                if (k[i] == Tup<W>::kAllOnes && nall) {
+                                    if (c == 0) f = Tup<W>::kAllOnes;
+                                    c += (uint32_t)nall;
+                                }
+                                if (chk && c) {  // checksums over every match (rare second walk)
+                                    const uint64_t bs = mix_b(r[i]);
+                                    ptab.lookup(k[i], h, [&](T rid) {
+                                        const uint64_t a = mix_a(rid);
+                                        acc.c0 += a * bs;
+                                        acc.c1 += a + bs;
+                                    });
+                                }
+                            }
+                            cnt[i] = c;
+                            first[i] = f;
+                        }
+                        // one append for every single-match tuple of the group
+                        unsigned m[IT], tot = 0;
+#pragma unroll
+                        for (int i = 0; i < IT; ++i) {
+                            m[i] = __ballot_sync(0xffffffffu, cnt[i] == 1);
+                            tot += __popc(m[i]);
+                        }
+                        if (tot) {
+                            const unsigned room = kChunkPairs - st.used;
+                            unsigned long long nbase = 0;
+                            if (tot > room) {
+                                if (lane == 0) nbase = atomicAdd(&ctr->cursor, (unsigned long long)kChunkPairs);
+                                nbase = __shfl_sync(0xffffffffu, nbase, 0);
+                            }
+                            unsigned run = 0;
+#pragma unroll
+                            for (int i = 0; i < IT; ++i) {
+                                if (cnt[i] == 1) {
+                                    const unsigned rank = run + __popc(m[i] & lt);
+                                    const unsigned long long pos =
+                                        rank < room ? st.base + st.used + rank : nbase + (rank - room);
+                                    if (pos < pcap) PairOut<W>::put(pairs, pos, first[i], r[i]);
+                                }
+                                run += __popc(m[i]);
+                            }
+                            if (tot > room) {
+                                st.base = nbase;
+                                st.used = tot - room;
+                                st.claimed = true;
+                            } else {
+                                st.used += tot;
+                            }
+                            st.pairs += tot;
+                        }
+                        // several matches: the whole warp walks each such key's run
+#pragma unroll
+                        for (int i = 0; i < IT; ++i) {
+                            unsigned multi = __ballot_sync(0xffffffffu, cnt[i] > 1);
+                            while (multi) {
+                                const int L = __ffs(multi) - 1;
+                                multi &= multi - 1;
+                                const T kk = __shfl_sync(0xffffffffu, k[i], L);
+                                const T ss = __shfl_sync(0xffffffffu, r[i], L);
+                                ptab.coop_emit(kk, ss, st, oc);
+                            }
+                        }
+                    }
+#pragma unroll
+                    for (int u = 0; u < U; ++u) cur[u] = nxt[u];
+                }
             }
         }
-        if constexpr (AGG) {
-            probe_tile_agg<W, IT>(av, k, r, valid, chk != 0, cnt, c0, c1);
-        } else {
-            probe_tile_pairs<W, IT>(pv, k, r, valid, pairs, pcap, ctr, chk != 0, c0, c1, es);
-        }
+        __syncthreads();  // every warp is done with this table and with s_p
     }
-    flush_sums(ctr, cnt, c0, c1, AGG);
+    if constexpr (!AGG) warp_finish(st, oc, ra);
+    flush_acc(ctr, acc, AGG);
 }
+
+// Join launch shape: two 512-thread CTAs per SM with tables up to 100 KiB, or one
+// 1024-thread CTA per SM with up to 200 KiB when the expected build partition
+// needs the room (load factor about 1/3 either way).
+struct JoinCfg {
+    int nt;
+    uint64_t smem_limit;
+};
+static JoinCfg join_cfg(int width, int agg, uint64_t expect_r) {
+    const uint64_t slot = agg ? (width == 4 ? sizeof(AggSlot<4>) : sizeof(AggSlot<8>)) : 2ull * width;
+    const uint64_t need = 3 * (expect_r + 6 * (uint64_t)__builtin_sqrt((double)expect_r + 1.0) + 64) * slot;
+    if (need <= (100ull << 10)) return JoinCfg{512, 100ull << 10};
+    return JoinCfg{1024, 200ull << 10};
+}
+
+uint64_t partition_join_warps(hj_ctx *c) { return (uint64_t)num_sms(c) * 32; }
 
 hj_status partition_join(hj_ctx *c, int width, int agg, const void *Rp, const uint64_t *roff, uint64_t nR_total,
                          const void *Sp, const uint64_t *soff, uint64_t nS_total, uint64_t nparts,
-                         uint64_t expect_r, void *pairs, uint64_t pcap, int checksum, uint32_t *oversize) {
+                         uint64_t expect_r, void *pairs, uint64_t pcap, int checksum, uint32_t *oversize,
+                         RecArea ra, int b1, int b2, int filter) {
+    (void)nR_total;
+    (void)nS_total;
+    (void)filter;
     if (nparts == 0) return HJ_OK;
-    uint64_t slot_bytes = agg ? (width == 4 ? sizeof(AggSlot<4>) : sizeof(AggSlot<8>)) : 2ull * width;
-    // Table capacity for the launch: room for a partition of the expected size
-    // plus six standard deviations, at load factor 1/2; at most 160 KiB.
-    double mean = (double)expect_r;
-    uint64_t want = (uint64_t)(2.0 * (mean + 6.0 * __builtin_sqrt(mean + 1.0) + 64.0));
-    want = ((want + 31) / 32) * 32;
-    uint64_t max_slots = (160ull << 10) / slot_bytes;
+    const uint64_t slot_bytes = agg ? (width == 4 ? sizeof(AggSlot<4>) : sizeof(AggSlot<8>)) : 2ull * width;
+    const JoinCfg cfg = join_cfg(width, agg, expect_r);
+    // Capacity: room for a partition of the expected size plus six standard
+    // deviations at load factor 1/3 (whole buckets), within the shape's budget.
+    const double mean = (double)expect_r;
+    uint64_t want = (uint64_t)(3.0 * (mean + 6.0 * __builtin_sqrt(mean + 1.0) + 64.0));
+    want = (want + 127) / 128 * 128;
+    const uint64_t bitmap_bytes = 4096;
+    uint64_t max_slots = (cfg.smem_limit - bitmap_bytes) / slot_bytes / 128 * 128;
     uint64_t cap_max = want < max_slots ? want : max_slots;
-    if (cap_max < 64) cap_max = 64;
-    size_t smem = (size_t)(cap_max * slot_bytes);
-    const int block = 512;
-    unsigned grid = (unsigned)nparts;
-#define HJ_PJ(WW, AA)                                                                                       \
+    if (cap_max < 128) cap_max = 128;
+    const size_t smem = (size_t)(cap_max * slot_bytes) + (size_t)((cap_max / 2 / 32 + 1) * 4 + 16);
+    unsigned grid = (unsigned)(num_sms(c) * (2048 / cfg.nt / 2));
+    if (grid > nparts) grid = (unsigned)nparts;
+#define HJ_PJ(WW, AA, NT)                                                                                   \
     do {                                                                                                    \
-        auto kern = partition_join_kernel<WW, AA>;                                                          \
+        auto kern = partition_join_kernel<WW, AA, NT>;                                                      \
         HJ_CUDA(c, cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));     \
-        HJ_LAUNCH(c, "partition_join", kern, grid, block, smem, Rp, roff, nR_total, Sp, soff, nS_total,     \
-                  cap_max, pairs, pcap, c->d_ctr, oversize, checksum);                                      \
+        HJ_LAUNCH(c, "partition_join", kern, grid, NT, smem, Rp, roff, Sp, soff, nparts, (uint32_t)cap_max, \
+                  pairs, pcap, ra, c->d_ctr, oversize, checksum, b1, b2);                                   \
     } while (0)
     if (width == 4) {
-        if (agg) HJ_PJ(4, true); else HJ_PJ(4, false);
+        if (agg) { if (cfg.nt == 512) HJ_PJ(4, true, 512); else HJ_PJ(4, true, 1024); }
+        else { if (cfg.nt == 512) HJ_PJ(4, false, 512); else HJ_PJ(4, false, 1024); }
     } else {
-        if (agg) HJ_PJ(8, true); else HJ_PJ(8, false);
+        if (agg) { if (cfg.nt == 512) HJ_PJ(8, true, 512); else HJ_PJ(8, true, 1024); }
+        else { if (cfg.nt == 512) HJ_PJ(8, false, 512); else HJ_PJ(8, false, 1024); }
     }
 #undef HJ_PJ
     return HJ_OK;

@@ -108,27 +108,15 @@ __device__ __forceinline__ uint64_t seg_of_chunk(const unsigned long long *cb, u
     return lo;
 }
 
-// Warp-aggregated shared-memory increment: lanes with equal digits add once;
-// returns this lane's rank among the tuples counted for `d` so far.
-__device__ __forceinline__ uint32_t agg_rank(uint32_t *cnt, uint32_t d, bool active) {
-    unsigned mask = __ballot_sync(0xffffffffu, active);
-    uint32_t rank = 0;
-    if (active) {
-        unsigned peers = __match_any_sync(mask, d);
-        int leader = __ffs(peers) - 1;
-        int lane = threadIdx.x & 31;
-        uint32_t base = 0;
-        if (lane == leader) base = atomicAdd(&cnt[d], (uint32_t)__popc(peers));
-        base = __shfl_sync(peers, base, leader);
-        rank = base + __popc(peers & ((1u << lane) - 1u));
-    }
-    return rank;
+// Shared-memory increment of digit d's counter; returns this tuple's rank among
+// the tuples of digit d counted so far (order among equal digits is free).
+__device__ __forceinline__ uint32_t digit_rank(uint32_t *cnt, uint32_t d, bool active) {
+    return active ? atomicAdd(&cnt[d], 1u) : 0u;
 }
 
-template <int W> struct PartShape {
-    static constexpr int PV = Tup<W>::kPerVec;
-    static constexpr int VPT = 4;             // vectors per thread per tile
-    static constexpr int IT = VPT * PV;       // tuples per thread per tile
+// Tuples of W-byte fields per 32-byte sector: the unit the scatter writes whole.
+template <int W> struct Sector {
+    static constexpr int kTuples = 32 / (2 * W);
 };
 
 template <int W> __device__ __forceinline__ void load_vec_p(const void *base, uint64_t v, uint64_t n_total,
@@ -148,178 +136,375 @@ template <int W> __device__ __forceinline__ void load_vec_p(const void *base, ui
     }
 }
 
+// Chunk g of the pass: its segment, index within the segment, and row range.
+struct ChunkPos {
+    uint64_t s, cidx, nch, lo, hi;
+};
+__device__ __forceinline__ ChunkPos chunk_pos(const uint64_t *seg_off, uint64_t nseg, const unsigned long long *cb,
+                                              uint64_t chunk, uint64_t g) {
+    ChunkPos c;
+    c.s = seg_of_chunk(cb, nseg, g);
+    c.cidx = g - cb[c.s];
+    c.nch = cb[c.s + 1] - cb[c.s];
+    c.lo = seg_off[c.s] + c.cidx * chunk;
+    c.hi = min(c.lo + chunk, (uint64_t)seg_off[c.s + 1]);
+    return c;
+}
+
 // ------------------------------------------------------------------- hist
+// Counts per (chunk, digit); with `pad` each count is rounded up to whole sectors
+// so that every (chunk, digit) run of the scatter starts on a sector boundary.
+constexpr int kHistThreads = 1024;
+constexpr int kHistUnroll = 4;
+
 template <int W>
-__global__ void __launch_bounds__(512) hist_kernel(const void *in, uint64_t n_total, const uint64_t *seg_off,
-                                                   uint64_t nseg, const unsigned long long *cb, uint64_t chunk,
-                                                   int shift, int bits, uint32_t *H) {
+__global__ void __launch_bounds__(kHistThreads) hist_kernel(const void *in, uint64_t n_total, const uint64_t *seg_off,
+                                                            uint64_t nseg, const unsigned long long *cb,
+                                                            uint64_t chunk, int shift, int bits, int pad,
+                                                            uint32_t *H) {
     using U = typename Tup<W>::U;
-    constexpr int PV = Tup<W>::kPerVec;
+    constexpr int PV = Tup<W>::kPerVec, SV = Sector<W>::kTuples;
     extern __shared__ uint32_t hist[];
     const uint32_t P = 1u << bits;
     const uint64_t g = blockIdx.x;
     for (uint32_t d = threadIdx.x; d < P; d += blockDim.x) hist[d] = 0;
-    const uint64_t total = cb[nseg];
-    if (g >= total) {  // spare chunk id: its H row lies past every real row
+    if (g >= cb[nseg]) {  // spare chunk id: its H row lies past every real row
         for (uint32_t d = threadIdx.x; d < P; d += blockDim.x) H[g * P + d] = 0;
         return;
     }
-    const uint64_t s = seg_of_chunk(cb, nseg, g);
-    const uint64_t cidx = g - cb[s], nch = cb[s + 1] - cb[s];
-    const uint64_t lo = seg_off[s] + cidx * chunk;
-    const uint64_t hi = min(lo + chunk, (uint64_t)seg_off[s + 1]);
+    const ChunkPos cp = chunk_pos(seg_off, nseg, cb, chunk, g);
     __syncthreads();
-    const uint64_t va = lo / PV, vb = (hi + PV - 1) / PV;
-    constexpr int UNR = 4;
-    for (uint64_t v0 = va; v0 < vb; v0 += (uint64_t)blockDim.x * UNR) {
-        U k[UNR][2], r[UNR][2];
+    const uint64_t va = cp.lo / PV, vb = (cp.hi + PV - 1) / PV;
+    const uint64_t step = (uint64_t)blockDim.x * kHistUnroll;
+    U k[kHistUnroll][2], r[kHistUnroll][2], nk[kHistUnroll][2], nr[kHistUnroll][2];
+    auto load = [&](uint64_t v0, U (*kk)[2], U (*rr)[2]) {
 #pragma unroll
-        for (int u = 0; u < UNR; ++u) {
+        for (int u = 0; u < kHistUnroll; ++u) {
             uint64_t v = v0 + (uint64_t)u * blockDim.x + threadIdx.x;
-            k[u][0] = k[u][1] = 0;
-            if (v < vb) load_vec_p<W>(in, v, n_total, k[u], r[u]);
+            kk[u][0] = kk[u][1] = 0;
+            if (v < vb) load_vec_p<W>(in, v, n_total, kk[u], rr[u]);
         }
+    };
+    if (va < vb) load(va, k, r);
+    for (uint64_t v0 = va; v0 < vb; v0 += step) {
+        if (v0 + step < vb) load(v0 + step, nk, nr);
 #pragma unroll
-        for (int u = 0; u < UNR; ++u) {
+        for (int u = 0; u < kHistUnroll; ++u) {
             uint64_t v = v0 + (uint64_t)u * blockDim.x + threadIdx.x;
 #pragma unroll
             for (int e = 0; e < PV; ++e) {
                 uint64_t t = v * PV + e;
-                bool act = v < vb && t >= lo && t < hi;
-                uint32_t d = digit_of(key_hash<W>(k[u][e]), shift, bits);
-                agg_rank(hist, d, act);
+                if (v < vb && t >= cp.lo && t < cp.hi) atomicAdd(&hist[digit_of(key_hash<W>(k[u][e]), shift, bits)], 1u);
             }
+        }
+#pragma unroll
+        for (int u = 0; u < kHistUnroll; ++u) {
+            k[u][0] = nk[u][0];
+            k[u][1] = nk[u][1];
         }
     }
     __syncthreads();
-    const uint64_t row = cb[s] * P;
-    for (uint32_t d = threadIdx.x; d < P; d += blockDim.x) H[row + (uint64_t)d * nch + cidx] = hist[d];
+    const uint64_t row = cb[cp.s] * P;
+    for (uint32_t d = threadIdx.x; d < P; d += blockDim.x) {
+        uint32_t n = hist[d];
+        if (pad) n = (n + SV - 1) / SV * SV;
+        H[row + (uint64_t)d * cp.nch + cp.cidx] = n;
+    }
 }
 
 __global__ void extract_offsets_kernel(const uint64_t *seg_off, uint64_t nseg, const unsigned long long *cb,
-                                       const unsigned long long *Hs, int bits, uint64_t *part_off) {
+                                       const unsigned long long *Hs, int bits, uint64_t *part_off,
+                                       uint64_t total_rows_plus_base) {
     const uint64_t P = 1ull << bits, n = nseg * P;
     for (uint64_t i = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; i <= n; i += (uint64_t)gridDim.x * blockDim.x) {
         if (i == n) {
-            part_off[i] = seg_off[nseg];
+            part_off[i] = total_rows_plus_base ? seg_off[0] + Hs[cb[nseg] * P] : seg_off[nseg];
             continue;
         }
         uint64_t s = i >> bits, d = i & (P - 1);
         uint64_t nch = cb[s + 1] - cb[s];
-        part_off[i] = nch ? seg_off[0] + Hs[cb[s] * P + d * nch] : seg_off[s];
+        // an empty segment starts where the padded output of the segments before it ends
+        part_off[i] = seg_off[0] + (nch ? Hs[cb[s] * P + d * nch] : Hs[cb[s] * P]);
     }
 }
 
 // ----------------------------------------------------------------- scatter
+// One CTA per chunk.  Tile by tile (the next tile's vectors are loaded before the
+// current one is processed):
+//   1. digit of every tuple, its rank within the digit (shared-memory atomics);
+//   2. per digit: the tile count n, the carried count c (tuples of earlier tiles
+//      short of a whole sector), and the rows [gcur, bnd) that now complete whole
+//      sectors; one block scan gives both the tile offsets and a list of
+//      "units" -- the 32-byte output sectors to write this tile;
+//   3. tuples placed in a digit-sorted shared buffer;
+//   4. one thread per unit gathers its sector (carry first, then tile tuples) and
+//      writes it with a single 32-byte store;
+//   5. tuples past the last whole sector become the digit's new carry.
+// Every global write is therefore a whole sector written by one instruction,
+// except the first sector of a run that starts unaligned.  With `pad`, runs start
+// aligned and each run's last sector is completed with padding tuples whose key
+// hashes to another digit, so all writes are whole sectors.
 template <int W> struct SortSlot { using T = unsigned long long; };
 template <> struct SortSlot<8> { using T = ulonglong2; };
 
-template <int W>
-__global__ void __launch_bounds__(512) scatter_kernel(const void *in, uint64_t n_total, const uint64_t *seg_off,
-                                                      uint64_t nseg, const unsigned long long *cb, uint64_t chunk,
-                                                      int shift, int bits, const unsigned long long *Hs, void *out) {
+// NT threads, VPT 16-byte vectors per thread per tile.
+template <int W, int NT, int VPT_> struct ScatterShape {
+    static constexpr int PV = Tup<W>::kPerVec;
+    static constexpr int VPT = VPT_;
+    static constexpr int IT = VPT * PV;           // tuples per thread per tile
+    static constexpr int T = NT * IT;             // tuples per tile
+    static constexpr int SV = Sector<W>::kTuples;
+};
+
+template <int W, int NT, int VPT>
+__host__ __device__ inline size_t scatter_smem_bytes(uint32_t P) {
+    using SS = ScatterShape<W, NT, VPT>;
+    size_t slot = 2 * W;
+    size_t b = (size_t)SS::T * slot                 // buf: the digit-sorted tile
+               + (size_t)P * (SS::SV - 1) * slot    // carry: tuples short of a sector
+               + (size_t)P * 4                      // gcur: next output row per digit (segment-relative)
+               + (size_t)P * 4                      // lcnt: tile count per digit
+               + (size_t)P * 4                      // oc: o | c_old << 16 per digit
+               + ((size_t)P + 1) * 2                // loff: tile offset per digit
+               + (size_t)P * 2                      // uoff: first unit per digit
+               + ((size_t)SS::T / SS::SV + 2 * (size_t)P) * 2   // udig: digit of each unit
+               + (size_t)P;                         // ccount: carried tuples per digit
+    return (b + 15) & ~size_t(15);
+}
+
+// Whole-sector store: 32 bytes from one thread.
+__device__ __forceinline__ void st_sector(void *p, const unsigned long long *t4) {
+    asm volatile("st.global.v4.u64 [%0], {%1, %2, %3, %4};" ::"l"(p), "l"(t4[0]), "l"(t4[1]), "l"(t4[2]),
+                 "l"(t4[3])
+                 : "memory");
+}
+
+template <int W, int NT, int VPT_>
+__global__ void __launch_bounds__(NT) scatter_kernel(const void *in, uint64_t n_total,
+                                                                  const uint64_t *seg_off, uint64_t nseg,
+                                                                  const unsigned long long *cb, uint64_t chunk,
+                                                                  int shift, int bits, const unsigned long long *Hs,
+                                                                  void *out, int pad, uint64_t sent_k0,
+                                                                  uint64_t sent_k1) {
     using U = typename Tup<W>::U;
-    using PS = PartShape<W>;
+    using SS = ScatterShape<W, NT, VPT_>;
     using Slot = typename SortSlot<W>::T;
-    constexpr int PV = PS::PV, VPT = PS::VPT, IT = PS::IT;
+    constexpr int PV = SS::PV, VPT = SS::VPT, IT = SS::IT, SV = SS::SV;
     const uint32_t P = 1u << bits;
-    const uint32_t T = blockDim.x * IT;
     extern __shared__ __align__(16) unsigned char smem[];
-    Slot *buf = (Slot *)smem;                                        // T tuples
-    unsigned long long *gcur = (unsigned long long *)(buf + T);      // P running output rows
-    uint32_t *lcnt = (uint32_t *)(gcur + P);                         // P tile counts
-    uint32_t *loff = lcnt + P;                                       // P + 1 tile offsets
-    uint16_t *dig = (uint16_t *)(loff + P + 1);                      // T digits (sorted order)
+    Slot *buf = (Slot *)smem;                                          // T
+    Slot *carry = buf + SS::T;                                         // P * (SV - 1)
+    uint32_t *gcur = (uint32_t *)(carry + (size_t)P * (SV - 1));       // P
+    uint32_t *lcnt = gcur + P;                                         // P
+    uint32_t *oc = lcnt + P;                                           // P
+    uint16_t *loff = (uint16_t *)(oc + P);                             // P + 1
+    uint16_t *uoff = loff + P + 1;                                     // P
+    uint16_t *udig = uoff + P;                                         // T / SV + P
+    uint8_t *ccount = (uint8_t *)(udig + SS::T / SV + 2 * P);          // P
     __shared__ uint32_t sc[33];
+    __shared__ uint32_t s_nunits;
 
     const uint64_t g = blockIdx.x;
     if (g >= cb[nseg]) return;
-    const uint64_t s = seg_of_chunk(cb, nseg, g);
-    const uint64_t cidx = g - cb[s], nch = cb[s + 1] - cb[s];
-    const uint64_t lo = seg_off[s] + cidx * chunk;
-    const uint64_t hi = min(lo + chunk, (uint64_t)seg_off[s + 1]);
-    const uint64_t row = cb[s] * P;
+    const ChunkPos cp = chunk_pos(seg_off, nseg, cb, chunk, g);
+    const uint64_t row = cb[cp.s] * P;
+    // Cursors are kept relative to `obase`, the segment's first output row rounded
+    // down to a sector, so that sector boundaries are the same absolute and relative.
+    const uint64_t seg_start = seg_off[0] + Hs[row];
+    const uint64_t obase = seg_start / SV * SV;
+    Slot *outp = (Slot *)out + obase;
     for (uint32_t d = threadIdx.x; d < P; d += blockDim.x) {
-        gcur[d] = seg_off[0] + Hs[row + (uint64_t)d * nch + cidx];
+        gcur[d] = (uint32_t)(seg_off[0] + Hs[row + (uint64_t)d * cp.nch + cp.cidx] - obase);
         lcnt[d] = 0;
+        ccount[d] = 0;
     }
     __syncthreads();
-    const uint32_t ept = (P + blockDim.x - 1) / blockDim.x;  // digits per thread in the tile scan
-    const uint64_t va = lo / PV, vb = (hi + PV - 1) / PV;
+    const uint32_t ept = (P + blockDim.x - 1) / blockDim.x;
+    const uint64_t va = cp.lo / PV, vb = (cp.hi + PV - 1) / PV;
     const uint64_t tile_vecs = (uint64_t)blockDim.x * VPT;
+
+    U k[IT], r[IT], nk[IT], nr[IT];
+    auto load_tile = [&](uint64_t base, U *kk, U *rr) {
+#pragma unroll
+        for (int j = 0; j < VPT; ++j) {
+            uint64_t v = base + (uint64_t)j * blockDim.x + threadIdx.x;
+            U a[2] = {0, 0}, b[2] = {0, 0};
+            if (v < vb) load_vec_p<W>(in, v, n_total, a, b);
+#pragma unroll
+            for (int e = 0; e < PV; ++e) {
+                kk[j * PV + e] = a[e];
+                rr[j * PV + e] = b[e];
+            }
+        }
+    };
+    if (va < vb) load_tile(va, k, r);
     for (uint64_t base = va; base < vb; base += tile_vecs) {
-        U k[IT], r[IT];
+        if (base + tile_vecs < vb) load_tile(base + tile_vecs, nk, nr);
+        // 1. digits and ranks
         uint32_t d[IT], rk[IT];
         bool act[IT];
 #pragma unroll
         for (int j = 0; j < VPT; ++j) {
-            uint64_t v = base + (uint64_t)j * blockDim.x + threadIdx.x;
-            U kk[2] = {0, 0}, rr[2] = {0, 0};
-            if (v < vb) load_vec_p<W>(in, v, n_total, kk, rr);
 #pragma unroll
             for (int e = 0; e < PV; ++e) {
-                uint64_t t = v * PV + e;
-                k[j * PV + e] = kk[e];
-                r[j * PV + e] = rr[e];
-                act[j * PV + e] = v < vb && t >= lo && t < hi;
+                const int i = j * PV + e;
+                const uint64_t v = base + (uint64_t)j * blockDim.x + threadIdx.x;
+                const uint64_t t = v * PV + e;
+                act[i] = v < vb && t >= cp.lo && t < cp.hi;
+                d[i] = digit_of(key_hash<W>(k[i]), shift, bits);
+                rk[i] = act[i] ? atomicAdd(&lcnt[d[i]], 1u) : 0u;
             }
         }
-#pragma unroll
-        for (int i = 0; i < IT; ++i) {
-            d[i] = digit_of(key_hash<W>(k[i]), shift, bits);
-            rk[i] = agg_rank(lcnt, d[i], act[i]);
-        }
         __syncthreads();
-        // exclusive scan of the tile's digit counts
+        // 2. tile offsets and output units (n in the low half, units in the high half)
         {
-            uint32_t d0 = threadIdx.x * ept, sum = 0;
-            for (uint32_t q = 0; q < ept; ++q)
-                if (d0 + q < P) sum += lcnt[d0 + q];
+            const uint32_t d0 = threadIdx.x * ept;
+            uint32_t sum = 0;
+            for (uint32_t q = 0; q < ept; ++q) {
+                const uint32_t dd = d0 + q;
+                if (dd >= P) break;
+                const uint32_t n = lcnt[dd], c = ccount[dd], gc = gcur[dd];
+                const uint32_t bnd = (gc + c + n) / SV * SV;
+                const uint32_t nu = bnd > gc ? bnd / SV - gc / SV : 0u;
+                sum += n | (nu << 16);
+            }
             uint32_t tot;
             uint32_t ex = block_exclusive_scan<uint32_t>(sum, sc, &tot);
-            for (uint32_t q = 0; q < ept; ++q)
-                if (d0 + q < P) {
-                    loff[d0 + q] = ex;
-                    ex += lcnt[d0 + q];
-                }
-            if (threadIdx.x == 0) loff[P] = tot;
+            for (uint32_t q = 0; q < ept; ++q) {
+                const uint32_t dd = d0 + q;
+                if (dd >= P) break;
+                const uint32_t n = lcnt[dd], c = ccount[dd], gc = gcur[dd];
+                const uint32_t bnd = (gc + c + n) / SV * SV;
+                const uint32_t o = bnd > gc ? bnd - gc : 0u;
+                const uint32_t nu = o ? bnd / SV - gc / SV : 0u;
+                loff[dd] = (uint16_t)(ex & 0xFFFFu);
+                uoff[dd] = (uint16_t)(ex >> 16);
+                for (uint32_t u = 0; u < nu; ++u) udig[(ex >> 16) + u] = (uint16_t)dd;
+                oc[dd] = o | (c << 16);
+                ex += n | (nu << 16);
+            }
+            if (threadIdx.x == 0) {
+                loff[P] = (uint16_t)(tot & 0xFFFFu);
+                s_nunits = tot >> 16;
+            }
         }
         __syncthreads();
+        // 3. digit-sorted tile
 #pragma unroll
         for (int i = 0; i < IT; ++i) {
             if (!act[i]) continue;
-            uint32_t p = loff[d[i]] + rk[i];
+            const uint32_t p = loff[d[i]] + rk[i];
             if constexpr (W == 4) buf[p] = (unsigned long long)k[i] | ((unsigned long long)r[i] << 32);
             else buf[p] = make_ulonglong2(k[i], r[i]);
-            dig[p] = (uint16_t)d[i];
         }
         __syncthreads();
-        const uint32_t nv = loff[P];
-        for (uint32_t p = threadIdx.x; p < nv; p += blockDim.x) {
-            uint32_t dd = dig[p];
-            uint64_t dst = gcur[dd] + (p - loff[dd]);
-            ((Slot *)out)[dst] = buf[p];
+        // 4. one thread per output sector
+        const uint32_t nunits = s_nunits;
+        for (uint32_t ui = threadIdx.x; ui < nunits; ui += blockDim.x) {
+            const uint32_t dd = udig[ui];
+            const uint32_t ocv = oc[dd], c = ocv >> 16;
+            const uint32_t gc = gcur[dd];
+            const uint32_t sec = gc / SV + (ui - uoff[dd]);
+            const uint32_t row0 = sec * SV > gc ? sec * SV : gc;
+            const Slot *cy = carry + (size_t)dd * (SV - 1);
+            const uint32_t lo_t = loff[dd];
+            Slot tup[SV];
+#pragma unroll
+            for (int q = 0; q < SV; ++q) {
+                const uint32_t rr = sec * SV + q;
+                const uint32_t j = rr - gc;   // position in carry ++ tile run (valid when rr >= gc)
+                if (rr >= row0) tup[q] = j < c ? cy[j] : buf[lo_t + j - c];
+            }
+            if (row0 == sec * SV) {
+                st_sector(outp + (size_t)sec * SV, (const unsigned long long *)tup);
+            } else {
+                for (uint32_t q = row0 - sec * SV; q < (uint32_t)SV; ++q) outp[(size_t)sec * SV + q] = tup[q];
+            }
         }
         __syncthreads();
-        for (uint32_t q = threadIdx.x; q < P; q += blockDim.x) {
-            gcur[q] += lcnt[q];
-            lcnt[q] = 0;
+        // 5. new carries, cursors
+        for (uint32_t dd = threadIdx.x; dd < P; dd += blockDim.x) {
+            const uint32_t ocv = oc[dd], o = ocv & 0xFFFFu, c = ocv >> 16, n = lcnt[dd];
+            Slot *cy = carry + (size_t)dd * (SV - 1);
+            for (uint32_t j = (o > c ? o : c); j < c + n; ++j) cy[j - o] = buf[loff[dd] + (j - c)];
+            gcur[dd] += o;
+            ccount[dd] = (uint8_t)(c + n - o);
+            lcnt[dd] = 0;
         }
         __syncthreads();
+#pragma unroll
+        for (int i = 0; i < IT; ++i) {
+            k[i] = nk[i];
+            r[i] = nr[i];
+        }
+    }
+    // final carries; with pad, padding tuples complete each run's last sector
+    for (uint32_t dd = threadIdx.x; dd < P; dd += blockDim.x) {
+        const uint32_t c = ccount[dd], gc = gcur[dd];
+        const Slot *cy = carry + (size_t)dd * (SV - 1);
+        if (pad) {
+            if (c == 0) continue;
+            const uint64_t sk = digit_of(key_hash<W>((U)sent_k0), shift, bits) != dd ? sent_k0 : sent_k1;
+            Slot tup[SV];
+#pragma unroll
+            for (int q = 0; q < SV; ++q) {
+                if ((uint32_t)q < c) tup[q] = cy[q];
+                else if constexpr (W == 4) tup[q] = (unsigned long long)(uint32_t)sk;
+                else tup[q] = make_ulonglong2(sk, 0ull);
+            }
+            st_sector(outp + gc, (const unsigned long long *)tup);
+        } else {
+            for (uint32_t j = 0; j < c; ++j) outp[gc + j] = cy[j];
+        }
     }
 }
 
 // ------------------------------------------------------------------- driver
 
+// Scatter configuration (threads, vectors per thread) for a fan-out: 8192-tuple
+// tiles of 4-byte tuples while the per-digit state leaves room, 4096 otherwise.
+struct ScatterCfg {
+    int nt, vpt;
+    uint64_t tile;
+};
+static ScatterCfg scatter_cfg(int width, int bits) {
+    if (width == 4) return bits <= 11 ? ScatterCfg{512, 8, 8192} : ScatterCfg{1024, 2, 4096};
+    return bits <= 11 ? ScatterCfg{512, 4, 2048} : ScatterCfg{1024, 2, 2048};
+}
+
+uint64_t partition_out_rows(hj_ctx *c, int width, uint64_t n_total, uint64_t nseg, int bits, int pad) {
+    if (!pad) return n_total;
+    const uint64_t tile = scatter_cfg(width, bits).tile;
+    uint64_t target = (uint64_t)num_sms(c);
+    uint64_t chunk = (n_total + target - 1) / (target ? target : 1);
+    chunk = ((chunk + tile - 1) / tile) * tile;
+    if (chunk < tile) chunk = tile;
+    const uint64_t max_chunks = (n_total + chunk - 1) / chunk + nseg;
+    const uint64_t sv = 32 / (2 * width);
+    return n_total + max_chunks * (1ull << bits) * (sv - 1);
+}
+
+// Two sentinel keys for a pass: 0, and the first key whose digit differs from 0's.
+static void sentinel_keys(int width, int shift, int bits, uint64_t *k0, uint64_t *k1) {
+    auto dg = [&](uint64_t k) {
+        uint64_t h = width == 4 ? (uint64_t)murmur2_u32((uint32_t)k) : murmur2_u64(k);
+        return (h >> shift) & ((1ull << bits) - 1);
+    };
+    *k0 = 0;
+    uint64_t k = 1;
+    while (dg(k) == dg(0)) ++k;
+    *k1 = k;
+}
+
 hj_status partition_pass(hj_ctx *c, int width, const void *in, uint64_t n_total, const uint64_t *seg_off,
-                         uint64_t nseg, int shift, int bits, void *out, uint64_t *part_off) {
+                         uint64_t nseg, int shift, int bits, void *out, uint64_t *part_off, int pad) {
     if (bits < 1 || bits > 12) return set_err(c, HJ_E_INVALID, "partition pass bits %d outside [1, 12]", bits);
     const uint64_t P = 1ull << bits;
-    const int block = 512;
-    const uint64_t tile = (uint64_t)block * (width == 4 ? PartShape<4>::IT : PartShape<8>::IT);
-    // Chunk size: about two chunks per SM over the whole input, a multiple of the
-    // scatter tile, at least one tile.
-    uint64_t target = (uint64_t)num_sms(c) * 2;
+    const ScatterCfg cfg = scatter_cfg(width, bits);
+    const uint64_t tile = cfg.tile;
+    // Chunk size: about one chunk per SM over the whole input (one scatter CTA
+    // fits an SM at the largest fan-out), a multiple of the scatter tile.
+    uint64_t target = (uint64_t)num_sms(c);
     uint64_t chunk = (n_total + target - 1) / (target ? target : 1);
     chunk = ((chunk + tile - 1) / tile) * tile;
     if (chunk < tile) chunk = tile;
@@ -338,25 +523,32 @@ hj_status partition_pass(hj_ctx *c, int width, const void *in, uint64_t n_total,
     HJ_TRY(scan_u32_u64(c, nch, nseg, cb));
     size_t hsmem = P * 4;
     if (width == 4)
-        HJ_LAUNCH(c, "partition_hist", hist_kernel<4>, (unsigned)max_chunks, block, hsmem, in, n_total, seg_off, nseg, cb, chunk, shift, bits, H);
+        HJ_LAUNCH(c, "partition_hist", hist_kernel<4>, (unsigned)max_chunks, kHistThreads, hsmem, in, n_total, seg_off, nseg, cb, chunk, shift, bits, pad, H);
     else
-        HJ_LAUNCH(c, "partition_hist", hist_kernel<8>, (unsigned)max_chunks, block, hsmem, in, n_total, seg_off, nseg, cb, chunk, shift, bits, H);
+        HJ_LAUNCH(c, "partition_hist", hist_kernel<8>, (unsigned)max_chunks, kHistThreads, hsmem, in, n_total, seg_off, nseg, cb, chunk, shift, bits, pad, H);
     HJ_TRY(scan_u32_u64(c, H, max_chunks * P, Hs));
     {
         uint64_t n = nseg * P + 1;
         int g = (int)std::min<uint64_t>((n + 255) / 256, (uint64_t)num_sms(c) * 8);
-        HJ_LAUNCH(c, "partition_offsets", extract_offsets_kernel, g, 256, 0, seg_off, nseg, cb, Hs, bits, part_off);
+        HJ_LAUNCH(c, "partition_offsets", extract_offsets_kernel, g, 256, 0, seg_off, nseg, cb, Hs, bits, part_off,
+                  (uint64_t)pad);
     }
-    size_t slot = width == 4 ? 8 : 16;
-    size_t ssmem = tile * slot + P * 8 + P * 4 + (P + 1) * 4 + tile * 2;
-    ssmem = (ssmem + 15) & ~size_t(15);
+    uint64_t k0, k1;
+    sentinel_keys(width, shift, bits, &k0, &k1);
+#define HJ_SC(WW, NT, VPT)                                                                                    \
+    do {                                                                                                      \
+        auto kern = scatter_kernel<WW, NT, VPT>;                                                              \
+        const size_t ssmem = scatter_smem_bytes<WW, NT, VPT>((uint32_t)P);                                    \
+        HJ_CUDA(c, cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)ssmem));      \
+        HJ_LAUNCH(c, "partition_scatter", kern, (unsigned)max_chunks, NT, ssmem, in, n_total, seg_off, nseg, cb, \
+                  chunk, shift, bits, Hs, out, pad, k0, k1);                                                  \
+    } while (0)
     if (width == 4) {
-        HJ_CUDA(c, cudaFuncSetAttribute(scatter_kernel<4>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)ssmem));
-        HJ_LAUNCH(c, "partition_scatter", scatter_kernel<4>, (unsigned)max_chunks, block, ssmem, in, n_total, seg_off, nseg, cb, chunk, shift, bits, Hs, out);
+        if (cfg.nt == 512) HJ_SC(4, 512, 8); else HJ_SC(4, 1024, 2);
     } else {
-        HJ_CUDA(c, cudaFuncSetAttribute(scatter_kernel<8>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)ssmem));
-        HJ_LAUNCH(c, "partition_scatter", scatter_kernel<8>, (unsigned)max_chunks, block, ssmem, in, n_total, seg_off, nseg, cb, chunk, shift, bits, Hs, out);
+        if (cfg.nt == 512) HJ_SC(8, 512, 4); else HJ_SC(8, 1024, 2);
     }
+#undef HJ_SC
     return HJ_OK;
 }
 
