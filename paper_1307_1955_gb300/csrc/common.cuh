@@ -105,9 +105,8 @@ struct PartFilter {
     int b1, b2, on;
     __device__ __forceinline__ bool keep(uint64_t h) const {
         if (!on) return true;
-        const uint32_t d1 = (uint32_t)h & ((1u << b1) - 1u);
-        const uint32_t d2 = b2 ? ((uint32_t)(h >> b1) & ((1u << b2) - 1u)) : 0u;
-        return ((d1 << b2) | d2) == p;
+        const uint32_t h32 = (uint32_t)h, m1 = (1u << b1) - 1u, m2 = (1u << b2) - 1u;
+        return (((h32 & m1) << b2) | ((h32 >> b1) & m2)) == p;
     }
 };
 
@@ -338,6 +337,38 @@ template <class T> __device__ __forceinline__ T warp_sum(T v) {
 #pragma unroll
     for (int o = 16; o; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
     return v;
+}
+
+// ------------------------------------------------------------- TMA bulk copies
+// One-dimensional bulk copy global -> shared completed on an mbarrier (sm_90+).
+__device__ __forceinline__ void mbar_init(uint32_t bar, uint32_t count) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(bar), "r"(count) : "memory");
+}
+__device__ __forceinline__ void fence_mbar_init() { asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory"); }
+// Order this thread's earlier generic-proxy shared accesses before later async-proxy ones.
+__device__ __forceinline__ void fence_proxy_async() { asm volatile("fence.proxy.async.shared::cta;" ::: "memory"); }
+__device__ __forceinline__ void mbar_expect_tx(uint32_t bar, uint32_t bytes) {
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(bytes) : "memory");
+}
+__device__ __forceinline__ void bulk_g2s(uint32_t dst, const void *src, uint32_t bytes, uint32_t bar) {
+    asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(dst),
+                 "l"(src), "r"(bytes), "r"(bar)
+                 : "memory");
+}
+__device__ __forceinline__ bool mbar_try_wait(uint32_t bar, uint32_t parity) {
+    uint32_t ok;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\tmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\tselp.u32 %0, 1, 0, p;\n\t}"
+        : "=r"(ok)
+        : "r"(bar), "r"(parity)
+        : "memory");
+    return ok != 0;
+}
+// Wait for an mbarrier phase with an iteration limit; false if the limit ran out.
+__device__ __forceinline__ bool mbar_wait_bounded(uint32_t bar, uint32_t parity, uint32_t limit) {
+    for (uint32_t i = 0; i < limit; ++i)
+        if (mbar_try_wait(bar, parity)) return true;
+    return false;
 }
 
 // Status bits written by kernels into the context's device status word.

@@ -413,50 +413,149 @@ template <> struct SmemPair<8> {
     static __device__ __forceinline__ uint64_t rid(ulonglong2 s) { return s.y; }
 };
 
+// Bucket of a key inside a partition's shared-memory table: Fibonacci
+// multiply-shift of the key.  Keys of one partition already share their
+// MurmurHash2 partition digit, so a cheap hash that spreads them is enough here.
+template <int W> __device__ __forceinline__ uint32_t part_bucket(typename Tup<W>::U k, uint32_t nb);
+template <> __device__ __forceinline__ uint32_t part_bucket<4>(uint32_t k, uint32_t nb) {
+    return __umulhi(k * 0x9E3779B1u, nb);
+}
+template <> __device__ __forceinline__ uint32_t part_bucket<8>(uint64_t k, uint32_t nb) {
+    return __umulhi((uint32_t)((k * 0x9E3779B97F4A7C15ull) >> 32), nb);
+}
+
 template <int W>
 __device__ __forceinline__ typename HashT<W>::type hashw(typename Tup<W>::U k) {
     if constexpr (W == 4) return murmur2_u32(k);
     else return murmur2_u64(k);
 }
 
-// Probe of a 4-byte key against one shared-memory bucket of four slots, without
-// branches: match mask, count, first matching rid, whether the run ends here.
-struct Bucket4 {
-    uint32_t cnt, first;
-    bool end;
+// ----------------------------------------------------------- shared-memory table
+// Bucketised open addressing in shared memory for one partition pair.  Bucket b is
+// 32 bytes: G keys, then their G rids (G = 4 for 4-byte tuples, 2 for 8-byte).
+// Every real key of partition p hashes to p, so a key that hashes to another
+// partition can never be stored or probed: it marks empty slots (no value of the
+// key domain needs reserving).  A key's run starts at its home bucket and moves
+// linearly over buckets; a bucket's overflow bit records that some insert moved
+// past it, so a lookup stops at the first bucket that has an empty slot or no
+// overflow bit.
+template <int W> struct SoaTab {
+    using T = typename Tup<W>::U;
+    static constexpr uint32_t G = 16 / W;
+    uint32_t sbase;  // shared address of bucket 0
+    uint32_t nb;     // buckets
+    T empty;
+    const uint32_t *ovf;
+
+    __device__ __forceinline__ bool overflowed(uint32_t b) const { return (ovf[b >> 5] >> (b & 31)) & 1u; }
+    // keys or rids of bucket b (half 0 = keys, half 1 = rids)
+    __device__ __forceinline__ void ld(uint32_t b, uint32_t half, T *v) const {
+        const uint32_t a = sbase + b * 32u + half * 16u;
+        if constexpr (W == 4)
+            asm volatile("ld.shared.v4.u32 {%0, %1, %2, %3}, [%4];" : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]) : "r"(a));
+        else
+            asm volatile("ld.shared.v2.u64 {%0, %1}, [%2];" : "=l"(v[0]), "=l"(v[1]) : "r"(a));
+    }
+    __device__ __forceinline__ T ld1(uint32_t b, uint32_t half, uint32_t q) const {
+        T v;
+        const uint32_t a = sbase + b * 32u + half * 16u + q * (uint32_t)W;
+        if constexpr (W == 4) asm volatile("ld.shared.u32 %0, [%1];" : "=r"(v) : "r"(a));
+        else asm volatile("ld.shared.u64 %0, [%1];" : "=l"(v) : "r"(a));
+        return v;
+    }
 };
-__device__ __forceinline__ Bucket4 probe_bucket4(uint32_t sbase, uint32_t bkt, uint32_t k, const uint32_t *ovf) {
-    ulonglong2 a, b;
-    const uint32_t addr = sbase + bkt * 32u;
-    asm volatile("ld.shared.v2.u64 {%0, %1}, [%2];" : "=l"(a.x), "=l"(a.y) : "r"(addr));
-    asm volatile("ld.shared.v2.u64 {%0, %1}, [%2];" : "=l"(b.x), "=l"(b.y) : "r"(addr + 16u));
-    const uint32_t k0 = (uint32_t)a.x, k1 = (uint32_t)a.y, k2 = (uint32_t)b.x, k3 = (uint32_t)b.y;
-    const uint32_t r0 = (uint32_t)(a.x >> 32), r1 = (uint32_t)(a.y >> 32), r2 = (uint32_t)(b.x >> 32),
-                   r3 = (uint32_t)(b.y >> 32);
-    // a slot is empty iff key and rid are all ones
-    const bool e0 = (k0 & r0) == 0xFFFFFFFFu, e1 = (k1 & r1) == 0xFFFFFFFFu, e2 = (k2 & r2) == 0xFFFFFFFFu,
-               e3 = (k3 & r3) == 0xFFFFFFFFu;
-    const bool m0 = k0 == k && !e0, m1 = k1 == k && !e1, m2 = k2 == k && !e2, m3 = k3 == k && !e3;
-    Bucket4 o;
-    o.cnt = (uint32_t)m0 + (uint32_t)m1 + (uint32_t)m2 + (uint32_t)m3;
-    o.first = m0 ? r0 : m1 ? r1 : m2 ? r2 : r3;
-    // the run of this key ends in this bucket if the bucket has an empty slot or
-    // no insert ever moved past it
-    o.end = e0 | e1 | e2 | e3;
-    if (!o.end) o.end = !((ovf[bkt >> 5] >> (bkt & 31)) & 1u);
-    return o;
+
+// Lookup of key k: number of build matches and the rid of the first one.
+template <int W>
+__device__ __forceinline__ uint32_t soa_lookup(const SoaTab<W> &t, typename Tup<W>::U k, uint32_t home,
+                                               typename Tup<W>::U *first) {
+    using T = typename Tup<W>::U;
+    constexpr uint32_t G = SoaTab<W>::G;
+    uint32_t c = 0, bkt = home;
+    for (uint32_t it = 0; it < t.nb; ++it) {
+        T key[G];
+        t.ld(bkt, 0, key);
+        uint32_t m = 0;
+        bool e = false;
+#pragma unroll
+        for (uint32_t q = 0; q < G; ++q) {
+            m |= (uint32_t)(key[q] == k) << q;
+            e |= key[q] == t.empty;
+        }
+        if (m) {
+            T rid[G];
+            t.ld(bkt, 1, rid);
+            if (c == 0) {
+                T f = rid[G - 1];
+#pragma unroll
+                for (int q = (int)G - 2; q >= 0; --q)
+                    if ((m >> q) & 1u) f = rid[q];
+                *first = f;
+            }
+            c += __popc(m);
+        }
+        if (e || !t.overflowed(bkt)) break;
+        bkt = bkt + 1 == t.nb ? 0 : bkt + 1;
+    }
+    return c;
+}
+
+// Visit every build rid of key k (slow path for checksums).
+template <int W, class F>
+__device__ __forceinline__ void soa_visit(const SoaTab<W> &t, typename Tup<W>::U k, uint32_t home, F &&f) {
+    using T = typename Tup<W>::U;
+    constexpr uint32_t G = SoaTab<W>::G;
+    uint32_t bkt = home;
+    for (uint32_t it = 0; it < t.nb; ++it) {
+        T key[G], rid[G];
+        t.ld(bkt, 0, key);
+        t.ld(bkt, 1, rid);
+        bool e = false;
+#pragma unroll
+        for (uint32_t q = 0; q < G; ++q) {
+            if (key[q] == k) f(rid[q]);
+            e |= key[q] == t.empty;
+        }
+        if (e || !t.overflowed(bkt)) break;
+        bkt = bkt + 1 == t.nb ? 0 : bkt + 1;
+    }
+}
+
+// The whole warp emits every build match of key kk (probe rid ss): a window of
+// 32 slots (32 / G buckets) per step, up to the first bucket that ends the run.
+template <int W>
+__device__ __forceinline__ void soa_coop_emit(const SoaTab<W> &t, typename Tup<W>::U kk, typename Tup<W>::U ss,
+                                              uint32_t home, OutState &st, const OutCtx &oc) {
+    using T = typename Tup<W>::U;
+    constexpr uint32_t G = SoaTab<W>::G, BPW = 32 / G;
+    const unsigned lane = threadIdx.x & 31, jb = lane / G, q = lane % G;
+    for (uint32_t off = 0; off < t.nb; off += BPW) {
+        const bool inr = off + jb < t.nb;
+        uint32_t b = home + off + jb;
+        if (b >= t.nb) b -= t.nb;
+        const T key = inr ? t.ld1(b, 0, q) : t.empty;
+        const T rid = inr ? t.ld1(b, 1, q) : T(0);
+        const unsigned emp = __ballot_sync(0xffffffffu, key == t.empty);
+        const bool bucket_empty_slot = ((emp >> (jb * G)) & ((1u << G) - 1u)) != 0;
+        const bool bucket_end = !inr || bucket_empty_slot || !t.overflowed(b);
+        const unsigned endm = __ballot_sync(0xffffffffu, bucket_end && q == 0);
+        const unsigned last_lane = endm ? (unsigned)(__ffs(endm) - 1) + G - 1 : 31u;
+        const bool m = inr && lane <= last_lane && key == kk;
+        warp_append<W>(st, oc, m, rid, ss);
+        if (endm) break;
+    }
 }
 
 template <int W, bool AGG, int NT>
 __global__ void __launch_bounds__(NT, 2048 / NT / 2) partition_join_kernel(
     const void *Rp, const uint64_t *roff, const void *Sp, const uint64_t *soff, uint64_t NP, uint32_t cap_max,
-    void *pairs, uint64_t pcap, RecArea ra, hj_counters *ctr, uint32_t *oversize, int chk, int b1, int b2) {
+    void *pairs, uint64_t pcap, RecArea ra, hj_counters *ctr, uint32_t *oversize, int chk, int b1, int b2,
+    uint64_t empty_k0, uint64_t empty_k1) {
     using T = typename Tup<W>::U;
     using Vec = typename Tup<W>::Vec;
     using Hh = typename HashT<W>::type;
-    using SP = SmemPair<W>;
     constexpr int PV = Tup<W>::kPerVec, U = 2, IT = U * PV;
-    constexpr uint32_t G = SmemBucket<W>::kSlots;
+    constexpr uint32_t G = SoaTab<W>::G;
     extern __shared__ __align__(16) unsigned char smem[];
     __shared__ TableSide side;
     __shared__ int s_full;
@@ -495,8 +594,9 @@ __global__ void __launch_bounds__(NT, 2048 / NT / 2) partition_join_kernel(
                 }
             }
         }
-        // overflow bitmap (one bit per bucket) after the slots
         uint32_t *ovf = (uint32_t *)(smem + (size_t)cap_max * (AGG ? sizeof(AggSlot<W>) : 2 * W));
+        const T empty = pf.keep(hashw<W>((T)empty_k0)) ? (T)empty_k1 : (T)empty_k0;
+        const SoaTab<W> tab{sbase, cap / G, empty, ovf};
         if (work) {
             if (AGG) {
                 AggSlot<W> *sl = (AggSlot<W> *)smem;
@@ -506,8 +606,8 @@ __global__ void __launch_bounds__(NT, 2048 / NT / 2) partition_join_kernel(
                     sl[i].suma = 0;
                 }
             } else {
-                typename PairSlot<W>::S *sl = (typename PairSlot<W>::S *)smem;
-                for (uint32_t i = threadIdx.x; i < cap; i += blockDim.x) sl[i] = PairSlot<W>::empty();
+                T *kv = (T *)smem;  // keys of bucket b at [b * 2G, b * 2G + G)
+                for (uint32_t i = threadIdx.x; i < cap; i += blockDim.x) kv[(i / G) * 2 * G + (i % G)] = empty;
                 for (uint32_t i = threadIdx.x; i < (cap / G + 31) / 32; i += blockDim.x) ovf[i] = 0;
             }
             if (threadIdx.x == 0) {
@@ -528,28 +628,24 @@ __global__ void __launch_bounds__(NT, 2048 / NT / 2) partition_join_kernel(
                 for (int e = 0; e < PV; ++e) {
                     const Hh h = hashw<W>(k[e]);
                     if (!pf.keep(h)) continue;
-                    bool ok;
+                    bool ok = false;
                     if constexpr (AGG) {
                         ok = agg_insert<W>((AggSlot<W> *)smem, cap, &side, k[e], mix_a(r[e]), h);
-                    } else if (k[e] == Tup<W>::kAllOnes && r[e] == Tup<W>::kAllOnes) {
-                        atomicAdd(&side.n_allones, 1ull);
-                        ok = true;
                     } else {
-                        typename PairSlot<W>::S *sl = (typename PairSlot<W>::S *)smem;
-                        const typename PairSlot<W>::S val = PairSlot<W>::pack(k[e], r[e]);
-                        const uint32_t nb = cap / G;
-                        uint32_t bkt = sbucket<W>(h, nb);
-                        ok = false;
-                        for (uint32_t it = 0; it < nb && !ok; ++it) {
+                        T *kv = (T *)smem;
+                        uint32_t bkt = part_bucket<W>(k[e], tab.nb);
+                        for (uint32_t it = 0; it < tab.nb && !ok; ++it) {
                             for (uint32_t q = 0; q < G; ++q) {
-                                if (PairSlot<W>::try_claim(&sl[bkt * G + q], val)) {
+                                T *slot = &kv[bkt * 2 * G + q];
+                                if (cas_key<W>(slot, empty, k[e]) == empty) {
+                                    slot[G] = r[e];  // the rid half of the bucket
                                     ok = true;
                                     break;
                                 }
                             }
                             if (!ok) {  // moving past a full bucket: mark it
                                 atomicOr(&ovf[bkt >> 5], 1u << (bkt & 31));
-                                bkt = bkt + 1 == nb ? 0 : bkt + 1;
+                                bkt = bkt + 1 == tab.nb ? 0 : bkt + 1;
                             }
                         }
                     }
@@ -560,10 +656,7 @@ __global__ void __launch_bounds__(NT, 2048 / NT / 2) partition_join_kernel(
             if (s_full) {
                 if (threadIdx.x == 0) oversize[atomicAdd(&ctr->n_oversize, 1ull)] = (uint32_t)p;
             } else {
-                const unsigned long long nall = side.n_allones;
-                PairTab<W> ptab{(const typename PairSlot<W>::S *)smem, cap, nall, G};
                 AggTab<W> atab{(const AggSlot<W> *)smem, cap, &side};
-                const uint32_t nb = cap / G;
                 const uint32_t gstride = nwarps * 32 * U;
                 Vec cur[U], nxt[U];
                 uint32_t g = warp * 32 * U;
@@ -607,49 +700,55 @@ __global__ void __launch_bounds__(NT, 2048 / NT / 2) partition_join_kernel(
                             }
                         }
                     } else {
-                        uint32_t cnt[IT];
+                        uint32_t cnt[IT], home[IT];
                         T first[IT];
+                        bool live[IT];
+                        T kb[IT][G];
+                        // Home buckets of all items, key halves loaded together.  Padding
+                        // tuples need no filtering here: their keys hash to another
+                        // partition, so they equal neither a stored key nor the marker.
 #pragma unroll
                         for (int i = 0; i < IT; ++i) {
-                            const Hh h = hashw<W>(k[i]);
+                            home[i] = part_bucket<W>(k[i], tab.nb);
+                            live[i] = val[i];
+#pragma unroll
+                            for (uint32_t q = 0; q < G; ++q) kb[i][q] = tab.empty;
+                            if (live[i]) tab.ld(home[i], 0, kb[i]);
+                        }
+#pragma unroll
+                        for (int i = 0; i < IT; ++i) {
+                            uint32_t mm = 0;
+                            bool e = false;
+#pragma unroll
+                            for (uint32_t q = 0; q < G; ++q) {
+                                mm |= (uint32_t)(kb[i][q] == k[i]) << q;
+                                e |= kb[i][q] == tab.empty;
+                            }
                             uint32_t c = 0;
                             T f = 0;
-                            if (val[i] && pf.keep(h)) {
-                                uint32_t bkt = sbucket<W>(h, nb);
-                                if constexpr (W == 4) {
-                                    for (uint32_t it = 0; it < nb; ++it) {
-                                        const Bucket4 o = probe_bucket4(sbase, bkt, k[i], ovf);
-                                        if (c == 0) f = o.first;
-                                        c += o.cnt;
-                                        if (o.end) break;
-                                        bkt = bkt + 1 == nb ? 0 : bkt + 1;
-                                    }
-                                } else {
-                                    for (uint32_t it = 0; it < nb; ++it) {
-                                        SmemBucket<W> bk;
-                                        bk.load(sbase, bkt);
-                                        const bool e0 = SP::empty(bk.a), e1 = SP::empty(bk.b);
-                                        const bool m0 = !e0 && SP::key(bk.a) == k[i], m1 = !e1 && SP::key(bk.b) == k[i];
-                                        if (c == 0) f = m0 ? SP::rid(bk.a) : SP::rid(bk.b);
-                                        c += (uint32_t)m0 + (uint32_t)m1;
-                                        bool end = e0 | e1;
-                                        if (!end) end = !((ovf[bkt >> 5] >> (bkt & 31)) & 1u);
-                                        if (end) break;
-                                        bkt = bkt + 1 == nb ? 0 : bkt + 1;
-                                    }
-                                }
-                                if (k[i] == Tup<W>::kAllOnes && nall) {
-                                    if (c == 0) f = Tup<W>::kAllOnes;
-                                    c += (uint32_t)nall;
-                                }
-                                if (chk && c) {  // checksums over every match (rare second walk)
-                                    const uint64_t bs = mix_b(r[i]);
-                                    ptab.lookup(k[i], h, [&](T rid) {
-                                        const uint64_t a = mix_a(rid);
-                                        acc.c0 += a * bs;
-                                        acc.c1 += a + bs;
-                                    });
-                                }
+                            if (live[i] && mm) {
+                                T rid[G];
+                                tab.ld(home[i], 1, rid);
+                                f = rid[G - 1];
+#pragma unroll
+                                for (int q = (int)G - 2; q >= 0; --q)
+                                    if ((mm >> q) & 1u) f = rid[q];
+                                c = __popc(mm);
+                            }
+                            if (live[i] && !e && tab.overflowed(home[i])) {  // the run continues (rare)
+                                const uint32_t nx = home[i] + 1 == tab.nb ? 0 : home[i] + 1;
+                                T f2 = 0;
+                                const uint32_t c2 = soa_lookup<W>(tab, k[i], nx, &f2);
+                                if (c == 0) f = f2;
+                                c += c2;
+                            }
+                            if (chk && c) {
+                                const uint64_t bs = mix_b(r[i]);
+                                soa_visit<W>(tab, k[i], home[i], [&](T rid) {
+                                    const uint64_t a = mix_a(rid);
+                                    acc.c0 += a * bs;
+                                    acc.c1 += a + bs;
+                                });
                             }
                             cnt[i] = c;
                             first[i] = f;
@@ -697,7 +796,8 @@ __global__ void __launch_bounds__(NT, 2048 / NT / 2) partition_join_kernel(
                                 multi &= multi - 1;
                                 const T kk = __shfl_sync(0xffffffffu, k[i], L);
                                 const T ss = __shfl_sync(0xffffffffu, r[i], L);
-                                ptab.coop_emit(kk, ss, st, oc);
+                                const uint32_t hh = __shfl_sync(0xffffffffu, home[i], L);
+                                soa_coop_emit<W>(tab, kk, ss, hh, st, oc);
                             }
                         }
                     }
@@ -736,6 +836,19 @@ hj_status partition_join(hj_ctx *c, int width, int agg, const void *Rp, const ui
     (void)nS_total;
     (void)filter;
     if (nparts == 0) return HJ_OK;
+    // Two keys in different partitions: each partition's empty-slot marker is
+    // whichever of them hashes elsewhere.  They come from the top of the key domain;
+    // the padding keys of the partitioner come from the bottom (0, 1, 2, ...), so a
+    // probe key never equals the marker.
+    auto pidx = [&](uint64_t k) {
+        uint64_t h = width == 4 ? (uint64_t)murmur2_u32((uint32_t)k) : murmur2_u64(k);
+        uint64_t d1 = h & ((1ull << b1) - 1), d2 = b2 ? (h >> b1) & ((1ull << b2) - 1) : 0;
+        return (d1 << b2) | d2;
+    };
+    const uint64_t top = width == 4 ? 0xFFFFFFFFull : ~0ull;
+    const uint64_t ek0 = top;
+    uint64_t ek1 = top - 1;
+    while (pidx(ek1) == pidx(ek0)) --ek1;
     const uint64_t slot_bytes = agg ? (width == 4 ? sizeof(AggSlot<4>) : sizeof(AggSlot<8>)) : 2ull * width;
     const JoinCfg cfg = join_cfg(width, agg, expect_r);
     // Capacity: room for a partition of the expected size plus six standard
@@ -755,7 +868,7 @@ hj_status partition_join(hj_ctx *c, int width, int agg, const void *Rp, const ui
         auto kern = partition_join_kernel<WW, AA, NT>;                                                      \
         HJ_CUDA(c, cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));     \
         HJ_LAUNCH(c, "partition_join", kern, grid, NT, smem, Rp, roff, Sp, soff, nparts, (uint32_t)cap_max, \
-                  pairs, pcap, ra, c->d_ctr, oversize, checksum, b1, b2);                                   \
+                  pairs, pcap, ra, c->d_ctr, oversize, checksum, b1, b2, ek0, ek1);                         \
     } while (0)
     if (width == 4) {
         if (agg) { if (cfg.nt == 512) HJ_PJ(4, true, 512); else HJ_PJ(4, true, 1024); }

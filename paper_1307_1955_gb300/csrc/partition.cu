@@ -459,6 +459,258 @@ __global__ void __launch_bounds__(NT) scatter_kernel(const void *in, uint64_t n_
     }
 }
 
+// Scatter with the next tile staged by a TMA bulk copy.  Same phases as
+// scatter_kernel; instead of registers, tile t + 1 travels global -> shared in one
+// cp.async.bulk issued right after tile t's tuples have been read out of the
+// staging buffer, so the copy overlaps phases 2-5 of tile t and only the current
+// tile lives in registers (1024 threads per CTA).
+constexpr int kTmaThreads = 1024;
+constexpr uint32_t kWaitLimit = 1u << 26;  // mbarrier polls before giving up
+
+template <int W> struct TmaShape {
+    static constexpr int IT = W == 4 ? 8 : 4;    // tuples per thread per tile
+    static constexpr int T = kTmaThreads * IT;
+    static constexpr int SV = Sector<W>::kTuples;
+};
+
+// Per-digit state of the TMA scatter, one 16-byte record so that the per-sector
+// writer reads it with a single shared load.
+struct DigitMeta {
+    uint32_t gcur;  // next output row (relative to the chunk's sector-aligned base)
+    uint32_t cnt;   // tuples of this digit in the current tile
+    uint32_t oc;    // o (rows completed this tile) | carried count << 16
+    uint32_t lu;    // tile offset | first unit << 16
+};
+
+template <int W>
+__host__ __device__ inline size_t scatter_tma_smem_bytes(uint32_t P) {
+    using TS = TmaShape<W>;
+    size_t slot = 2 * W;
+    size_t b = ((size_t)TS::T + 4) * slot + (size_t)TS::T * slot  // stage (tile + alignment slack), buf
+               + (size_t)P * (TS::SV - 1) * slot                  // carry
+               + (size_t)P * sizeof(DigitMeta)                    // meta
+               + ((size_t)TS::T / TS::SV + 2 * (size_t)P) * 2     // udig
+               + (size_t)P;                                       // ccount
+    return (b + 15) & ~size_t(15);
+}
+
+template <int W>
+__global__ void __launch_bounds__(kTmaThreads, 1) scatter_tma_kernel(
+    const void *in, uint64_t n_total, const uint64_t *seg_off, uint64_t nseg, const unsigned long long *cb,
+    uint64_t chunk, int shift, int bits, const unsigned long long *Hs, void *out, int pad, uint64_t sent_k0,
+    uint64_t sent_k1, hj_counters *ctr) {
+    using U = typename Tup<W>::U;
+    using TS = TmaShape<W>;
+    using Slot = typename SortSlot<W>::T;
+    constexpr int IT = TS::IT, SV = TS::SV, T = TS::T;
+    constexpr int EPT = 2;  // digits per thread (fan-out <= 2 * kTmaThreads)
+    const uint32_t P = 1u << bits;
+    extern __shared__ __align__(16) unsigned char smem[];
+    Slot *stage = (Slot *)smem;                                        // T + 4: an unaligned tile
+    Slot *buf = stage + T + 4;                                         // T      spans T + 2 slots
+    Slot *carry = buf + T;                                             // P * (SV - 1)
+    DigitMeta *meta = (DigitMeta *)(carry + (size_t)P * (SV - 1));     // P
+    uint16_t *udig = (uint16_t *)(meta + P);                           // T / SV + 2P
+    uint8_t *ccount = (uint8_t *)(udig + T / SV + 2 * P);              // P
+    __shared__ uint32_t sc[33];
+    __shared__ uint32_t s_nunits;
+    __shared__ int s_abort;
+    __shared__ __align__(8) unsigned long long mbar;
+    const uint32_t bar = (uint32_t)__cvta_generic_to_shared(&mbar);
+    const uint32_t stage_s = (uint32_t)__cvta_generic_to_shared(stage);
+
+    const uint64_t g = blockIdx.x;
+    if (g >= cb[nseg]) return;
+    const ChunkPos cp = chunk_pos(seg_off, nseg, cb, chunk, g);
+    const uint64_t row = cb[cp.s] * P;
+    const uint64_t seg_start = seg_off[0] + Hs[row];
+    const uint64_t obase = seg_start / SV * SV;
+    Slot *outp = (Slot *)out + obase;
+    const uint64_t tb = 2 * W;
+    const uint64_t last16 = (n_total * tb) / 16 * 16;  // bytes of `in` a 16-byte copy may touch
+    for (uint32_t d = threadIdx.x; d < P; d += blockDim.x) {
+        DigitMeta m;
+        m.gcur = (uint32_t)(seg_off[0] + Hs[row + (uint64_t)d * cp.nch + cp.cidx] - obase);
+        m.cnt = 0;
+        m.oc = 0;
+        m.lu = 0;
+        meta[d] = m;
+        ccount[d] = 0;
+    }
+    if (threadIdx.x == 0) {
+        s_abort = 0;
+        mbar_init(bar, 1);
+        fence_mbar_init();
+    }
+    __syncthreads();
+    auto stage_range = [&](uint64_t t0, uint64_t t1, uint64_t *b0, uint64_t *b1) {
+        *b0 = (t0 * tb) / 16 * 16;
+        uint64_t e = (t1 * tb + 15) / 16 * 16;
+        *b1 = e < last16 ? e : last16;
+    };
+    auto issue = [&](uint64_t t0, uint64_t t1) {
+        uint64_t b0, b1;
+        stage_range(t0, t1, &b0, &b1);
+        if (b1 > b0) {
+            mbar_expect_tx(bar, (uint32_t)(b1 - b0));
+            bulk_g2s(stage_s, (const char *)in + b0, (uint32_t)(b1 - b0), bar);
+        } else {
+            mbar_expect_tx(bar, 0);
+        }
+    };
+    const uint32_t d0 = threadIdx.x * EPT;  // this thread's digits: d0, d0 + 1
+    uint32_t parity = 0;
+    if (threadIdx.x == 0 && cp.lo < cp.hi) issue(cp.lo, min(cp.lo + (uint64_t)T, cp.hi));
+    for (uint64_t t0 = cp.lo; t0 < cp.hi; t0 += T) {
+        const uint64_t t1 = min(t0 + (uint64_t)T, cp.hi);
+        if (!mbar_wait_bounded(bar, parity, kWaitLimit)) s_abort = 1;
+        parity ^= 1u;
+        __syncthreads();
+        if (s_abort) {  // a copy did not complete: report, let it drain, stop
+            if (threadIdx.x == 0) {
+                atomicOr(&ctr->status, (unsigned long long)kStatusTimeout);
+                mbar_wait_bounded(bar, parity ^ 1u, kWaitLimit);
+            }
+            return;
+        }
+        // 1. tuples of this tile (staged, except an odd final tuple past the last 16 bytes)
+        uint64_t b0, b1;
+        stage_range(t0, t1, &b0, &b1);
+        const uint32_t ntile = (uint32_t)(t1 - t0);
+        const uint32_t skew = (uint32_t)(t0 - b0 / tb);                   // 0 or 1 leading slots
+        const uint32_t staged = b1 > b0 ? (uint32_t)((b1 - b0) / tb) : 0u;
+        const uint32_t nstaged = staged > skew ? staged - skew : 0u;       // tuples of the tile in the stage
+        U k[IT], r[IT];
+        uint32_t d[IT], rk[IT];
+#pragma unroll
+        for (int i = 0; i < IT; ++i) {
+            const uint32_t t = (uint32_t)i * kTmaThreads + threadIdx.x;
+            Slot sl;
+            if (t < nstaged) sl = stage[t + skew];
+            else if (t < ntile) sl = ((const Slot *)in)[t0 + t];
+            else {
+                if constexpr (W == 4) sl = 0ull;
+                else sl = make_ulonglong2(0ull, 0ull);
+            }
+            if constexpr (W == 4) {
+                k[i] = (uint32_t)sl;
+                r[i] = (uint32_t)(sl >> 32);
+            } else {
+                k[i] = sl.x;
+                r[i] = sl.y;
+            }
+            d[i] = digit_of(key_hash<W>(k[i]), shift, bits);
+            rk[i] = t < ntile ? atomicAdd(&meta[d[i]].cnt, 1u) : 0u;
+        }
+        fence_proxy_async();
+        __syncthreads();
+        if (threadIdx.x == 0 && t1 < cp.hi) issue(t1, min(t1 + (uint64_t)T, cp.hi));
+        // 2. tile offsets and output units (n in the low half, units in the high half)
+        uint32_t n_[EPT], c_[EPT], gc_[EPT], o_[EPT], nu_[EPT];
+        uint32_t sum = 0;
+#pragma unroll
+        for (int q = 0; q < EPT; ++q) {
+            const uint32_t dd = d0 + q;
+            n_[q] = c_[q] = gc_[q] = o_[q] = nu_[q] = 0;
+            if (dd < P) {
+                const DigitMeta m = meta[dd];
+                n_[q] = m.cnt;
+                c_[q] = ccount[dd];
+                gc_[q] = m.gcur;
+                const uint32_t bnd = (gc_[q] + c_[q] + n_[q]) / SV * SV;
+                o_[q] = bnd > gc_[q] ? bnd - gc_[q] : 0u;
+                nu_[q] = o_[q] ? bnd / SV - gc_[q] / SV : 0u;
+                sum += n_[q] | (nu_[q] << 16);
+            }
+        }
+        {
+            uint32_t tot;
+            uint32_t ex = block_exclusive_scan<uint32_t>(sum, sc, &tot);
+#pragma unroll
+            for (int q = 0; q < EPT; ++q) {
+                const uint32_t dd = d0 + q;
+                if (dd < P) {
+                    meta[dd].oc = o_[q] | (c_[q] << 16);
+                    meta[dd].lu = ex;
+                    for (uint32_t u = 0; u < nu_[q]; ++u) udig[(ex >> 16) + u] = (uint16_t)dd;
+                    ex += n_[q] | (nu_[q] << 16);
+                }
+            }
+            if (threadIdx.x == 0) s_nunits = tot >> 16;
+        }
+        __syncthreads();
+        // 3. digit-sorted tile
+#pragma unroll
+        for (int i = 0; i < IT; ++i) {
+            const uint32_t t = (uint32_t)i * kTmaThreads + threadIdx.x;
+            if (t >= ntile) continue;
+            const uint32_t p = (meta[d[i]].lu & 0xFFFFu) + rk[i];
+            if constexpr (W == 4) buf[p] = (unsigned long long)k[i] | ((unsigned long long)r[i] << 32);
+            else buf[p] = make_ulonglong2(k[i], r[i]);
+        }
+        __syncthreads();
+        // 4. one thread per output sector
+        const uint32_t nunits = s_nunits;
+        for (uint32_t ui = threadIdx.x; ui < nunits; ui += blockDim.x) {
+            const uint32_t dd = udig[ui];
+            const DigitMeta m = meta[dd];
+            const uint32_t c = m.oc >> 16, gc = m.gcur, lo_t = m.lu & 0xFFFFu;
+            const uint32_t sec = gc / SV + (ui - (m.lu >> 16));
+            const uint32_t row0 = sec * SV > gc ? sec * SV : gc;
+            const Slot *cy = carry + (size_t)dd * (SV - 1);
+            Slot tup[SV];
+#pragma unroll
+            for (int q = 0; q < SV; ++q) {
+                const uint32_t rr = sec * SV + q;
+                const uint32_t j = rr - gc;
+                if (rr >= row0) tup[q] = j < c ? cy[j] : buf[lo_t + j - c];
+            }
+            if (row0 == sec * SV) {
+                st_sector(outp + (size_t)sec * SV, (const unsigned long long *)tup);
+            } else {
+#pragma unroll
+                for (int q = 0; q < SV; ++q)
+                    if (sec * SV + q >= row0) outp[(size_t)sec * SV + q] = tup[q];
+            }
+        }
+        __syncthreads();
+        // 5. new carries, cursors (this thread's digits, values from phase 2)
+#pragma unroll
+        for (int q = 0; q < EPT; ++q) {
+            const uint32_t dd = d0 + q;
+            if (dd < P) {
+                Slot *cy = carry + (size_t)dd * (SV - 1);
+                const uint32_t lo_t = meta[dd].lu & 0xFFFFu;
+                for (uint32_t j = (o_[q] > c_[q] ? o_[q] : c_[q]); j < c_[q] + n_[q]; ++j)
+                    cy[j - o_[q]] = buf[lo_t + (j - c_[q])];
+                meta[dd].gcur = gc_[q] + o_[q];
+                meta[dd].cnt = 0;
+                ccount[dd] = (uint8_t)(c_[q] + n_[q] - o_[q]);
+            }
+        }
+        __syncthreads();
+    }
+    // final carries; with pad, padding tuples complete each run's last sector
+    for (uint32_t dd = threadIdx.x; dd < P; dd += blockDim.x) {
+        const uint32_t c = ccount[dd], gc = meta[dd].gcur;
+        const Slot *cy = carry + (size_t)dd * (SV - 1);
+        if (pad) {
+            if (c == 0) continue;
+            const uint64_t sk = digit_of(key_hash<W>((U)sent_k0), shift, bits) != dd ? sent_k0 : sent_k1;
+            Slot tup[SV];
+#pragma unroll
+            for (int q = 0; q < SV; ++q) {
+                if ((uint32_t)q < c) tup[q] = cy[q];
+                else if constexpr (W == 4) tup[q] = (unsigned long long)(uint32_t)sk;
+                else tup[q] = make_ulonglong2(sk, 0ull);
+            }
+            st_sector(outp + gc, (const unsigned long long *)tup);
+        } else {
+            for (uint32_t j = 0; j < c; ++j) outp[gc + j] = cy[j];
+        }
+    }
+}
+
 // ------------------------------------------------------------------- driver
 
 // Scatter configuration (threads, vectors per thread) for a fan-out: 8192-tuple
@@ -466,10 +718,13 @@ __global__ void __launch_bounds__(NT) scatter_kernel(const void *in, uint64_t n_
 struct ScatterCfg {
     int nt, vpt;
     uint64_t tile;
+    bool tma;
 };
 static ScatterCfg scatter_cfg(int width, int bits) {
-    if (width == 4) return bits <= 11 ? ScatterCfg{512, 8, 8192} : ScatterCfg{1024, 2, 4096};
-    return bits <= 11 ? ScatterCfg{512, 4, 2048} : ScatterCfg{1024, 2, 2048};
+    // up to 2^11 digits the TMA-staged kernel fits shared memory
+    if (bits <= 11) return ScatterCfg{kTmaThreads, 0, (uint64_t)(width == 4 ? TmaShape<4>::T : TmaShape<8>::T), true};  // 2^bits <= 2 * kTmaThreads
+    if (width == 4) return ScatterCfg{1024, 2, 4096, false};
+    return ScatterCfg{1024, 2, 2048, false};
 }
 
 uint64_t partition_out_rows(hj_ctx *c, int width, uint64_t n_total, uint64_t nseg, int bits, int pad) {
@@ -543,7 +798,18 @@ hj_status partition_pass(hj_ctx *c, int width, const void *in, uint64_t n_total,
         HJ_LAUNCH(c, "partition_scatter", kern, (unsigned)max_chunks, NT, ssmem, in, n_total, seg_off, nseg, cb, \
                   chunk, shift, bits, Hs, out, pad, k0, k1);                                                  \
     } while (0)
-    if (width == 4) {
+    const size_t tma_smem = width == 4 ? scatter_tma_smem_bytes<4>((uint32_t)P) : scatter_tma_smem_bytes<8>((uint32_t)P);
+    if (cfg.tma) {
+        if (width == 4) {
+            HJ_CUDA(c, cudaFuncSetAttribute(scatter_tma_kernel<4>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)tma_smem));
+            HJ_LAUNCH(c, "partition_scatter", scatter_tma_kernel<4>, (unsigned)max_chunks, kTmaThreads, tma_smem, in,
+                      n_total, seg_off, nseg, cb, chunk, shift, bits, Hs, out, pad, k0, k1, c->d_ctr);
+        } else {
+            HJ_CUDA(c, cudaFuncSetAttribute(scatter_tma_kernel<8>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)tma_smem));
+            HJ_LAUNCH(c, "partition_scatter", scatter_tma_kernel<8>, (unsigned)max_chunks, kTmaThreads, tma_smem, in,
+                      n_total, seg_off, nseg, cb, chunk, shift, bits, Hs, out, pad, k0, k1, c->d_ctr);
+        }
+    } else if (width == 4) {
         if (cfg.nt == 512) HJ_SC(4, 512, 8); else HJ_SC(4, 1024, 2);
     } else {
         if (cfg.nt == 512) HJ_SC(8, 512, 4); else HJ_SC(8, 1024, 2);
