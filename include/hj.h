@@ -158,6 +158,33 @@ hj_status hj_join_host(hj_ctx *ctx, const hj_rel *R_host, const hj_rel *S_host, 
 /* Release a result's pairs (no-op for the count modes) and zero the struct. */
 hj_status hj_result_free(hj_ctx *ctx, hj_result *res);
 
+/* Simple hash join that allocates nothing.  (The paper has no counterpart: this
+ * entry exists for callers that may not allocate device memory -- for example a
+ * host process whose device memory is owned by another allocator that reserves
+ * it all, or a latency-critical or certified loop that forbids allocation after
+ * start-up.)  It needs no context: it runs on the current device and on
+ * `cuda_stream` (NULL: the default stream), and returns when the join is done.
+ * The caller provides R, S (device, 16-byte aligned, same width) and the pair
+ * buffer `pairs` (device, room for `pairs_cap` pairs of 2 * width bytes; may be
+ * NULL when pairs_cap is 0).  *count receives the number of pairs; checksum
+ * (NULL allowed) receives c0, c1 as in HJ_COUNT_CHECKSUM; the pairs are written
+ * densely in no particular order.  Returns HJ_E_OVERFLOW, with *count set, if
+ * the join has more than pairs_cap pairs (the first pairs_cap are written).
+ *
+ * Its scratch -- counters and the hash table -- is one file-scope device array of
+ * HJ_STATIC_SCRATCH_BYTES bytes in the library, which every GPU that loads the
+ * library holds until the process exits.  The table needs 2 * width bytes for
+ * each of the next power of two at least 2|R| + 1 slots, so |R| may be at most
+ * 2097151 tuples for HJ_U32 and 1048575 for HJ_U64; a larger R is rejected with
+ * HJ_E_NOMEM before any work is queued.  The first call on a device looks up
+ * the array's device address (cudaGetSymbolAddress) with that device current;
+ * make that first call before any stream capture.  Every call reuses the same
+ * array, so calls whose work overlaps on the GPU (other streams, other threads)
+ * race and corrupt each other's results: serialise them. */
+#define HJ_STATIC_SCRATCH_BYTES (64ull << 20)
+hj_status hj_join_static(const hj_rel *R, const hj_rel *S, void *cuda_stream, void *pairs, uint64_t pairs_cap,
+                         uint64_t *count, uint64_t *checksum);
+
 /* Wait for all work queued on the context's stream. */
 hj_status hj_sync(hj_ctx *ctx);
 

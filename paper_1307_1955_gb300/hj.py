@@ -76,6 +76,7 @@ def load_library(path: str = LIB_PATH):
         "hj_join": (I32, [V, P(hj_rel), P(hj_rel), P(hj_opts), P(hj_result)]),
         "hj_result_free": (I32, [V, P(hj_result)]),
         "hj_join_host": (I32, [V, P(hj_rel), P(hj_rel), P(hj_opts), V, U64, P(hj_result)]),
+        "hj_join_static": (I32, [P(hj_rel), P(hj_rel), V, V, U64, P(U64), P(U64)]),
         "hj_sync": (I32, [V]),
         "hj_copy": (I32, [V, V, V, U64]),
         "hj_prof_enable": (I32, [V, ctypes.c_int]),
@@ -245,6 +246,24 @@ def hj_join_host(ctx: Context, R: torch.Tensor, S: torch.Tensor, pairs_out: torc
     _check(ctx, load_library().hj_join_host(ctx.handle, ctypes.byref(r), ctypes.byref(s), ctypes.byref(o), ptr,
                                             cap, ctypes.byref(res)))
     return _result(ctx, res)
+
+
+def hj_join_static(R: torch.Tensor, S: torch.Tensor, pairs: torch.Tensor | None, stream=None):
+    """The allocation-free SHJ: pairs land in the caller's (m, 2) CUDA tensor of R's
+    dtype.  Returns (count, (c0, c1)); raises HJError on a non-OK status (count is
+    then in .count for HJ_E_OVERFLOW)."""
+    r, s = rel_of(R), rel_of(S)
+    cnt = ctypes.c_uint64()
+    chk = (ctypes.c_uint64 * 2)()
+    ptr = pairs.data_ptr() if pairs is not None and pairs.numel() else None
+    cap = pairs.shape[0] if pairs is not None else 0
+    st = load_library().hj_join_static(ctypes.byref(r), ctypes.byref(s), stream.cuda_stream if stream else None, ptr,
+                                       cap, ctypes.byref(cnt), chk)
+    if st != HJ_OK:
+        e = HJError(st, "hj_join_static failed")
+        e.count = int(cnt.value)
+        raise e
+    return int(cnt.value), (int(chk[0]), int(chk[1]))
 
 
 def hj_result_free(ctx: Context, res: Result):
