@@ -432,7 +432,9 @@ __device__ __forceinline__ typename HashT<W>::type hashw(typename Tup<W>::U k) {
 
 // ----------------------------------------------------------- shared-memory table
 // Bucketised open addressing in shared memory for one partition pair.  Bucket b is
-// 32 bytes: G keys, then their G rids (G = 4 for 4-byte tuples, 2 for 8-byte).
+// G slots (G = 4 for 4-byte tuples, 2 for 8-byte): its G keys are 16 bytes of the
+// key region and its G rids 16 bytes of the rid region (separate regions, so that
+// the key loads of random buckets spread over all shared-memory banks).
 // Every real key of partition p hashes to p, so a key that hashes to another
 // partition can never be stored or probed: it marks empty slots (no value of the
 // key domain needs reserving).  A key's run starts at its home bucket and moves
@@ -442,15 +444,16 @@ __device__ __forceinline__ typename HashT<W>::type hashw(typename Tup<W>::U k) {
 template <int W> struct SoaTab {
     using T = typename Tup<W>::U;
     static constexpr uint32_t G = 16 / W;
-    uint32_t sbase;  // shared address of bucket 0
+    uint32_t kbase;  // shared address of the key region: 16 bytes (G keys) per bucket
+    uint32_t rbase;  // shared address of the rid region, same shape
     uint32_t nb;     // buckets
     T empty;
     const uint32_t *ovf;
 
     __device__ __forceinline__ bool overflowed(uint32_t b) const { return (ovf[b >> 5] >> (b & 31)) & 1u; }
-    // keys or rids of bucket b (half 0 = keys, half 1 = rids)
+    // keys (half 0) or rids (half 1) of bucket b
     __device__ __forceinline__ void ld(uint32_t b, uint32_t half, T *v) const {
-        const uint32_t a = sbase + b * 32u + half * 16u;
+        const uint32_t a = (half ? rbase : kbase) + b * 16u;
         if constexpr (W == 4)
             asm volatile("ld.shared.v4.u32 {%0, %1, %2, %3}, [%4];" : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]) : "r"(a));
         else
@@ -458,7 +461,7 @@ template <int W> struct SoaTab {
     }
     __device__ __forceinline__ T ld1(uint32_t b, uint32_t half, uint32_t q) const {
         T v;
-        const uint32_t a = sbase + b * 32u + half * 16u + q * (uint32_t)W;
+        const uint32_t a = (half ? rbase : kbase) + b * 16u + q * (uint32_t)W;
         if constexpr (W == 4) asm volatile("ld.shared.u32 %0, [%1];" : "=r"(v) : "r"(a));
         else asm volatile("ld.shared.u64 %0, [%1];" : "=l"(v) : "r"(a));
         return v;
@@ -596,7 +599,7 @@ __global__ void __launch_bounds__(NT, 2048 / NT / 2) partition_join_kernel(
         }
         uint32_t *ovf = (uint32_t *)(smem + (size_t)cap_max * (AGG ? sizeof(AggSlot<W>) : 2 * W));
         const T empty = pf.keep(hashw<W>((T)empty_k0)) ? (T)empty_k1 : (T)empty_k0;
-        const SoaTab<W> tab{sbase, cap / G, empty, ovf};
+        const SoaTab<W> tab{sbase, sbase + (cap / G) * 16u, cap / G, empty, ovf};
         if (work) {
             if (AGG) {
                 AggSlot<W> *sl = (AggSlot<W> *)smem;
@@ -606,8 +609,8 @@ __global__ void __launch_bounds__(NT, 2048 / NT / 2) partition_join_kernel(
                     sl[i].suma = 0;
                 }
             } else {
-                T *kv = (T *)smem;  // keys of bucket b at [b * 2G, b * 2G + G)
-                for (uint32_t i = threadIdx.x; i < cap; i += blockDim.x) kv[(i / G) * 2 * G + (i % G)] = empty;
+                T *kv = (T *)smem;  // key region: cap keys; the rid region follows
+                for (uint32_t i = threadIdx.x; i < cap; i += blockDim.x) kv[i] = empty;
                 for (uint32_t i = threadIdx.x; i < (cap / G + 31) / 32; i += blockDim.x) ovf[i] = 0;
             }
             if (threadIdx.x == 0) {
@@ -636,9 +639,9 @@ __global__ void __launch_bounds__(NT, 2048 / NT / 2) partition_join_kernel(
                         uint32_t bkt = part_bucket<W>(k[e], tab.nb);
                         for (uint32_t it = 0; it < tab.nb && !ok; ++it) {
                             for (uint32_t q = 0; q < G; ++q) {
-                                T *slot = &kv[bkt * 2 * G + q];
+                                T *slot = &kv[bkt * G + q];
                                 if (cas_key<W>(slot, empty, k[e]) == empty) {
-                                    slot[G] = r[e];  // the rid half of the bucket
+                                    slot[cap] = r[e];  // the same slot of the rid region
                                     ok = true;
                                     break;
                                 }

@@ -473,13 +473,13 @@ template <int W> struct TmaShape {
     static constexpr int SV = Sector<W>::kTuples;
 };
 
-// Per-digit state of the TMA scatter, one 16-byte record so that the per-sector
-// writer reads it with a single shared load.
+// Per-digit state of the TMA scatter.  What the per-sector writer needs is one
+// 8-byte record (a single shared load); the per-tuple fields -- the tile count
+// bumped by every tuple and the tile offset read by every tuple -- live in dense
+// arrays so that random digits spread over all shared-memory banks.
 struct DigitMeta {
     uint32_t gcur;  // next output row (relative to the chunk's sector-aligned base)
-    uint32_t cnt;   // tuples of this digit in the current tile
     uint32_t oc;    // o (rows completed this tile) | carried count << 16
-    uint32_t lu;    // tile offset | first unit << 16
 };
 
 template <int W>
@@ -489,6 +489,8 @@ __host__ __device__ inline size_t scatter_tma_smem_bytes(uint32_t P) {
     size_t b = ((size_t)TS::T + 4) * slot + (size_t)TS::T * slot  // stage (tile + alignment slack), buf
                + (size_t)P * (TS::SV - 1) * slot                  // carry
                + (size_t)P * sizeof(DigitMeta)                    // meta
+               + (size_t)P * 4                                    // cnt
+               + (size_t)P * 2 * 2                                // loff, uoff
                + ((size_t)TS::T / TS::SV + 2 * (size_t)P) * 2     // udig
                + (size_t)P;                                       // ccount
     return (b + 15) & ~size_t(15);
@@ -510,7 +512,10 @@ __global__ void __launch_bounds__(kTmaThreads, 1) scatter_tma_kernel(
     Slot *buf = stage + T + 4;                                         // T      spans T + 2 slots
     Slot *carry = buf + T;                                             // P * (SV - 1)
     DigitMeta *meta = (DigitMeta *)(carry + (size_t)P * (SV - 1));     // P
-    uint16_t *udig = (uint16_t *)(meta + P);                           // T / SV + 2P
+    uint32_t *cnt = (uint32_t *)(meta + P);                            // P
+    uint16_t *loff = (uint16_t *)(cnt + P);                            // P
+    uint16_t *uoff = loff + P;                                         // P
+    uint16_t *udig = uoff + P;                                         // T / SV + 2P
     uint8_t *ccount = (uint8_t *)(udig + T / SV + 2 * P);              // P
     __shared__ uint32_t sc[33];
     __shared__ uint32_t s_nunits;
@@ -531,10 +536,9 @@ __global__ void __launch_bounds__(kTmaThreads, 1) scatter_tma_kernel(
     for (uint32_t d = threadIdx.x; d < P; d += blockDim.x) {
         DigitMeta m;
         m.gcur = (uint32_t)(seg_off[0] + Hs[row + (uint64_t)d * cp.nch + cp.cidx] - obase);
-        m.cnt = 0;
         m.oc = 0;
-        m.lu = 0;
         meta[d] = m;
+        cnt[d] = 0;
         ccount[d] = 0;
     }
     if (threadIdx.x == 0) {
@@ -600,7 +604,7 @@ __global__ void __launch_bounds__(kTmaThreads, 1) scatter_tma_kernel(
                 r[i] = sl.y;
             }
             d[i] = digit_of(key_hash<W>(k[i]), shift, bits);
-            rk[i] = t < ntile ? atomicAdd(&meta[d[i]].cnt, 1u) : 0u;
+            rk[i] = t < ntile ? atomicAdd(&cnt[d[i]], 1u) : 0u;
         }
         fence_proxy_async();
         __syncthreads();
@@ -613,10 +617,9 @@ __global__ void __launch_bounds__(kTmaThreads, 1) scatter_tma_kernel(
             const uint32_t dd = d0 + q;
             n_[q] = c_[q] = gc_[q] = o_[q] = nu_[q] = 0;
             if (dd < P) {
-                const DigitMeta m = meta[dd];
-                n_[q] = m.cnt;
+                n_[q] = cnt[dd];
                 c_[q] = ccount[dd];
-                gc_[q] = m.gcur;
+                gc_[q] = meta[dd].gcur;
                 const uint32_t bnd = (gc_[q] + c_[q] + n_[q]) / SV * SV;
                 o_[q] = bnd > gc_[q] ? bnd - gc_[q] : 0u;
                 nu_[q] = o_[q] ? bnd / SV - gc_[q] / SV : 0u;
@@ -631,7 +634,8 @@ __global__ void __launch_bounds__(kTmaThreads, 1) scatter_tma_kernel(
                 const uint32_t dd = d0 + q;
                 if (dd < P) {
                     meta[dd].oc = o_[q] | (c_[q] << 16);
-                    meta[dd].lu = ex;
+                    loff[dd] = (uint16_t)(ex & 0xFFFFu);
+                    uoff[dd] = (uint16_t)(ex >> 16);
                     for (uint32_t u = 0; u < nu_[q]; ++u) udig[(ex >> 16) + u] = (uint16_t)dd;
                     ex += n_[q] | (nu_[q] << 16);
                 }
@@ -644,7 +648,7 @@ __global__ void __launch_bounds__(kTmaThreads, 1) scatter_tma_kernel(
         for (int i = 0; i < IT; ++i) {
             const uint32_t t = (uint32_t)i * kTmaThreads + threadIdx.x;
             if (t >= ntile) continue;
-            const uint32_t p = (meta[d[i]].lu & 0xFFFFu) + rk[i];
+            const uint32_t p = loff[d[i]] + rk[i];
             if constexpr (W == 4) buf[p] = (unsigned long long)k[i] | ((unsigned long long)r[i] << 32);
             else buf[p] = make_ulonglong2(k[i], r[i]);
         }
@@ -654,8 +658,8 @@ __global__ void __launch_bounds__(kTmaThreads, 1) scatter_tma_kernel(
         for (uint32_t ui = threadIdx.x; ui < nunits; ui += blockDim.x) {
             const uint32_t dd = udig[ui];
             const DigitMeta m = meta[dd];
-            const uint32_t c = m.oc >> 16, gc = m.gcur, lo_t = m.lu & 0xFFFFu;
-            const uint32_t sec = gc / SV + (ui - (m.lu >> 16));
+            const uint32_t c = m.oc >> 16, gc = m.gcur, lo_t = loff[dd];
+            const uint32_t sec = gc / SV + (ui - uoff[dd]);
             const uint32_t row0 = sec * SV > gc ? sec * SV : gc;
             const Slot *cy = carry + (size_t)dd * (SV - 1);
             Slot tup[SV];
@@ -680,11 +684,11 @@ __global__ void __launch_bounds__(kTmaThreads, 1) scatter_tma_kernel(
             const uint32_t dd = d0 + q;
             if (dd < P) {
                 Slot *cy = carry + (size_t)dd * (SV - 1);
-                const uint32_t lo_t = meta[dd].lu & 0xFFFFu;
+                const uint32_t lo_t = loff[dd];
                 for (uint32_t j = (o_[q] > c_[q] ? o_[q] : c_[q]); j < c_[q] + n_[q]; ++j)
                     cy[j - o_[q]] = buf[lo_t + (j - c_[q])];
                 meta[dd].gcur = gc_[q] + o_[q];
-                meta[dd].cnt = 0;
+                cnt[dd] = 0;
                 ccount[dd] = (uint8_t)(c_[q] + n_[q] - o_[q]);
             }
         }
