@@ -72,7 +72,8 @@ typedef struct hj_rel {
 #define HJ_ALGO_PHJ 2
 
 /* opts.flags */
-#define HJ_FLAG_CHECKSUM 1u /* MATERIALIZE: also compute c0, c1 over the pairs */
+#define HJ_FLAG_CHECKSUM 1u /* MATERIALIZE: also compute c0, c1 over the pairs           */
+#define HJ_FLAG_GRAPH 2u    /* hj_join_batch: capture each wave's launches in a CUDA graph */
 
 typedef struct hj_opts {
     int32_t algo;          /* HJ_ALGO_*                                              */
@@ -144,6 +145,19 @@ hj_status hj_partition_free(hj_ctx *ctx, hj_rel *tuples, uint64_t *offsets);
  * partitioning, per-partition build and probe, and output.  `out` as for hj_probe. */
 hj_status hj_join(hj_ctx *ctx, const hj_rel *R, const hj_rel *S, const hj_opts *opts,
                   hj_result *out);
+
+/* Many independent joins: outs[j] receives the join of Rs[j] and Ss[j] exactly as
+ * hj_join would return it (count, checksums, library-owned pairs).  All relations
+ * share one width; each must have fewer than 2^32 - 1 tuples.  Joins are grouped
+ * by the radix bits their build side needs; every group is partitioned in one
+ * pass per relation side and all (join, partition) pairs of all groups are joined
+ * by ONE persistent launch that takes them from a work counter, so small and large
+ * joins share the GPU.  If the joins' workspace exceeds the HBM budget (the
+ * context's, else 70% of free device memory) they run in several such waves.
+ * opts->flags & HJ_FLAG_GRAPH captures each wave's device work in a CUDA graph and
+ * launches it as one.  opts->algo, radix_bits and passes are ignored. */
+hj_status hj_join_batch(hj_ctx *ctx, int n, const hj_rel *Rs, const hj_rel *Ss, const hj_opts *opts,
+                        hj_result *outs);
 
 /* End-to-end join on HOST buffers: copies R and S from host memory (page-locked
  * memory gives full link speed; pageable works) to device buffers the library

@@ -10,6 +10,40 @@
 
 using namespace hj;
 
+namespace hj {
+
+// A global table released when it goes out of scope.
+struct TableHold {
+    hj_ctx *c;
+    hj_table *t = nullptr;
+    ~TableHold() { table_destroy(c, t); }
+};
+
+// Partitions whose table did not fit in shared memory: SHJ with a global table,
+// task by task (host loop over the listed tasks).
+hj_status oversize_fallback(hj_ctx *c, int W, bool agg, bool chk, const PartTask *tasks, const uint32_t *list_dev,
+                            uint64_t nov, const std::vector<JoinSlot> &slots_host, bool dense, PairSink *sink) {
+    std::vector<uint32_t> list(nov);
+    HJ_CUDA(c, cudaMemcpyAsync(list.data(), list_dev, nov * 4, cudaMemcpyDeviceToHost, c->stream));
+    HJ_CUDA(c, cudaStreamSynchronize(c->stream));
+    for (uint32_t ti : list) {
+        PartTask tk;
+        HJ_CUDA(c, cudaMemcpyAsync(&tk, tasks + ti, sizeof tk, cudaMemcpyDeviceToHost, c->stream));
+        HJ_CUDA(c, cudaStreamSynchronize(c->stream));
+        const PartFilter pf{tk.p, (int)tk.b1, (int)tk.b2, 1};
+        const JoinSlot &js = slots_host[tk.join];
+        TableHold tg{c};
+        HJ_TRY(table_create(c, W, agg, tk.nr, &tg.t));
+        HJ_TRY(table_build(c, tg.t, tk.R, 0, tk.nr, tk.nr, pf));
+        RecArea ra2{nullptr, nullptr, 0};
+        if (!agg && !dense) HJ_TRY(sink->new_area(table_probe_warps(c, tk.ns), &ra2));
+        HJ_TRY(table_probe(c, tg.t, tk.S, 0, tk.ns, tk.ns, js.pairs, js.pcap, chk, ra2, pf, js.ctr, dense));
+    }
+    return HJ_OK;
+}
+
+}  // namespace hj
+
 namespace {
 
 hj_status check_rel(hj_ctx *c, const hj_rel *r, const char *name) {
@@ -188,38 +222,31 @@ hj_status join_shj(hj_ctx *c, const hj_rel *R, const hj_rel *S, const hj_opts &o
 }
 
 // ----------------------------------------------------------------------- PHJ
+__global__ void set_slot_kernel(JoinSlot *s, void *pairs, unsigned long long pcap, hj_counters *ctr) {
+    s->pairs = pairs;
+    s->pcap = pcap;
+    s->ctr = ctr;
+    s->pad = 0;
+}
+
 hj_status run_partition_join(hj_ctx *c, const hj_rel *R, const hj_rel *S, const hj_opts &o, const void *Rp,
-                             const uint64_t *roff, uint64_t r_rows, const void *Sp, const uint64_t *soff,
-                             uint64_t s_rows, uint64_t NP, int b1, int b2, PairSink *sink, uint32_t *oversize) {
+                             const uint64_t *roff, const void *Sp, const uint64_t *soff, uint64_t NP, int b1, int b2,
+                             PairSink *sink, uint32_t *oversize, PartTask *tasks, JoinSlot *slot_dev) {
     const bool agg = is_agg(o.mode), chk = wants_checksum(o), mat = o.mode == HJ_MATERIALIZE;
     const int W = R->width;
     RecArea ra{nullptr, nullptr, 0};
     if (mat) HJ_TRY(sink->new_area(partition_join_warps(c), &ra));
     HJ_TRY(zero_counters(c));
-    uint64_t expect = NP ? (R->n + NP - 1) / NP : 0;
     void *pairs = mat ? sink->pairs.p : nullptr;
-    uint64_t pcap = mat ? sink->pcap : 0;
-    HJ_TRY(partition_join(c, W, agg, Rp, roff, r_rows, Sp, soff, s_rows, NP, expect, pairs, pcap, chk, oversize, ra,
-                          b1, b2, 1));
+    const uint64_t pcap = mat ? sink->pcap : 0;
+    HJ_LAUNCH(c, "set_slot", set_slot_kernel, 1, 1, 0, slot_dev, pairs, (unsigned long long)pcap, c->d_ctr);
+    const uint64_t expect = NP ? (R->n + NP - 1) / NP : 0;
+    HJ_TRY(partition_join(c, W, agg, tasks, NP, slot_dev, expect, chk, oversize, ra, nullptr, 0));
     HJ_TRY(read_counters(c));
-    uint64_t nov = c->h_ctr->n_oversize;
+    const uint64_t nov = c->h_ctr->n_oversize;
     if (nov == 0) return HJ_OK;
-    // Partitions whose table did not fit in shared memory: SHJ with a global table.
-    std::vector<uint32_t> list(nov);
-    std::vector<uint64_t> hr(NP + 1), hs(NP + 1);
-    HJ_CUDA(c, cudaMemcpyAsync(list.data(), oversize, nov * 4, cudaMemcpyDeviceToHost, c->stream));
-    HJ_CUDA(c, cudaMemcpyAsync(hr.data(), roff, (NP + 1) * 8, cudaMemcpyDeviceToHost, c->stream));
-    HJ_CUDA(c, cudaMemcpyAsync(hs.data(), soff, (NP + 1) * 8, cudaMemcpyDeviceToHost, c->stream));
-    HJ_CUDA(c, cudaStreamSynchronize(c->stream));
-    for (uint32_t p : list) {
-        TableGuard tg{c};
-        const PartFilter pf{p, b1, b2, 1};
-        HJ_TRY(table_create(c, W, agg, hr[p + 1] - hr[p], &tg.t));
-        HJ_TRY(table_build(c, tg.t, Rp, hr[p], hr[p + 1], r_rows, pf));
-        RecArea ra2{nullptr, nullptr, 0};
-        if (mat) HJ_TRY(sink->new_area(table_probe_warps(c, hs[p + 1] - hs[p]), &ra2));
-        HJ_TRY(table_probe(c, tg.t, Sp, hs[p], hs[p + 1], s_rows, pairs, pcap, chk, ra2, pf));
-    }
+    std::vector<JoinSlot> slots_host{JoinSlot{pairs, pcap, c->d_ctr, 0}};
+    HJ_TRY(oversize_fallback(c, W, agg, chk, tasks, oversize, nov, slots_host, false, sink));
     HJ_TRY(read_counters(c));
     if (c->h_ctr->status & kStatusTableFull) return set_err(c, HJ_E_CUDA, "hash table unexpectedly full");
     return HJ_OK;
@@ -232,18 +259,22 @@ hj_status join_phj(hj_ctx *c, const hj_rel *R, const hj_rel *S, const hj_opts &o
     if (b1 < 1 || b1 > 12 || b2 < 0 || b2 > 12)
         return set_err(c, HJ_E_INVALID, "radix bits %d in %d passes: each pass takes 1..12 bits", bits, passes);
     const uint64_t NP = 1ull << bits;
-    DevBuf Rp(c), Sp(c), roff(c), soff(c), oversize(c);
+    DevBuf Rp(c), Sp(c), roff(c), soff(c), oversize(c), tasks(c), slot(c);
     PairSink sink(c, R->width);
     uint64_t r_rows = 0, s_rows = 0;
     HJ_TRY(partition_rel(c, R, b1, b2, 1, Rp, roff, &r_rows));
     HJ_TRY(partition_rel(c, S, b1, b2, 1, Sp, soff, &s_rows));
     HJ_TRY(oversize.alloc(NP * 4));
+    HJ_TRY(tasks.alloc(NP * sizeof(PartTask)));
+    HJ_TRY(slot.alloc(sizeof(JoinSlot)));
+    HJ_TRY(make_tasks(c, Rp.p, roff.as<uint64_t>(), Sp.p, soff.as<uint64_t>(), NP, 0, b1, b2, R->width,
+                      tasks.as<PartTask>()));
     const uint64_t warps = partition_join_warps(c);
     uint64_t cap = mat ? first_capacity(o, S->n, warps) : 0;
     for (int attempt = 0; attempt < 2; ++attempt) {
         if (mat) HJ_TRY(sink.reset(cap));
-        HJ_TRY(run_partition_join(c, R, S, o, Rp.p, roff.as<uint64_t>(), r_rows, Sp.p, soff.as<uint64_t>(), s_rows, NP,
-                                  b1, b2, &sink, oversize.as<uint32_t>()));
+        HJ_TRY(run_partition_join(c, R, S, o, Rp.p, roff.as<uint64_t>(), Sp.p, soff.as<uint64_t>(), NP, b1, b2, &sink,
+                                  oversize.as<uint32_t>(), tasks.as<PartTask>(), slot.as<JoinSlot>()));
         if (c->h_ctr->status & 8ull) return set_err(c, HJ_E_CUDA, "output record area overflow");
         if (!mat) break;
         if (c->h_ctr->cursor <= sink.pcap) {

@@ -18,7 +18,9 @@ namespace hj {
 constexpr unsigned kChunkPairs = 1024;
 
 struct ChunkRec {
-    unsigned long long base, used;
+    unsigned long long base;
+    unsigned int used;
+    unsigned int join;
 };
 
 // Where the warps of one launch record their partly filled chunks.
@@ -40,11 +42,15 @@ template <> struct PairOut<8> {
     }
 };
 
-// Output context of a launch.
+// Output context of a launch: the pair buffer of one join and its counters.  With
+// `dense`, every append claims exactly its pairs from ctr->count (no chunks, no
+// holes); otherwise warps take whole chunks from ctr->cursor.
 struct OutCtx {
     void *pairs;
     uint64_t pcap;
     hj_counters *ctr;
+    unsigned int join = 0;
+    bool dense = false;
 };
 
 // Warp-uniform state of a warp's current chunk.
@@ -58,12 +64,19 @@ struct OutState {
 // Append one pair per lane whose `has` is set.  All 32 lanes must call.
 template <int W>
 __device__ __forceinline__ void warp_append(OutState &st, const OutCtx &oc, bool has, typename Tup<W>::U a,
-                                            typename Tup<W>::U b) {
+                                            typename Tup<W>::U b_) {
     const unsigned mask = __ballot_sync(0xffffffffu, has);
     if (!mask) return;
     const unsigned lane = threadIdx.x & 31;
     const unsigned k = __popc(mask);
     const unsigned rank = __popc(mask & ((1u << lane) - 1u));
+    if (oc.dense) {
+        unsigned long long b = 0;
+        if (lane == 0) b = atomicAdd(&oc.ctr->count, (unsigned long long)k);
+        b = __shfl_sync(0xffffffffu, b, 0);
+        if (has && b + rank < oc.pcap) PairOut<W>::put(oc.pairs, b + rank, a, b_);
+        return;
+    }
     const unsigned room = kChunkPairs - st.used;
     unsigned long long nb = 0;
     if (k > room) {
@@ -72,7 +85,7 @@ __device__ __forceinline__ void warp_append(OutState &st, const OutCtx &oc, bool
     }
     if (has) {
         unsigned long long pos = rank < room ? st.base + st.used + rank : nb + (rank - room);
-        if (pos < oc.pcap) PairOut<W>::put(oc.pairs, pos, a, b);
+        if (pos < oc.pcap) PairOut<W>::put(oc.pairs, pos, a, b_);
     }
     if (k > room) {
         st.base = nb;
@@ -87,11 +100,13 @@ __device__ __forceinline__ void warp_append(OutState &st, const OutCtx &oc, bool
 // Record the warp's partly filled chunk and add its pair count.  All lanes call.
 __device__ __forceinline__ void warp_finish(const OutState &st, const OutCtx &oc, const RecArea &ra) {
     if ((threadIdx.x & 31) != 0) return;
+    if (oc.dense) return;  // dense appends count themselves and leave no holes
     if (st.claimed && st.used < kChunkPairs) {
         unsigned long long i = atomicAdd(ra.n, 1ull);
         if (i < ra.cap) {
             ra.rec[i].base = st.base;
             ra.rec[i].used = st.used;
+            ra.rec[i].join = oc.join;
         } else {
             atomicOr(&oc.ctr->status, 8ull);  // record area too small
         }

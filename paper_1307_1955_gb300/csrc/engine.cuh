@@ -22,22 +22,58 @@ hj_status table_build(hj_ctx *c, hj_table *t, const void *R, uint64_t lo, uint64
 // Probe with tuples [lo, hi) of S; counts and checksums accumulate into the
 // context counters, pairs into `pairs` (capacity pcap; unused in count modes).
 // Warps that leave a partly filled output chunk record it in `ra`.
+// ctr: the counters to accumulate into (NULL: the context's); with `dense`
+// every append claims exactly its rows from ctr->count (no chunks, no holes).
 hj_status table_probe(hj_ctx *c, const hj_table *t, const void *S, uint64_t lo, uint64_t hi, uint64_t n_total,
-                      void *pairs, uint64_t pcap, int checksum, RecArea ra, PartFilter pf);
+                      void *pairs, uint64_t pcap, int checksum, RecArea ra, PartFilter pf,
+                      hj_counters *ctr = nullptr, int dense = 0);
 // Number of warps table_probe launches for n probe tuples (record-area size).
 uint64_t table_probe_warps(hj_ctx *c, uint64_t n);
 
+// A partition pair for the shared-memory join: padded partitions (every row
+// range starts on a 32-byte sector, its row count is a multiple of the sector's
+// tuples), their partition index p under pass bits (b1, b2) -- rows hashing
+// elsewhere are padding -- and the join (output target) they belong to.
+struct PartTask {
+    const void *R;
+    const void *S;
+    uint32_t nr, ns;
+    uint32_t join, p;
+    uint16_t b1, b2;
+    uint32_t pad;
+    uint64_t ek1;  // second empty-slot marker candidate for (b1, b2)
+};
+// Output of one join: its pair buffer and its counters.
+struct JoinSlot {
+    void *pairs;
+    unsigned long long pcap;
+    hj_counters *ctr;
+    unsigned long long pad;
+};
+uint64_t empty_key2(int width, int b1, int b2);
+// Tasks for one join's NP partitions (device array `tasks`).
+hj_status make_tasks(hj_ctx *c, const void *Rp, const uint64_t *roff, const void *Sp, const uint64_t *soff,
+                     uint64_t NP, uint32_t join, int b1, int b2, int width, PartTask *tasks);
+
 // Per-partition join (Alg. 2's "apply SHJ on each partition pair") with the
-// table in shared memory, persistent CTAs over nparts pairs.  roff/soff hold
-// nparts+1 row offsets into Rp/Sp.  Partitions whose table does not fit are
-// appended to `oversize` (device, nparts entries) and counted in
-// counters.n_oversize.  counters.work must be zero at launch.  With `filter`,
-// tuples whose hash belongs to another partition (padding) are skipped.
-hj_status partition_join(hj_ctx *c, int width, int agg, const void *Rp, const uint64_t *roff, uint64_t nR_total,
-                         const void *Sp, const uint64_t *soff, uint64_t nS_total, uint64_t nparts,
-                         uint64_t expect_r, void *pairs, uint64_t pcap, int checksum, uint32_t *oversize,
-                         RecArea ra, int b1, int b2, int filter);
+// table in shared memory; persistent CTAs take tasks from c->d_ctr->work (which
+// must be zero at launch).  Tasks whose table does not fit are appended to
+// `oversize` (task indices) and counted in c->d_ctr->n_oversize.  Pairs go to
+// each task's join slot: with `stage` (a staging area of scap pairs per CTA) by
+// exact claims, otherwise by per-warp chunks recorded in `ra`.
+hj_status partition_join(hj_ctx *c, int width, int agg, const PartTask *tasks, uint64_t ntasks, const JoinSlot *slots,
+                         uint64_t expect_r, int checksum, uint32_t *oversize, RecArea ra, void *stage,
+                         uint32_t scap);
 uint64_t partition_join_warps(hj_ctx *c);
+uint64_t partition_join_ctas(hj_ctx *c, int width, int agg, uint64_t expect_r);
+
+struct PairSink;
+// Tasks listed in `list_dev` (nov task indices) whose table did not fit in shared
+// memory: SHJ with a global table per task, into the task's join slot (slots_host
+// mirrors the device slots).  With `dense` pairs are claimed exactly; otherwise
+// warps take chunks recorded in new areas of `sink`.
+hj_status oversize_fallback(hj_ctx *c, int W, bool agg, bool chk, const PartTask *tasks, const uint32_t *list_dev,
+                            uint64_t nov, const std::vector<JoinSlot> &slots_host, bool dense, PairSink *sink);
 
 // ------------------------------------------------------------ partition.cu
 // One radix-partition pass over nseg independent segments of `in` (segment s is
@@ -48,8 +84,11 @@ uint64_t partition_join_warps(hj_ctx *c);
 // run is rounded up to whole 32-byte sectors with padding tuples whose key
 // hashes to another digit, so the output holds up to partition_out_rows() rows
 // and segment s of the output starts where the padded segments before it end.
+// With seg_ptrs (device array of nseg pointers, 16-byte aligned), segment s is read
+// from its own array seg_ptrs[s] instead of from `in` (fan-out at most 2^11).
 hj_status partition_pass(hj_ctx *c, int width, const void *in, uint64_t n_total, const uint64_t *seg_off,
-                         uint64_t nseg, int shift, int bits, void *out, uint64_t *part_off, int pad);
+                         uint64_t nseg, int shift, int bits, void *out, uint64_t *part_off, int pad,
+                         const void *const *seg_ptrs = nullptr);
 uint64_t partition_out_rows(hj_ctx *c, int width, uint64_t n_total, uint64_t nseg, int bits, int pad);
 
 // --------------------------------------------------------------- output.cu

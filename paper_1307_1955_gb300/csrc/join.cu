@@ -11,6 +11,8 @@
 // probe loop).  A probe key with several build matches (duplicate R keys) is
 // walked by the whole warp, 32 consecutive slots at a time -- the GPU answer to
 // the divergence that skew causes in steps b3/p3 (Sec. 3.3, workload divergence).
+#include <type_traits>
+
 #include "common.cuh"
 #include "emit.cuh"
 #include "engine.cuh"
@@ -261,13 +263,13 @@ template <int W, bool AGG>
 __global__ void __launch_bounds__(256) table_probe_kernel(const void *S, uint64_t lo, uint64_t hi, uint64_t n_total,
                                                           const void *slots, uint64_t cap, const TableSide *side,
                                                           void *pairs, uint64_t pcap, RecArea ra, hj_counters *ctr,
-                                                          int chk, PartFilter pf) {
+                                                          int chk, PartFilter pf, int dense) {
     constexpr int PV = Tup<W>::kPerVec, U = ProbeU<W>::value;
     const unsigned warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const unsigned nwarps = (gridDim.x * blockDim.x) >> 5;
     const uint64_t va = lo / PV;
     OutState st;
-    OutCtx oc{pairs, pcap, ctr};
+    OutCtx oc{pairs, pcap, ctr, 0u, dense != 0};
     ProbeAcc acc;
     if constexpr (AGG) {
         AggTab<W> tab{(const AggSlot<W> *)slots, cap, side};
@@ -343,11 +345,12 @@ uint64_t table_probe_warps(hj_ctx *c, uint64_t n) {
 }
 
 hj_status table_probe(hj_ctx *c, const hj_table *t, const void *S, uint64_t lo, uint64_t hi, uint64_t n_total,
-                      void *pairs, uint64_t pcap, int checksum, RecArea ra, PartFilter pf) {
+                      void *pairs, uint64_t pcap, int checksum, RecArea ra, PartFilter pf, hj_counters *ctr, int dense) {
     if (hi <= lo) return HJ_OK;
+    if (!ctr) ctr = c->d_ctr;
     const unsigned grid = (unsigned)(table_probe_warps(c, hi - lo) / 8);
     const TableSide *side = (const TableSide *)t->side;
-#define HJ_TP(WW, AA) HJ_LAUNCH(c, "table_probe", (table_probe_kernel<WW, AA>), grid, 256, 0, S, lo, hi, n_total, t->slots, t->cap, side, pairs, pcap, ra, c->d_ctr, checksum, pf)
+#define HJ_TP(WW, AA) HJ_LAUNCH(c, "table_probe", (table_probe_kernel<WW, AA>), grid, 256, 0, S, lo, hi, n_total, t->slots, t->cap, side, pairs, pcap, ra, ctr, checksum, pf, dense)
     if (t->width == 4) {
         if (t->agg) HJ_TP(4, true); else HJ_TP(4, false);
     } else {
@@ -526,9 +529,9 @@ __device__ __forceinline__ void soa_visit(const SoaTab<W> &t, typename Tup<W>::U
 
 // The whole warp emits every build match of key kk (probe rid ss): a window of
 // 32 slots (32 / G buckets) per step, up to the first bucket that ends the run.
-template <int W>
+template <int W, class Sink>
 __device__ __forceinline__ void soa_coop_emit(const SoaTab<W> &t, typename Tup<W>::U kk, typename Tup<W>::U ss,
-                                              uint32_t home, OutState &st, const OutCtx &oc) {
+                                              uint32_t home, Sink &sink) {
     using T = typename Tup<W>::U;
     constexpr uint32_t G = SoaTab<W>::G, BPW = 32 / G;
     const unsigned lane = threadIdx.x & 31, jb = lane / G, q = lane % G;
@@ -544,16 +547,174 @@ __device__ __forceinline__ void soa_coop_emit(const SoaTab<W> &t, typename Tup<W
         const unsigned endm = __ballot_sync(0xffffffffu, bucket_end && q == 0);
         const unsigned last_lane = endm ? (unsigned)(__ffs(endm) - 1) + G - 1 : 31u;
         const bool m = inr && lane <= last_lane && key == kk;
-        warp_append<W>(st, oc, m, rid, ss);
+        sink.append(m, rid, ss);
         if (endm) break;
     }
 }
 
-template <int W, bool AGG, int NT>
+// ------------------------------------------------------------------ output sinks
+// How a CTA's warps place the pairs of its partition tasks.
+//
+// ChunkSink: every warp takes whole chunks of the join's pair buffer (emit.cuh);
+// partly used chunks are recorded and compacted by the host afterwards.  Used for
+// a single join: no extra traffic, a small host fix-up at the end.
+//
+// StageSink: the CTA appends a task's pairs to its own staging area (global
+// memory, L2-resident) through a shared-memory cursor; when the task is done the
+// CTA claims exactly that many rows of the join's buffer with one atomicAdd and
+// copies them.  Used for batches of joins, where per-warp chunks would leave a
+// partly used chunk per warp per task.  A task whose pairs overflow the staging
+// area places the rest with exact warp-sized claims.  The join's pair count is the
+// claim cursor (ctr->count).
+template <int W> struct ChunkSink {
+    using T = typename Tup<W>::U;
+    OutState st;
+    OutCtx oc;
+    unsigned join = ~0u;
+    const JoinSlot *slots;
+    RecArea ra;
+    __device__ __forceinline__ void begin_task(unsigned j) {
+        if (j == join) return;
+        if (join != ~0u) warp_finish(st, oc, ra);
+        st = OutState();
+        oc = OutCtx{slots[j].pairs, slots[j].pcap, slots[j].ctr, j, false};
+        join = j;
+    }
+    __device__ __forceinline__ void append(bool has, T a, T b) { warp_append<W>(st, oc, has, a, b); }
+    // one append for all single-match items of a group
+    template <int IT>
+    __device__ __forceinline__ void append_group(const uint32_t *cnt, const T *first, const T *r) {
+        const unsigned lane = threadIdx.x & 31, lt = (1u << lane) - 1u;
+        unsigned m[IT], tot = 0;
+#pragma unroll
+        for (int i = 0; i < IT; ++i) {
+            m[i] = __ballot_sync(0xffffffffu, cnt[i] == 1);
+            tot += __popc(m[i]);
+        }
+        if (!tot) return;
+        const unsigned room = kChunkPairs - st.used;
+        unsigned long long nbase = 0;
+        if (tot > room) {
+            if (lane == 0) nbase = atomicAdd(&oc.ctr->cursor, (unsigned long long)kChunkPairs);
+            nbase = __shfl_sync(0xffffffffu, nbase, 0);
+        }
+        unsigned run = 0;
+#pragma unroll
+        for (int i = 0; i < IT; ++i) {
+            if (cnt[i] == 1) {
+                const unsigned rank = run + __popc(m[i] & lt);
+                const unsigned long long pos = rank < room ? st.base + st.used + rank : nbase + (rank - room);
+                if (pos < oc.pcap) PairOut<W>::put(oc.pairs, pos, first[i], r[i]);
+            }
+            run += __popc(m[i]);
+        }
+        if (tot > room) {
+            st.base = nbase;
+            st.used = tot - room;
+            st.claimed = true;
+        } else {
+            st.used += tot;
+        }
+        st.pairs += tot;
+    }
+    __device__ __forceinline__ hj_counters *ctr() const { return oc.ctr; }
+    __device__ __forceinline__ void end_task() {}
+    __device__ __forceinline__ void finish() {
+        if (join != ~0u) warp_finish(st, oc, ra);
+    }
+};
+
+struct StageShared {
+    unsigned int cnt, fail;
+    unsigned long long base;
+};
+
+template <int W> struct StageSink {
+    using T = typename Tup<W>::U;
+    using P = typename std::conditional<W == 4, uint2, ulonglong2>::type;
+    P *stage;  // this CTA's staging area
+    uint32_t scap;
+    StageShared *sh;
+    const JoinSlot *slots;
+    unsigned join = 0;
+    __device__ __forceinline__ static P mk(T a, T b) {
+        if constexpr (W == 4) return make_uint2(a, b);
+        else return make_ulonglong2(a, b);
+    }
+    // every thread calls it at the start of a task (the counters are reset by
+    // thread 0 before the task's first barrier)
+    __device__ __forceinline__ void begin_task(unsigned j) { join = j; }
+    __device__ __forceinline__ void append(bool has, T a, T b) {
+        const unsigned mask = __ballot_sync(0xffffffffu, has);
+        if (!mask) return;
+        const unsigned lane = threadIdx.x & 31, k = __popc(mask), rank = __popc(mask & ((1u << lane) - 1u));
+        unsigned pos = 0;
+        if (lane == 0) pos = atomicAdd(&sh->cnt, k);
+        pos = __shfl_sync(0xffffffffu, pos, 0);
+        if (pos + k <= scap) {
+            if (has) stage[pos + rank] = mk(a, b);
+            return;
+        }
+        // the staging area is full: claim exact rows of the join's buffer
+        if (lane == 0) atomicMin(&sh->fail, pos);
+        unsigned long long g = 0;
+        if (lane == 0) g = atomicAdd(&slots[join].ctr->count, (unsigned long long)k);
+        g = __shfl_sync(0xffffffffu, g, 0);
+        if (has && g + rank < slots[join].pcap) ((P *)slots[join].pairs)[g + rank] = mk(a, b);
+    }
+    template <int IT>
+    __device__ __forceinline__ void append_group(const uint32_t *cnt, const T *first, const T *r) {
+        const unsigned lane = threadIdx.x & 31, lt = (1u << lane) - 1u;
+        unsigned m[IT], tot = 0;
+#pragma unroll
+        for (int i = 0; i < IT; ++i) {
+            m[i] = __ballot_sync(0xffffffffu, cnt[i] == 1);
+            tot += __popc(m[i]);
+        }
+        if (!tot) return;
+        unsigned pos = 0;
+        if (lane == 0) pos = atomicAdd(&sh->cnt, tot);
+        pos = __shfl_sync(0xffffffffu, pos, 0);
+        if (pos + tot <= scap) {
+            unsigned run = 0;
+#pragma unroll
+            for (int i = 0; i < IT; ++i) {
+                if (cnt[i] == 1) stage[pos + run + __popc(m[i] & lt)] = mk(first[i], r[i]);
+                run += __popc(m[i]);
+            }
+            return;
+        }
+        if (lane == 0) atomicMin(&sh->fail, pos);
+        unsigned long long g = 0;
+        if (lane == 0) g = atomicAdd(&slots[join].ctr->count, (unsigned long long)tot);
+        g = __shfl_sync(0xffffffffu, g, 0);
+        unsigned run = 0;
+#pragma unroll
+        for (int i = 0; i < IT; ++i) {
+            const unsigned long long q = g + run + __popc(m[i] & lt);
+            if (cnt[i] == 1 && q < slots[join].pcap) ((P *)slots[join].pairs)[q] = mk(first[i], r[i]);
+            run += __popc(m[i]);
+        }
+    }
+    __device__ __forceinline__ hj_counters *ctr() const { return slots[join].ctr; }
+    // all threads: claim the staged pairs' rows and copy them (contains barriers)
+    __device__ __forceinline__ void end_task() {
+        __syncthreads();
+        const unsigned n = sh->cnt < sh->fail ? sh->cnt : sh->fail;
+        if (threadIdx.x == 0) sh->base = n ? atomicAdd(&slots[join].ctr->count, (unsigned long long)n) : 0ull;
+        __syncthreads();
+        const unsigned long long b = sh->base, pc = slots[join].pcap;
+        P *out = (P *)slots[join].pairs;
+        for (unsigned i = threadIdx.x; i < n; i += blockDim.x)
+            if (b + i < pc) out[b + i] = stage[i];
+    }
+    __device__ __forceinline__ void finish() {}
+};
+
+template <int W, bool AGG, int NT, class Sink>
 __global__ void __launch_bounds__(NT, 2048 / NT / 2) partition_join_kernel(
-    const void *Rp, const uint64_t *roff, const void *Sp, const uint64_t *soff, uint64_t NP, uint32_t cap_max,
-    void *pairs, uint64_t pcap, RecArea ra, hj_counters *ctr, uint32_t *oversize, int chk, int b1, int b2,
-    uint64_t empty_k0, uint64_t empty_k1) {
+    const PartTask *tasks, uint64_t ntasks, const JoinSlot *slots, hj_counters *work, uint32_t cap_max, RecArea ra,
+    uint32_t *oversize, int chk, void *stage_base, uint32_t scap) {
     using T = typename Tup<W>::U;
     using Vec = typename Tup<W>::Vec;
     using Hh = typename HashT<W>::type;
@@ -563,27 +724,41 @@ __global__ void __launch_bounds__(NT, 2048 / NT / 2) partition_join_kernel(
     __shared__ TableSide side;
     __shared__ int s_full;
     __shared__ unsigned long long s_p;
+    __shared__ StageShared s_stage;
     const uint32_t sbase = (uint32_t)__cvta_generic_to_shared(smem);
     const unsigned lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
-    const unsigned lt = (1u << lane) - 1u;
 
-    OutState st;
-    OutCtx oc{pairs, pcap, ctr};
-    ProbeAcc acc;
+    Sink sink;
+    if constexpr (std::is_same<Sink, ChunkSink<W>>::value) {
+        sink.slots = slots;
+        sink.ra = ra;
+    } else {
+        sink.stage = (typename StageSink<W>::P *)stage_base + (size_t)blockIdx.x * scap;
+        sink.scap = scap;
+        sink.sh = &s_stage;
+        sink.slots = slots;
+    }
     for (;;) {
-        if (threadIdx.x == 0) s_p = atomicAdd(&ctr->work, 1ull);
+        if (threadIdx.x == 0) {
+            s_p = atomicAdd(&work->work, 1ull);
+            s_stage.cnt = 0;
+            s_stage.fail = 0xFFFFFFFFu;
+        }
         __syncthreads();
-        const uint64_t p = s_p;
-        if (p >= NP) break;
-        const uint64_t r0 = roff[p], r1 = roff[p + 1], s0 = soff[p], s1 = soff[p + 1];
-        const uint32_t nrv = (uint32_t)((r1 - r0) / PV), nsv = (uint32_t)((s1 - s0) / PV);
-        const Vec *Rv = (const Vec *)Rp + r0 / PV;
-        const Vec *Sv = (const Vec *)Sp + s0 / PV;
-        const uint64_t nr = r1 - r0;  // build rows, padding included
-        const PartFilter pf{(uint32_t)p, b1, b2, 1};
-        bool work = nsv > 0 && nrv > 0;
+        const uint64_t ti = s_p;
+        if (ti >= ntasks) break;
+        const PartTask tk = tasks[ti];
+        const uint32_t nrv = tk.nr / PV, nsv = tk.ns / PV;
+        const Vec *Rv = (const Vec *)tk.R;
+        const Vec *Sv = (const Vec *)tk.S;
+        const uint64_t nr = tk.nr;  // build rows, padding included
+        const PartFilter pf{tk.p, (int)tk.b1, (int)tk.b2, 1};
+        hj_counters *jc = slots[tk.join].ctr;
+        sink.begin_task(tk.join);
+        ProbeAcc acc;
+        bool work_p = nsv > 0 && nrv > 0;
         uint32_t cap = 0;
-        if (work) {
+        if (work_p) {
             if (AGG) {
                 const uint64_t want = 2 * nr + 32;
                 cap = want < cap_max ? (uint32_t)want : cap_max;
@@ -592,15 +767,16 @@ __global__ void __launch_bounds__(NT, 2048 / NT / 2) partition_join_kernel(
                 const uint64_t want = (3 * nr + 127) / 128 * 128;
                 cap = want < cap_max ? (uint32_t)want : cap_max;
                 if (nr >= cap - cap / 4) {  // load factor above 3/4: leave to the fallback
-                    if (threadIdx.x == 0) oversize[atomicAdd(&ctr->n_oversize, 1ull)] = (uint32_t)p;
-                    work = false;
+                    if (threadIdx.x == 0) oversize[atomicAdd(&work->n_oversize, 1ull)] = (uint32_t)ti;
+                    work_p = false;
                 }
             }
         }
         uint32_t *ovf = (uint32_t *)(smem + (size_t)cap_max * (AGG ? sizeof(AggSlot<W>) : 2 * W));
-        const T empty = pf.keep(hashw<W>((T)empty_k0)) ? (T)empty_k1 : (T)empty_k0;
+        const T top = Tup<W>::kAllOnes;
+        const T empty = pf.keep(hashw<W>(top)) ? (T)tk.ek1 : top;
         const SoaTab<W> tab{sbase, sbase + (cap / G) * 16u, cap / G, empty, ovf};
-        if (work) {
+        if (work_p) {
             if (AGG) {
                 AggSlot<W> *sl = (AggSlot<W> *)smem;
                 for (uint32_t i = threadIdx.x; i < cap; i += blockDim.x) {
@@ -657,7 +833,7 @@ __global__ void __launch_bounds__(NT, 2048 / NT / 2) partition_join_kernel(
             }
             __syncthreads();
             if (s_full) {
-                if (threadIdx.x == 0) oversize[atomicAdd(&ctr->n_oversize, 1ull)] = (uint32_t)p;
+                if (threadIdx.x == 0) oversize[atomicAdd(&work->n_oversize, 1ull)] = (uint32_t)ti;
             } else {
                 AggTab<W> atab{(const AggSlot<W> *)smem, cap, &side};
                 const uint32_t gstride = nwarps * 32 * U;
@@ -756,40 +932,7 @@ __global__ void __launch_bounds__(NT, 2048 / NT / 2) partition_join_kernel(
                             cnt[i] = c;
                             first[i] = f;
                         }
-                        // one append for every single-match tuple of the group
-                        unsigned m[IT], tot = 0;
-#pragma unroll
-                        for (int i = 0; i < IT; ++i) {
-                            m[i] = __ballot_sync(0xffffffffu, cnt[i] == 1);
-                            tot += __popc(m[i]);
-                        }
-                        if (tot) {
-                            const unsigned room = kChunkPairs - st.used;
-                            unsigned long long nbase = 0;
-                            if (tot > room) {
-                                if (lane == 0) nbase = atomicAdd(&ctr->cursor, (unsigned long long)kChunkPairs);
-                                nbase = __shfl_sync(0xffffffffu, nbase, 0);
-                            }
-                            unsigned run = 0;
-#pragma unroll
-                            for (int i = 0; i < IT; ++i) {
-                                if (cnt[i] == 1) {
-                                    const unsigned rank = run + __popc(m[i] & lt);
-                                    const unsigned long long pos =
-                                        rank < room ? st.base + st.used + rank : nbase + (rank - room);
-                                    if (pos < pcap) PairOut<W>::put(pairs, pos, first[i], r[i]);
-                                }
-                                run += __popc(m[i]);
-                            }
-                            if (tot > room) {
-                                st.base = nbase;
-                                st.used = tot - room;
-                                st.claimed = true;
-                            } else {
-                                st.used += tot;
-                            }
-                            st.pairs += tot;
-                        }
+                        sink.template append_group<IT>(cnt, first, r);
                         // several matches: the whole warp walks each such key's run
 #pragma unroll
                         for (int i = 0; i < IT; ++i) {
@@ -800,7 +943,7 @@ __global__ void __launch_bounds__(NT, 2048 / NT / 2) partition_join_kernel(
                                 const T kk = __shfl_sync(0xffffffffu, k[i], L);
                                 const T ss = __shfl_sync(0xffffffffu, r[i], L);
                                 const uint32_t hh = __shfl_sync(0xffffffffu, home[i], L);
-                                soa_coop_emit<W>(tab, kk, ss, hh, st, oc);
+                                soa_coop_emit<W>(tab, kk, ss, hh, sink);
                             }
                         }
                     }
@@ -809,10 +952,55 @@ __global__ void __launch_bounds__(NT, 2048 / NT / 2) partition_join_kernel(
                 }
             }
         }
+        flush_acc(jc, acc, AGG);
+        if constexpr (!AGG) sink.end_task();
         __syncthreads();  // every warp is done with this table and with s_p
     }
-    if constexpr (!AGG) warp_finish(st, oc, ra);
-    flush_acc(ctr, acc, AGG);
+    if constexpr (!AGG) sink.finish();
+}
+
+// Tasks of one join partitioned into NP padded partitions: task p covers rows
+// [roff[p], roff[p+1]) of Rp and [soff[p], soff[p+1]) of Sp.
+__global__ void make_tasks_kernel(const void *Rp, const uint64_t *roff, const void *Sp, const uint64_t *soff,
+                                  uint64_t NP, uint32_t join, int b1, int b2, uint64_t ek1, int tb, PartTask *tasks) {
+    for (uint64_t p = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; p < NP; p += (uint64_t)gridDim.x * blockDim.x) {
+        PartTask t;
+        t.R = (const char *)Rp + roff[p] * tb;
+        t.S = (const char *)Sp + soff[p] * tb;
+        t.nr = (uint32_t)(roff[p + 1] - roff[p]);
+        t.ns = (uint32_t)(soff[p + 1] - soff[p]);
+        t.join = join;
+        t.p = (uint32_t)p;
+        t.b1 = (uint16_t)b1;
+        t.b2 = (uint16_t)b2;
+        t.pad = 0;
+        t.ek1 = ek1;
+        tasks[p] = t;
+    }
+}
+
+hj_status make_tasks(hj_ctx *c, const void *Rp, const uint64_t *roff, const void *Sp, const uint64_t *soff,
+                     uint64_t NP, uint32_t join, int b1, int b2, int width, PartTask *tasks) {
+    const unsigned grid = (unsigned)((NP + 255) / 256);
+    HJ_LAUNCH(c, "make_tasks", make_tasks_kernel, grid ? grid : 1, 256, 0, Rp, roff, Sp, soff, NP, join, b1, b2,
+              empty_key2(width, b1, b2), (int)tuple_bytes(width), tasks);
+    return HJ_OK;
+}
+
+// Second empty-marker candidate for pass bits (b1, b2): the first key below the top
+// of the key domain whose partition differs from the top key's.  Padding keys of
+// the partitioner come from the bottom of the domain (0, 1, 2, ...), so a probe key
+// never equals a marker.
+uint64_t empty_key2(int width, int b1, int b2) {
+    auto pidx = [&](uint64_t k) {
+        uint64_t h = width == 4 ? (uint64_t)murmur2_u32((uint32_t)k) : murmur2_u64(k);
+        uint64_t d1 = h & ((1ull << b1) - 1), d2 = b2 ? (h >> b1) & ((1ull << b2) - 1) : 0;
+        return (d1 << b2) | d2;
+    };
+    const uint64_t top = width == 4 ? 0xFFFFFFFFull : ~0ull;
+    uint64_t k = top - 1;
+    while (pidx(k) == pidx(top)) --k;
+    return k;
 }
 
 // Join launch shape: two 512-thread CTAs per SM with tables up to 100 KiB, or one
@@ -830,28 +1018,14 @@ static JoinCfg join_cfg(int width, int agg, uint64_t expect_r) {
 }
 
 uint64_t partition_join_warps(hj_ctx *c) { return (uint64_t)num_sms(c) * 32; }
+uint64_t partition_join_ctas(hj_ctx *c, int width, int agg, uint64_t expect_r) {
+    return (uint64_t)num_sms(c) * (2048 / join_cfg(width, agg, expect_r).nt / 2);
+}
 
-hj_status partition_join(hj_ctx *c, int width, int agg, const void *Rp, const uint64_t *roff, uint64_t nR_total,
-                         const void *Sp, const uint64_t *soff, uint64_t nS_total, uint64_t nparts,
-                         uint64_t expect_r, void *pairs, uint64_t pcap, int checksum, uint32_t *oversize,
-                         RecArea ra, int b1, int b2, int filter) {
-    (void)nR_total;
-    (void)nS_total;
-    (void)filter;
-    if (nparts == 0) return HJ_OK;
-    // Two keys in different partitions: each partition's empty-slot marker is
-    // whichever of them hashes elsewhere.  They come from the top of the key domain;
-    // the padding keys of the partitioner come from the bottom (0, 1, 2, ...), so a
-    // probe key never equals the marker.
-    auto pidx = [&](uint64_t k) {
-        uint64_t h = width == 4 ? (uint64_t)murmur2_u32((uint32_t)k) : murmur2_u64(k);
-        uint64_t d1 = h & ((1ull << b1) - 1), d2 = b2 ? (h >> b1) & ((1ull << b2) - 1) : 0;
-        return (d1 << b2) | d2;
-    };
-    const uint64_t top = width == 4 ? 0xFFFFFFFFull : ~0ull;
-    const uint64_t ek0 = top;
-    uint64_t ek1 = top - 1;
-    while (pidx(ek1) == pidx(ek0)) --ek1;
+hj_status partition_join(hj_ctx *c, int width, int agg, const PartTask *tasks, uint64_t ntasks, const JoinSlot *slots,
+                         uint64_t expect_r, int checksum, uint32_t *oversize, RecArea ra, void *stage,
+                         uint32_t scap) {
+    if (ntasks == 0) return HJ_OK;
     const uint64_t slot_bytes = agg ? (width == 4 ? sizeof(AggSlot<4>) : sizeof(AggSlot<8>)) : 2ull * width;
     const JoinCfg cfg = join_cfg(width, agg, expect_r);
     // Capacity: room for a partition of the expected size plus six standard
@@ -864,23 +1038,33 @@ hj_status partition_join(hj_ctx *c, int width, int agg, const void *Rp, const ui
     uint64_t cap_max = want < max_slots ? want : max_slots;
     if (cap_max < 128) cap_max = 128;
     const size_t smem = (size_t)(cap_max * slot_bytes) + (size_t)((cap_max / 2 / 32 + 1) * 4 + 16);
-    unsigned grid = (unsigned)(num_sms(c) * (2048 / cfg.nt / 2));
-    if (grid > nparts) grid = (unsigned)nparts;
-#define HJ_PJ(WW, AA, NT)                                                                                   \
-    do {                                                                                                    \
-        auto kern = partition_join_kernel<WW, AA, NT>;                                                      \
-        HJ_CUDA(c, cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));     \
-        HJ_LAUNCH(c, "partition_join", kern, grid, NT, smem, Rp, roff, Sp, soff, nparts, (uint32_t)cap_max, \
-                  pairs, pcap, ra, c->d_ctr, oversize, checksum, b1, b2, ek0, ek1);                         \
+    unsigned grid = (unsigned)partition_join_ctas(c, width, agg, expect_r);
+    if (grid > ntasks) grid = (unsigned)ntasks;
+#define HJ_PJ(WW, AA, NT, SK)                                                                                   \
+    do {                                                                                                        \
+        auto kern = partition_join_kernel<WW, AA, NT, SK<WW>>;                                                  \
+        HJ_CUDA(c, cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));         \
+        HJ_LAUNCH(c, "partition_join", kern, grid, NT, smem, tasks, ntasks, slots, c->d_ctr, (uint32_t)cap_max, \
+                  ra, oversize, checksum, stage, scap);                                                         \
+    } while (0)
+#define HJ_PJ_NT(WW, AA, SK)                                   \
+    do {                                                       \
+        if (cfg.nt == 512) HJ_PJ(WW, AA, 512, SK);              \
+        else HJ_PJ(WW, AA, 1024, SK);                           \
+    } while (0)
+#define HJ_PJ_SK(WW, AA)                                       \
+    do {                                                       \
+        if (stage) HJ_PJ_NT(WW, AA, StageSink);                 \
+        else HJ_PJ_NT(WW, AA, ChunkSink);                       \
     } while (0)
     if (width == 4) {
-        if (agg) { if (cfg.nt == 512) HJ_PJ(4, true, 512); else HJ_PJ(4, true, 1024); }
-        else { if (cfg.nt == 512) HJ_PJ(4, false, 512); else HJ_PJ(4, false, 1024); }
+        if (agg) HJ_PJ_NT(4, true, ChunkSink); else HJ_PJ_SK(4, false);
     } else {
-        if (agg) { if (cfg.nt == 512) HJ_PJ(8, true, 512); else HJ_PJ(8, true, 1024); }
-        else { if (cfg.nt == 512) HJ_PJ(8, false, 512); else HJ_PJ(8, false, 1024); }
+        if (agg) HJ_PJ_NT(8, true, ChunkSink); else HJ_PJ_SK(8, false);
     }
 #undef HJ_PJ
+#undef HJ_PJ_NT
+#undef HJ_PJ_SK
     return HJ_OK;
 }
 

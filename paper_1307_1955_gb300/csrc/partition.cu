@@ -161,7 +161,7 @@ template <int W>
 __global__ void __launch_bounds__(kHistThreads) hist_kernel(const void *in, uint64_t n_total, const uint64_t *seg_off,
                                                             uint64_t nseg, const unsigned long long *cb,
                                                             uint64_t chunk, int shift, int bits, int pad,
-                                                            uint32_t *H) {
+                                                            uint32_t *H, const void *const *seg_ptrs) {
     using U = typename Tup<W>::U;
     constexpr int PV = Tup<W>::kPerVec, SV = Sector<W>::kTuples;
     extern __shared__ uint32_t hist[];
@@ -173,8 +173,13 @@ __global__ void __launch_bounds__(kHistThreads) hist_kernel(const void *in, uint
         return;
     }
     const ChunkPos cp = chunk_pos(seg_off, nseg, cb, chunk, g);
+    // tuples come from `in` (global row index), or from the segment's own array
+    const void *src = seg_ptrs ? seg_ptrs[cp.s] : in;
+    const uint64_t ioff = seg_ptrs ? seg_off[cp.s] : 0;
+    const uint64_t nsrc = seg_ptrs ? seg_off[cp.s + 1] - seg_off[cp.s] : n_total;
+    const uint64_t lo = cp.lo - ioff, hi = cp.hi - ioff;
     __syncthreads();
-    const uint64_t va = cp.lo / PV, vb = (cp.hi + PV - 1) / PV;
+    const uint64_t va = lo / PV, vb = (hi + PV - 1) / PV;
     const uint64_t step = (uint64_t)blockDim.x * kHistUnroll;
     U k[kHistUnroll][2], r[kHistUnroll][2], nk[kHistUnroll][2], nr[kHistUnroll][2];
     auto load = [&](uint64_t v0, U (*kk)[2], U (*rr)[2]) {
@@ -182,7 +187,7 @@ __global__ void __launch_bounds__(kHistThreads) hist_kernel(const void *in, uint
         for (int u = 0; u < kHistUnroll; ++u) {
             uint64_t v = v0 + (uint64_t)u * blockDim.x + threadIdx.x;
             kk[u][0] = kk[u][1] = 0;
-            if (v < vb) load_vec_p<W>(in, v, n_total, kk[u], rr[u]);
+            if (v < vb) load_vec_p<W>(src, v, nsrc, kk[u], rr[u]);
         }
     };
     if (va < vb) load(va, k, r);
@@ -194,7 +199,7 @@ __global__ void __launch_bounds__(kHistThreads) hist_kernel(const void *in, uint
 #pragma unroll
             for (int e = 0; e < PV; ++e) {
                 uint64_t t = v * PV + e;
-                if (v < vb && t >= cp.lo && t < cp.hi) atomicAdd(&hist[digit_of(key_hash<W>(k[u][e]), shift, bits)], 1u);
+                if (v < vb && t >= lo && t < hi) atomicAdd(&hist[digit_of(key_hash<W>(k[u][e]), shift, bits)], 1u);
             }
         }
 #pragma unroll
@@ -500,7 +505,7 @@ template <int W>
 __global__ void __launch_bounds__(kTmaThreads, 1) scatter_tma_kernel(
     const void *in, uint64_t n_total, const uint64_t *seg_off, uint64_t nseg, const unsigned long long *cb,
     uint64_t chunk, int shift, int bits, const unsigned long long *Hs, void *out, int pad, uint64_t sent_k0,
-    uint64_t sent_k1, hj_counters *ctr) {
+    uint64_t sent_k1, hj_counters *ctr, const void *const *seg_ptrs) {
     using U = typename Tup<W>::U;
     using TS = TmaShape<W>;
     using Slot = typename SortSlot<W>::T;
@@ -532,7 +537,11 @@ __global__ void __launch_bounds__(kTmaThreads, 1) scatter_tma_kernel(
     const uint64_t obase = seg_start / SV * SV;
     Slot *outp = (Slot *)out + obase;
     const uint64_t tb = 2 * W;
-    const uint64_t last16 = (n_total * tb) / 16 * 16;  // bytes of `in` a 16-byte copy may touch
+    // tuples come from `in` (global row index), or from the segment's own array
+    const void *src = seg_ptrs ? seg_ptrs[cp.s] : in;
+    const uint64_t ioff = seg_ptrs ? seg_off[cp.s] : 0;
+    const uint64_t nsrc = seg_ptrs ? seg_off[cp.s + 1] - seg_off[cp.s] : n_total;
+    const uint64_t last16 = (nsrc * tb) / 16 * 16;  // bytes of `src` a 16-byte copy may touch
     for (uint32_t d = threadIdx.x; d < P; d += blockDim.x) {
         DigitMeta m;
         m.gcur = (uint32_t)(seg_off[0] + Hs[row + (uint64_t)d * cp.nch + cp.cidx] - obase);
@@ -547,9 +556,11 @@ __global__ void __launch_bounds__(kTmaThreads, 1) scatter_tma_kernel(
         fence_mbar_init();
     }
     __syncthreads();
+    // byte range of src staged for the tile of global rows [t0, t1): 16-byte
+    // aligned, inside the array
     auto stage_range = [&](uint64_t t0, uint64_t t1, uint64_t *b0, uint64_t *b1) {
-        *b0 = (t0 * tb) / 16 * 16;
-        uint64_t e = (t1 * tb + 15) / 16 * 16;
+        *b0 = ((t0 - ioff) * tb) / 16 * 16;
+        uint64_t e = ((t1 - ioff) * tb + 15) / 16 * 16;
         *b1 = e < last16 ? e : last16;
     };
     auto issue = [&](uint64_t t0, uint64_t t1) {
@@ -557,7 +568,7 @@ __global__ void __launch_bounds__(kTmaThreads, 1) scatter_tma_kernel(
         stage_range(t0, t1, &b0, &b1);
         if (b1 > b0) {
             mbar_expect_tx(bar, (uint32_t)(b1 - b0));
-            bulk_g2s(stage_s, (const char *)in + b0, (uint32_t)(b1 - b0), bar);
+            bulk_g2s(stage_s, (const char *)src + b0, (uint32_t)(b1 - b0), bar);
         } else {
             mbar_expect_tx(bar, 0);
         }
@@ -581,7 +592,7 @@ __global__ void __launch_bounds__(kTmaThreads, 1) scatter_tma_kernel(
         uint64_t b0, b1;
         stage_range(t0, t1, &b0, &b1);
         const uint32_t ntile = (uint32_t)(t1 - t0);
-        const uint32_t skew = (uint32_t)(t0 - b0 / tb);                   // 0 or 1 leading slots
+        const uint32_t skew = (uint32_t)(t0 - ioff - b0 / tb);            // 0 or 1 leading slots
         const uint32_t staged = b1 > b0 ? (uint32_t)((b1 - b0) / tb) : 0u;
         const uint32_t nstaged = staged > skew ? staged - skew : 0u;       // tuples of the tile in the stage
         U k[IT], r[IT];
@@ -591,7 +602,7 @@ __global__ void __launch_bounds__(kTmaThreads, 1) scatter_tma_kernel(
             const uint32_t t = (uint32_t)i * kTmaThreads + threadIdx.x;
             Slot sl;
             if (t < nstaged) sl = stage[t + skew];
-            else if (t < ntile) sl = ((const Slot *)in)[t0 + t];
+            else if (t < ntile) sl = ((const Slot *)src)[t0 - ioff + t];
             else {
                 if constexpr (W == 4) sl = 0ull;
                 else sl = make_ulonglong2(0ull, 0ull);
@@ -731,13 +742,21 @@ static ScatterCfg scatter_cfg(int width, int bits) {
     return ScatterCfg{1024, 2, 2048, false};
 }
 
+// Chunk size of a pass: about one chunk per SM over the whole input (one scatter
+// CTA fits an SM at the largest fan-out), at most 2^21 rows so that many segments
+// spread over the SMs, a multiple of the scatter tile.
+static uint64_t pass_chunk(hj_ctx *c, int width, int bits, uint64_t n_total) {
+    const uint64_t tile = scatter_cfg(width, bits).tile;
+    const uint64_t target = (uint64_t)num_sms(c);
+    uint64_t chunk = (n_total + target - 1) / target;
+    if (chunk > (1ull << 21)) chunk = 1ull << 21;
+    chunk = ((chunk + tile - 1) / tile) * tile;
+    return chunk < tile ? tile : chunk;
+}
+
 uint64_t partition_out_rows(hj_ctx *c, int width, uint64_t n_total, uint64_t nseg, int bits, int pad) {
     if (!pad) return n_total;
-    const uint64_t tile = scatter_cfg(width, bits).tile;
-    uint64_t target = (uint64_t)num_sms(c);
-    uint64_t chunk = (n_total + target - 1) / (target ? target : 1);
-    chunk = ((chunk + tile - 1) / tile) * tile;
-    if (chunk < tile) chunk = tile;
+    const uint64_t chunk = pass_chunk(c, width, bits, n_total);
     const uint64_t max_chunks = (n_total + chunk - 1) / chunk + nseg;
     const uint64_t sv = 32 / (2 * width);
     return n_total + max_chunks * (1ull << bits) * (sv - 1);
@@ -756,17 +775,14 @@ static void sentinel_keys(int width, int shift, int bits, uint64_t *k0, uint64_t
 }
 
 hj_status partition_pass(hj_ctx *c, int width, const void *in, uint64_t n_total, const uint64_t *seg_off,
-                         uint64_t nseg, int shift, int bits, void *out, uint64_t *part_off, int pad) {
+                         uint64_t nseg, int shift, int bits, void *out, uint64_t *part_off, int pad,
+                         const void *const *seg_ptrs) {
     if (bits < 1 || bits > 12) return set_err(c, HJ_E_INVALID, "partition pass bits %d outside [1, 12]", bits);
     const uint64_t P = 1ull << bits;
     const ScatterCfg cfg = scatter_cfg(width, bits);
-    const uint64_t tile = cfg.tile;
-    // Chunk size: about one chunk per SM over the whole input (one scatter CTA
-    // fits an SM at the largest fan-out), a multiple of the scatter tile.
-    uint64_t target = (uint64_t)num_sms(c);
-    uint64_t chunk = (n_total + target - 1) / (target ? target : 1);
-    chunk = ((chunk + tile - 1) / tile) * tile;
-    if (chunk < tile) chunk = tile;
+    if (seg_ptrs && !cfg.tma)
+        return set_err(c, HJ_E_UNSUPPORTED, "per-segment inputs need a fan-out of at most 2^11");
+    const uint64_t chunk = pass_chunk(c, width, bits, n_total);
     const uint64_t max_chunks = (n_total + chunk - 1) / chunk + nseg;
 
     DevBuf b_nch(c), b_cb(c), b_H(c), b_Hs(c);
@@ -782,9 +798,9 @@ hj_status partition_pass(hj_ctx *c, int width, const void *in, uint64_t n_total,
     HJ_TRY(scan_u32_u64(c, nch, nseg, cb));
     size_t hsmem = P * 4;
     if (width == 4)
-        HJ_LAUNCH(c, "partition_hist", hist_kernel<4>, (unsigned)max_chunks, kHistThreads, hsmem, in, n_total, seg_off, nseg, cb, chunk, shift, bits, pad, H);
+        HJ_LAUNCH(c, "partition_hist", hist_kernel<4>, (unsigned)max_chunks, kHistThreads, hsmem, in, n_total, seg_off, nseg, cb, chunk, shift, bits, pad, H, seg_ptrs);
     else
-        HJ_LAUNCH(c, "partition_hist", hist_kernel<8>, (unsigned)max_chunks, kHistThreads, hsmem, in, n_total, seg_off, nseg, cb, chunk, shift, bits, pad, H);
+        HJ_LAUNCH(c, "partition_hist", hist_kernel<8>, (unsigned)max_chunks, kHistThreads, hsmem, in, n_total, seg_off, nseg, cb, chunk, shift, bits, pad, H, seg_ptrs);
     HJ_TRY(scan_u32_u64(c, H, max_chunks * P, Hs));
     {
         uint64_t n = nseg * P + 1;
@@ -807,11 +823,11 @@ hj_status partition_pass(hj_ctx *c, int width, const void *in, uint64_t n_total,
         if (width == 4) {
             HJ_CUDA(c, cudaFuncSetAttribute(scatter_tma_kernel<4>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)tma_smem));
             HJ_LAUNCH(c, "partition_scatter", scatter_tma_kernel<4>, (unsigned)max_chunks, kTmaThreads, tma_smem, in,
-                      n_total, seg_off, nseg, cb, chunk, shift, bits, Hs, out, pad, k0, k1, c->d_ctr);
+                      n_total, seg_off, nseg, cb, chunk, shift, bits, Hs, out, pad, k0, k1, c->d_ctr, seg_ptrs);
         } else {
             HJ_CUDA(c, cudaFuncSetAttribute(scatter_tma_kernel<8>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)tma_smem));
             HJ_LAUNCH(c, "partition_scatter", scatter_tma_kernel<8>, (unsigned)max_chunks, kTmaThreads, tma_smem, in,
-                      n_total, seg_off, nseg, cb, chunk, shift, bits, Hs, out, pad, k0, k1, c->d_ctr);
+                      n_total, seg_off, nseg, cb, chunk, shift, bits, Hs, out, pad, k0, k1, c->d_ctr, seg_ptrs);
         }
     } else if (width == 4) {
         if (cfg.nt == 512) HJ_SC(4, 512, 8); else HJ_SC(4, 1024, 2);

@@ -18,6 +18,7 @@ HJ_OK, HJ_E_INVALID, HJ_E_NOMEM, HJ_E_OVERFLOW, HJ_E_CUDA, HJ_E_TIMEOUT, HJ_E_UN
 HJ_COUNT, HJ_COUNT_CHECKSUM, HJ_MATERIALIZE = 0, 1, 2
 HJ_ALGO_AUTO, HJ_ALGO_SHJ, HJ_ALGO_PHJ = 0, 1, 2
 HJ_FLAG_CHECKSUM = 1
+HJ_FLAG_GRAPH = 2
 
 _STATUS = {0: "HJ_OK", 1: "HJ_E_INVALID", 2: "HJ_E_NOMEM", 3: "HJ_E_OVERFLOW", 4: "HJ_E_CUDA",
            5: "HJ_E_TIMEOUT", 6: "HJ_E_UNSUPPORTED", 7: "HJ_E_PENDING"}
@@ -77,6 +78,7 @@ def load_library(path: str = LIB_PATH):
         "hj_result_free": (I32, [V, P(hj_result)]),
         "hj_join_host": (I32, [V, P(hj_rel), P(hj_rel), P(hj_opts), V, U64, P(hj_result)]),
         "hj_join_static": (I32, [P(hj_rel), P(hj_rel), V, V, U64, P(U64), P(U64)]),
+        "hj_join_batch": (I32, [V, ctypes.c_int, P(hj_rel), P(hj_rel), P(hj_opts), P(hj_result)]),
         "hj_sync": (I32, [V]),
         "hj_copy": (I32, [V, V, V, U64]),
         "hj_prof_enable": (I32, [V, ctypes.c_int]),
@@ -246,6 +248,26 @@ def hj_join_host(ctx: Context, R: torch.Tensor, S: torch.Tensor, pairs_out: torc
     _check(ctx, load_library().hj_join_host(ctx.handle, ctypes.byref(r), ctypes.byref(s), ctypes.byref(o), ptr,
                                             cap, ctypes.byref(res)))
     return _result(ctx, res)
+
+
+def hj_join_batch(ctx: Context, Rs: list, Ss: list, mode: int = HJ_MATERIALIZE, out_capacity: int = 0,
+                  checksum: bool = False, graph: bool = False) -> list:
+    """Many independent joins: Rs[j] join Ss[j] for every j, one Result each."""
+    n = len(Rs)
+    if len(Ss) != n:
+        raise ValueError("Rs and Ss differ in length")
+    ra = (hj_rel * max(n, 1))(*[rel_of(t) for t in Rs])
+    sa = (hj_rel * max(n, 1))(*[rel_of(t) for t in Ss])
+    outs = (hj_result * max(n, 1))()
+    flags = (HJ_FLAG_CHECKSUM if checksum else 0) | (HJ_FLAG_GRAPH if graph else 0)
+    o = hj_opts(HJ_ALGO_AUTO, mode, 0, 0, out_capacity, flags)
+    _check(ctx, load_library().hj_join_batch(ctx.handle, n, ra, sa, ctypes.byref(o), outs))
+    res = []
+    for j in range(n):
+        r = hj_result()
+        ctypes.pointer(r)[0] = outs[j]
+        res.append(_result(ctx, r))
+    return res
 
 
 def hj_join_static(R: torch.Tensor, S: torch.Tensor, pairs: torch.Tensor | None, stream=None):

@@ -214,3 +214,83 @@ def to_numpy_u(rel: torch.Tensor):
 
     a = rel.detach().cpu().contiguous().numpy()
     return a.view(np.uint32 if a.dtype == np.int32 else np.uint64)
+
+
+# ------------------------------------------------------------------ batched relations
+
+
+def _bijection_vec(x: torch.Tensor, kbits: torch.Tensor, keys: torch.Tensor) -> torch.Tensor:
+    """_bijection with a per-element bit width and per-element round keys [rounds, n]."""
+    mask = (torch.ones_like(kbits) << kbits) - 1
+    s = torch.clamp((kbits + 1) // 2, min=1)
+    for r in range(keys.shape[0]):
+        mult = (0xD1B54A32D192ED03 + 2 * r * 0x2545F4914F6CDD1D) | 1
+        x = (x * _s64(mult)) & mask
+        x = x ^ (x >> s)
+        x = x ^ (keys[r] & mask)
+    return x
+
+
+def _segments(sizes: list[int]) -> list[int]:
+    """Start rows of consecutive segments, each starting on an even row (16-byte
+    aligned for 4-byte tuples); the last entry is the total row count."""
+    out, at = [], 0
+    for n in sizes:
+        out.append(at)
+        at += n + (n & 1)
+    out.append(at)
+    return out
+
+
+def batched_relations(specs: list, seed: int, device, ids: tuple = (4,), chunk: int = 1 << 26):
+    """All joins of a batch in two big int32 tensors: join j's R is rows
+    [r_start[j], r_start[j] + n_r) of R_all (likewise S), byte-identical to
+    unique_and_uniform(n_r, n_s, s_domain, seed, ids=ids + (j,)).  Returns
+    (R_all, S_all, r_start, s_start)."""
+    nj = len(specs)
+    rs = _segments([sp.n_r for sp in specs])
+    ss = _segments([sp.n_s for sp in specs])
+    R = torch.zeros((rs[-1], 2), dtype=torch.int32, device=device)
+    S = torch.zeros((ss[-1], 2), dtype=torch.int32, device=device)
+    # per-join parameters (CPU), gathered per element on the device
+    pr = [stream_id(seed, *ids, j, 1) for j in range(nj)]
+    ps = [stream_id(seed, *ids, j, 2) for j in range(nj)]
+    kb = [max(2, math.ceil(math.log2(sp.n_r))) if sp.n_r > 1 else 0 for sp in specs]
+    rkeys = torch.tensor([[_s64(_fin_int(pr[j] + r + 1)) for j in range(nj)] for r in range(4)], dtype=torch.int64,
+                         device=device)
+    t_nr = torch.tensor([sp.n_r for sp in specs], dtype=torch.int64, device=device)
+    t_dom = torch.tensor([sp.s_domain for sp in specs], dtype=torch.int64, device=device)
+    t_kb = torch.tensor(kb, dtype=torch.int64, device=device)
+    t_ps = torch.tensor([_s64(x) for x in ps], dtype=torch.int64, device=device)
+    t_rs = torch.tensor(rs, dtype=torch.int64, device=device)
+    t_ss = torch.tensor(ss, dtype=torch.int64, device=device)
+    t_ns = torch.tensor([sp.n_s for sp in specs], dtype=torch.int64, device=device)
+    for a in range(0, rs[-1], chunk):
+        row = torch.arange(a, min(a + chunk, rs[-1]), dtype=torch.int64, device=device)
+        j = torch.searchsorted(t_rs, row, right=True) - 1
+        local = row - t_rs[j]
+        live = local < t_nr[j]
+        nr = t_nr[j]
+        x = local.clone()
+        big = live & (nr > 1)
+        kj = t_kb[j]
+        keys = rkeys[:, j]
+        y = _bijection_vec(x, kj, keys)
+        while True:
+            bad = big & (y >= nr)
+            if not bool(bad.any()):
+                break
+            y = torch.where(bad, _bijection_vec(y, kj, keys), y)
+        key = torch.where(big, y, local) + 1
+        blk = torch.stack([_u32_bits(key), _u32_bits(local)], dim=1)
+        R[a:a + len(row)] = torch.where(live[:, None], blk, torch.zeros_like(blk))
+    for a in range(0, ss[-1], chunk):
+        row = torch.arange(a, min(a + chunk, ss[-1]), dtype=torch.int64, device=device)
+        j = torch.searchsorted(t_ss, row, right=True) - 1
+        local = row - t_ss[j]
+        live = local < t_ns[j]
+        w = _fin((local + 1) * _s64(GAMMA) + t_ps[j])
+        key = ((_srl(w, 32) * t_dom[j]) >> 32) + 1
+        blk = torch.stack([_u32_bits(key), _u32_bits(local)], dim=1)
+        S[a:a + len(row)] = torch.where(live[:, None], blk, torch.zeros_like(blk))
+    return R, S, rs[:-1], ss[:-1]

@@ -115,3 +115,15 @@ def test_serving_specs_ranges():
     for sp in specs:
         assert 1 << 12 <= sp.n_r <= 1 << 24
         assert sp.n_r <= sp.n_s <= 16 * sp.n_r
+
+
+def test_batched_relations_equal_per_join_generation():
+    specs = W.batched_specs(40, 3, lo_log2=1, hi_log2=12)
+    specs[3] = W.JoinSpec(1, 4, 2)
+    specs[4] = W.JoinSpec(0, 0, 1)
+    R, S, rs, ss = W.batched_relations(specs, 3, "cpu", chunk=1000)
+    for j, sp in enumerate(specs):
+        r1, s1 = W.unique_and_uniform(sp.n_r, sp.n_s, sp.s_domain, 3, "cpu", ids=(4, j))
+        assert torch.equal(R[rs[j]:rs[j] + sp.n_r], r1)
+        assert torch.equal(S[ss[j]:ss[j] + sp.n_s], s1)
+        assert rs[j] % 2 == 0 and ss[j] % 2 == 0       # 16-byte aligned segments
