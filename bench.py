@@ -36,6 +36,11 @@ WORKLOADS = {
         nr=1 << 24, ns=1 << 28, dom=1 << 25, algo=2,
         desc="PHJ radix-partitioned join, |R|=2^24, |S|=2^28 (uint32 key, uint32 rid); R keys a seeded "
              "permutation of 1..2^24, S keys uniform over [1, 2^25] (~50% match); pairs materialised"),
+    "batch_4096": dict(
+        kind="batch", njoins=4096, nr=0, ns=0, algo=2,
+        desc="4096 independent joins, |R| log-uniform in [2^10, 2^22], |S| = 4|R| (uint32 key, uint32 rid); "
+             "R keys a permutation of 1..|R|, S keys uniform over [1, ceil(|R|/0.75)] (75% match); pairs "
+             "materialised; one hj_join_batch call (CUDA graph per wave) per step vs one hj_join per join"),
     "shj_1m": dict(
         nr=1 << 20, ns=1 << 20, dom=1 << 20, algo=1,
         desc="SHJ, |R|=|S|=2^20 (uint32 key, uint32 rid); R keys a permutation of 1..2^20, S keys drawn "
@@ -53,6 +58,7 @@ def parse():
     ap.add_argument("--radix-bits", type=int, default=0)
     ap.add_argument("--passes", type=int, default=0)
     ap.add_argument("--e2e-steps", type=int, default=3)
+    ap.add_argument("--plain-steps", type=int, default=2)
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-clocks", action="store_true")
@@ -216,6 +222,9 @@ def run_reference(args, wl, ws, rank):
     oracle.build()
     total = args.steps + args.warmup
     per_step = max(0.05, min(20.0, 150.0 / max(total, 1)))
+    if wl.get("kind") == "batch":
+        run_reference_batch(args, wl, ws, per_step)
+        return
     # Scale the workload down (|S| / |R| and the key-domain ratio kept) so that one
     # step takes about per_step seconds: time the oracle at 1/256 and extrapolate.
     cal = 256
@@ -242,6 +251,42 @@ def run_reference(args, wl, ws, rank):
         "config": {"workload": wl["desc"], "sample_scale": f"1/{scale} of |R| and |S|"},
         "cpu_baseline": {"value": value, "unit": UNIT, "kind": "oracle", "cores": 1,
                          "sample": f"|R|={len(Rn)}, |S|={len(Sn)} (the workload scaled by 1/{scale}), "
+                                   f"single-threaded C oracle hash join, pairs materialised"},
+        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+
+
+def run_reference_batch(args, wl, ws, per_step):
+    """Oracle on the batch's joins in order: each step joins the first joins of the
+    batch whose oracle time adds up to about per_step seconds."""
+    from paper_1307_1955_gb300 import workload as W
+
+    specs = W.batched_specs(wl["njoins"], W.DEFAULT_SEED)
+    sample, acc = [], 0.0
+    for j, sp in enumerate(specs):
+        R, S = W.unique_and_uniform(sp.n_r, sp.n_s, sp.s_domain, W.DEFAULT_SEED, "cpu", ids=(4, j))
+        sample.append((W.to_numpy_u(R), W.to_numpy_u(S)))
+        acc += oracle_rate(*sample[-1])[1]
+        if acc >= per_step:
+            break
+    tuples = sum(len(r) + len(s) for r, s in sample)
+    for _ in range(args.warmup):
+        for r, s in sample[:1]:
+            oracle_rate(r, s)
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        for r, s in sample:
+            oracle_rate(r, s)
+    dt = time.perf_counter() - t0
+    value = tuples * args.steps / dt
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": 1000 * dt / max(args.steps, 1), "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "u32", "data": "synthetic",
+        "config": {"workload": wl["desc"], "sample": f"the first {len(sample)} of {len(specs)} joins"},
+        "cpu_baseline": {"value": value, "unit": UNIT, "kind": "oracle", "cores": 1,
+                         "sample": f"the first {len(sample)} joins of the batch ({tuples} tuples), "
                                    f"single-threaded C oracle hash join, pairs materialised"},
         "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
@@ -378,12 +423,158 @@ def run_hj(args, wl, ws, rank, local):
         dist.destroy_process_group()
 
 
+def batch_inputs(wl, rank, dev):
+    from paper_1307_1955_gb300 import workload as W
+
+    seed = W.DEFAULT_SEED + rank
+    specs = W.batched_specs(wl["njoins"], seed)
+    R_all, S_all, rs, ss = W.batched_relations(specs, seed, dev)
+    Rs = [R_all[rs[j]:rs[j] + sp.n_r] for j, sp in enumerate(specs)]
+    Ss = [S_all[ss[j]:ss[j] + sp.n_s] for j, sp in enumerate(specs)]
+    return specs, R_all, S_all, Rs, Ss
+
+
+def batch_cpu_sample(Rs, Ss, target_s: float):
+    """The oracle over the batch's joins in order until about target_s seconds."""
+    from paper_1307_1955_gb300 import workload as W
+
+    tuples, dt, k, pairs = 0, 0.0, 0, 0
+    while k < len(Rs) and dt < target_s:
+        n, t, m = oracle_rate(W.to_numpy_u(Rs[k]), W.to_numpy_u(Ss[k]))
+        tuples += n
+        dt += t
+        pairs += m
+        k += 1
+    return {"value": tuples / dt, "unit": UNIT, "cores": 1, "kind": "oracle",
+            "sample": f"the first {k} of {len(Rs)} joins ({tuples} tuples, {pairs} pairs materialised), "
+                      f"single-threaded C oracle, {dt:.1f} s"}
+
+
+def run_batch(args, wl, ws, rank, local):
+    """Config of many uneven joins: hj_join_batch (one persistent join launch per wave,
+    CUDA graph) against one hj_join call per join, on the same resident inputs."""
+    import torch
+    import torch.distributed as dist
+
+    import __graft_entry__
+
+    if ws > 1:
+        dist.init_process_group("nccl" if torch.cuda.is_available() else "gloo")
+    torch.cuda.set_device(local)
+    if rank == 0:
+        __graft_entry__.build()
+    if ws > 1:
+        dist.barrier()
+    from paper_1307_1955_gb300 import hj
+
+    dev = torch.device("cuda", local)
+    specs, R_all, S_all, Rs, Ss = batch_inputs(wl, rank, dev)
+    torch.cuda.synchronize()
+    tuples_step = sum(sp.n_r + sp.n_s for sp in specs)
+    stream = torch.cuda.current_stream(dev)
+    ctx = hj.Context(local, stream=stream)
+    ra, sa = hj.rel_array(Rs), hj.rel_array(Ss)
+    n = len(specs)
+
+    def batched(graph=True):
+        outs = hj.hj_join_batch(ctx, ra, sa, graph=graph, raw=True)
+        counts = [outs[j].count for j in range(n)]
+        hj.hj_results_free(ctx, outs, n)
+        return counts
+
+    def plain():
+        for j in range(n):
+            hj.hj_join(ctx, Rs[j], Ss[j]).free()
+
+    def timed(fn, steps):
+        if ws > 1:
+            dist.barrier()
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(steps):
+            out = fn()
+        e1.record(stream)
+        torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1)
+        if ws > 1:
+            t = torch.tensor([ms], device=dev)
+            dist.all_reduce(t, op=dist.ReduceOp.MAX)
+            ms = float(t.item())
+        return ms, out
+
+    for _ in range(args.warmup):
+        counts = batched()
+    sampler = ClockSampler(local)
+    if not args.no_clocks:
+        sampler.start()
+        time.sleep(0.3)
+    l0 = hj.launch_count(ctx)
+    ms, counts = timed(batched, args.steps)
+    launches = hj.launch_count(ctx) - l0
+    clocks = sampler.stop() if not args.no_clocks else None
+    pairs = sum(counts)
+    value = tuples_step * args.steps * ws / (ms / 1000.0)
+
+    # the same joins one hj_join call at a time
+    plain()
+    psteps = max(1, min(args.steps, args.plain_steps))
+    pms, _ = timed(plain, psteps)
+    plain_value = tuples_step * psteps * ws / (pms / 1000.0)
+
+    # kernel times from one profiled step without the graph (events are not captured)
+    hj.prof_reset(ctx)
+    hj.prof_enable(ctx, True)
+    batched(graph=False)
+    torch.cuda.synchronize()
+    prof = hj.prof_read(ctx)
+    hj.prof_enable(ctx, False)
+    peak, peak_kind = measured_peak()
+    dom_name, (dom_launches, dom_ms) = max(prof.items(), key=lambda kv: kv[1][1])
+    wl1 = {"nr": sum(sp.n_r for sp in specs), "ns": sum(sp.n_s for sp in specs)}
+    bytes_k = kernel_bytes(dom_name, wl1, 4, 1, pairs)
+    achieved = bytes_k / (dom_ms / 1000.0) / 1e9 if dom_ms > 0 else 0.0
+    roofline = {"bound": "hbm", "kernel": dom_name, "achieved": achieved, "peak": peak, "unit": "GB/s",
+                "frac": achieved / peak, "peak_kind": peak_kind, "bytes_per_launch": bytes_k / max(dom_launches, 1),
+                "launches": dom_launches, "avg_launch_ms": dom_ms / max(dom_launches, 1),
+                "traffic": traffic_record(dom_name, args.workload)}
+    join_bytes = 3 * 8 * tuples_step + 8 * pairs
+    step_s = ms / 1000.0 / args.steps
+    join_roof = {"bytes_per_step": join_bytes, "achieved_gbs": join_bytes / step_s / 1e9,
+                 "frac": join_bytes / step_s / 1e9 / peak}
+    kernels = {k: {"launches": v[0], "ms": v[1], "share": v[1] / sum(x[1] for x in prof.values())}
+               for k, v in sorted(prof.items(), key=lambda kv: -kv[1][1])}
+    cpu = None
+    if rank == 0 and not args.no_cpu_baseline:
+        cpu = batch_cpu_sample(Rs, Ss, 12.0)
+    if rank == 0:
+        line = {
+            "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "u32", "data": "synthetic",
+            "config": {"workload": wl["desc"], "joins": n, "tuples_per_step": tuples_step,
+                       "pairs_per_step": pairs, "parallelism": f"replicas x{ws}",
+                       "l2": f"inputs {8 * tuples_step / 1e9:.1f} GB per step exceed the 129 MB L2; no flush"},
+            "plain": {"value": plain_value, "unit": UNIT, "ms_per_step": pms / psteps, "steps": psteps,
+                      "api": "hj_join once per join"},
+            "batched_vs_plain": value / plain_value,
+            "roofline": roofline, "join_roofline": join_roof, "kernels": kernels,
+            "cpu_baseline": cpu, "e2e": None, "gpu_launches": launches, "clocks": clocks,
+        }
+        print(json.dumps(line), flush=True)
+    ctx.close()
+    if ws > 1:
+        dist.destroy_process_group()
+
+
 def main():
     args = parse()
     ws, rank, local = dist_env()
     wl = WORKLOADS[args.workload]
     if args.impl == "reference":
         run_reference(args, wl, ws, rank)
+    elif wl.get("kind") == "batch":
+        run_batch(args, wl, ws, rank, local)
     else:
         run_hj(args, wl, ws, rank, local)
 

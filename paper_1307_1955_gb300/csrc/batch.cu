@@ -205,9 +205,14 @@ extern "C" hj_status hj_join_batch(hj_ctx *c, int n, const hj_rel *Rs, const hj_
         if (mat) ws += (Ss[j].n + 64) * tb;
         return ws;
     };
+    // free device memory plus what the context's pool holds reserved but unused
     size_t freeb = 0, totalb = 0;
     cudaMemGetInfo(&freeb, &totalb);
-    uint64_t budget = (uint64_t)(freeb * 0.7);
+    unsigned long long reserved = 0, used_pool = 0;  // the attributes are 64-bit
+    cudaMemPoolGetAttribute(c->pool, cudaMemPoolAttrReservedMemCurrent, &reserved);
+    cudaMemPoolGetAttribute(c->pool, cudaMemPoolAttrUsedMemCurrent, &used_pool);
+    const uint64_t avail = freeb + (reserved > used_pool ? reserved - used_pool : 0);
+    uint64_t budget = (uint64_t)(avail * 0.7);
     if (c->budget) budget = std::min<uint64_t>(budget, c->budget > c->in_use ? (c->budget - c->in_use) * 9 / 10 : 0);
 
     // waves
@@ -292,8 +297,7 @@ extern "C" hj_status hj_join_batch(hj_ctx *c, int n, const hj_rel *Rs, const hj_
                 if (e != cudaSuccess) st = cuda_err(c, e, "cudaGraphInstantiate");
             }
             if (st == HJ_OK) {
-                c->launches++;
-                e = cudaGraphLaunch(ge, c->stream);
+                e = cudaGraphLaunch(ge, c->stream);  // its kernels were counted at capture
                 if (e != cudaSuccess) st = cuda_err(c, e, "cudaGraphLaunch");
             }
             if (st == HJ_OK) {

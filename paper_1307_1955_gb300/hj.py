@@ -250,24 +250,40 @@ def hj_join_host(ctx: Context, R: torch.Tensor, S: torch.Tensor, pairs_out: torc
     return _result(ctx, res)
 
 
-def hj_join_batch(ctx: Context, Rs: list, Ss: list, mode: int = HJ_MATERIALIZE, out_capacity: int = 0,
-                  checksum: bool = False, graph: bool = False) -> list:
-    """Many independent joins: Rs[j] join Ss[j] for every j, one Result each."""
+def rel_array(tensors: list) -> ctypes.Array:
+    """hj_rel structs of many relations, built once and passed to hj_join_batch."""
+    return (hj_rel * len(tensors))(*[rel_of(t) for t in tensors])
+
+
+def hj_join_batch(ctx: Context, Rs, Ss, mode: int = HJ_MATERIALIZE, out_capacity: int = 0,
+                  checksum: bool = False, graph: bool = False, raw: bool = False):
+    """Many independent joins: Rs[j] join Ss[j] for every j.  Rs and Ss are lists of
+    relations or arrays from rel_array().  Returns one Result per join, or with raw=True
+    the hj_result array itself (free it with hj_results_free)."""
     n = len(Rs)
     if len(Ss) != n:
         raise ValueError("Rs and Ss differ in length")
-    ra = (hj_rel * max(n, 1))(*[rel_of(t) for t in Rs])
-    sa = (hj_rel * max(n, 1))(*[rel_of(t) for t in Ss])
+    ra = Rs if isinstance(Rs, ctypes.Array) else rel_array(Rs)
+    sa = Ss if isinstance(Ss, ctypes.Array) else rel_array(Ss)
     outs = (hj_result * max(n, 1))()
     flags = (HJ_FLAG_CHECKSUM if checksum else 0) | (HJ_FLAG_GRAPH if graph else 0)
     o = hj_opts(HJ_ALGO_AUTO, mode, 0, 0, out_capacity, flags)
     _check(ctx, load_library().hj_join_batch(ctx.handle, n, ra, sa, ctypes.byref(o), outs))
+    if raw:
+        return outs
     res = []
     for j in range(n):
         r = hj_result()
         ctypes.pointer(r)[0] = outs[j]
         res.append(_result(ctx, r))
     return res
+
+
+def hj_results_free(ctx: Context, outs: ctypes.Array, n: int | None = None):
+    """Free the first n results of an hj_result array (all of them by default)."""
+    lib = load_library()
+    for j in range(len(outs) if n is None else n):
+        _check(ctx, lib.hj_result_free(ctx.handle, ctypes.byref(outs[j])))
 
 
 def hj_join_static(R: torch.Tensor, S: torch.Tensor, pairs: torch.Tensor | None, stream=None):
