@@ -22,7 +22,7 @@ struct TableHold {
 // Partitions whose table did not fit in shared memory: SHJ with a global table,
 // task by task (host loop over the listed tasks).
 hj_status oversize_fallback(hj_ctx *c, int W, bool agg, bool chk, const PartTask *tasks, const uint32_t *list_dev,
-                            uint64_t nov, const std::vector<JoinSlot> &slots_host, bool dense, PairSink *sink) {
+                            uint64_t nov, const std::vector<JoinSlot> &slots_host) {
     std::vector<uint32_t> list(nov);
     HJ_CUDA(c, cudaMemcpyAsync(list.data(), list_dev, nov * 4, cudaMemcpyDeviceToHost, c->stream));
     HJ_CUDA(c, cudaStreamSynchronize(c->stream));
@@ -35,9 +35,8 @@ hj_status oversize_fallback(hj_ctx *c, int W, bool agg, bool chk, const PartTask
         TableHold tg{c};
         HJ_TRY(table_create(c, W, agg, tk.nr, &tg.t));
         HJ_TRY(table_build(c, tg.t, tk.R, 0, tk.nr, tk.nr, pf));
-        RecArea ra2{nullptr, nullptr, 0};
-        if (!agg && !dense) HJ_TRY(sink->new_area(table_probe_warps(c, tk.ns), &ra2));
-        HJ_TRY(table_probe(c, tg.t, tk.S, 0, tk.ns, tk.ns, js.pairs, js.pcap, chk, ra2, pf, js.ctr, dense));
+        const RecArea none{nullptr, nullptr, 0};
+        HJ_TRY(table_probe(c, tg.t, tk.S, 0, tk.ns, tk.ns, js.pairs, js.pcap, chk, none, pf, js.ctr, 1));
     }
     return HJ_OK;
 }
@@ -173,6 +172,12 @@ struct TableGuard {
     ~TableGuard() { table_destroy(c, t); }
 };
 
+hj_status check_output_status(hj_ctx *c) {
+    if (c->h_ctr->status & kStatusRecords) return set_err(c, HJ_E_CUDA, "output record area overflow");
+    if (c->h_ctr->status & kStatusCompact) return set_err(c, HJ_E_CUDA, "output compaction mismatch");
+    return HJ_OK;
+}
+
 // Initial pair capacity: the caller's hint, else |S| (every probe tuple matching
 // once), plus one chunk per emitting warp for the holes of partly filled chunks.
 uint64_t first_capacity(const hj_opts &o, uint64_t nS, uint64_t warps) {
@@ -194,15 +199,12 @@ hj_status probe_into(hj_ctx *c, const hj_table *t, const hj_rel *S, const hj_opt
         }
         HJ_TRY(zero_counters(c));
         HJ_TRY(table_probe(c, t, S->tuples, 0, S->n, S->n, sink.pairs.p, sink.pcap, chk, ra, PartFilter{0, 0, 0, 0}));
+        if (mat) HJ_TRY(sink.finalize_device(c->d_ctr));
         HJ_TRY(read_counters(c));
-        if (c->h_ctr->status & 8ull) return set_err(c, HJ_E_CUDA, "output record area overflow");
-        if (!mat) break;
-        if (c->h_ctr->cursor <= sink.pcap) {
-            HJ_TRY(sink.finalize(c->h_ctr->count, c->h_ctr->cursor));
-            break;
-        }
+        HJ_TRY(check_output_status(c));
+        if (!mat || c->h_ctr->cursor <= sink.pcap) break;
         // more pairs than the capacity: run the probe again at the exact size
-        cap = c->h_ctr->cursor + warps * kChunkPairs;
+        cap = c->h_ctr->count + warps * kChunkPairs;
         if (attempt == 1) return set_err(c, HJ_E_CUDA, "pair capacity still too small after resizing");
     }
     fill_result(c, res, t->width, HJ_ALGO_SHJ, 0, 0);
@@ -242,11 +244,15 @@ hj_status run_partition_join(hj_ctx *c, const hj_rel *R, const hj_rel *S, const 
     HJ_LAUNCH(c, "set_slot", set_slot_kernel, 1, 1, 0, slot_dev, pairs, (unsigned long long)pcap, c->d_ctr);
     const uint64_t expect = NP ? (R->n + NP - 1) / NP : 0;
     HJ_TRY(partition_join(c, W, agg, tasks, NP, slot_dev, expect, chk, oversize, ra, nullptr, 0));
+    if (mat) HJ_TRY(sink->finalize_device(c->d_ctr));
     HJ_TRY(read_counters(c));
+    HJ_TRY(check_output_status(c));
     const uint64_t nov = c->h_ctr->n_oversize;
     if (nov == 0) return HJ_OK;
+    // partitions whose table did not fit shared memory: global tables, pairs claimed
+    // exactly after the compacted ones (counted even past the capacity)
     std::vector<JoinSlot> slots_host{JoinSlot{pairs, pcap, c->d_ctr, 0}};
-    HJ_TRY(oversize_fallback(c, W, agg, chk, tasks, oversize, nov, slots_host, false, sink));
+    HJ_TRY(oversize_fallback(c, W, agg, chk, tasks, oversize, nov, slots_host));
     HJ_TRY(read_counters(c));
     if (c->h_ctr->status & kStatusTableFull) return set_err(c, HJ_E_CUDA, "hash table unexpectedly full");
     return HJ_OK;
@@ -275,15 +281,9 @@ hj_status join_phj(hj_ctx *c, const hj_rel *R, const hj_rel *S, const hj_opts &o
         if (mat) HJ_TRY(sink.reset(cap));
         HJ_TRY(run_partition_join(c, R, S, o, Rp.p, roff.as<uint64_t>(), Sp.p, soff.as<uint64_t>(), NP, b1, b2, &sink,
                                   oversize.as<uint32_t>(), tasks.as<PartTask>(), slot.as<JoinSlot>()));
-        if (c->h_ctr->status & 8ull) return set_err(c, HJ_E_CUDA, "output record area overflow");
-        if (!mat) break;
-        if (c->h_ctr->cursor <= sink.pcap) {
-            HJ_TRY(sink.finalize(c->h_ctr->count, c->h_ctr->cursor));
-            break;
-        }
-        uint64_t extra = 0;
-        for (auto cp : sink.caps) extra += cp;
-        cap = c->h_ctr->cursor + extra * kChunkPairs;
+        if (!mat || (c->h_ctr->cursor <= sink.pcap && c->h_ctr->count <= sink.pcap)) break;
+        // more pairs than the buffer holds: the count is exact, run again at that size
+        cap = c->h_ctr->count + warps * kChunkPairs;
         if (attempt == 1) return set_err(c, HJ_E_CUDA, "pair capacity still too small after resizing");
     }
     fill_result(c, res, R->width, HJ_ALGO_PHJ, bits, passes);

@@ -315,7 +315,7 @@ extern "C" hj_status hj_join_batch(hj_ctx *c, int n, const hj_rel *Rs, const hj_
             for (int j = 0; j < n; ++j)
                 sh[j] = JoinSlot{pairs[j], cap[j], ctrs.as<hj_counters>() + j, 0};
             st = oversize_fallback(c, W, agg, chk, w.tasks->as<PartTask>(), w.oversize->as<uint32_t>(),
-                                   c->h_ctr->n_oversize, sh, true, nullptr);
+                                   c->h_ctr->n_oversize, sh);
             if (st == HJ_OK) st = read_counters(c);
         }
         if (st == HJ_OK && (c->h_ctr->status & (kStatusTableFull | kStatusTimeout)))

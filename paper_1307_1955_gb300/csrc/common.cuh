@@ -376,6 +376,8 @@ enum : int {
     kStatusTableFull = 1,
     kStatusTimeout = 2,
     kStatusBadInput = 4,
+    kStatusRecords = 8,    // a chunk-record area was too small
+    kStatusCompact = 16,   // device compaction found holes and tail pairs of different sizes
 };
 
 }  // namespace hj

@@ -5,9 +5,8 @@
 // a chunk of kChunkPairs output slots from the global cursor with one atomicAdd
 // and appends the pairs its lanes find with ballot/popc offsets -- no block-wide
 // barrier, one global atomic per kChunkPairs pairs.  A warp's last chunk is
-// usually partly filled; the warp records (base, used) so that the host can plan a
-// small move of pairs from the tail into those holes, after which pairs[0, count)
-// is dense.
+// usually partly filled; the warp records (base, used) so that a small device-side
+// move of pairs from the tail into those holes makes pairs[0, count) dense.
 #pragma once
 
 #include "common.cuh"
@@ -108,7 +107,7 @@ __device__ __forceinline__ void warp_finish(const OutState &st, const OutCtx &oc
             ra.rec[i].used = st.used;
             ra.rec[i].join = oc.join;
         } else {
-            atomicOr(&oc.ctr->status, 8ull);  // record area too small
+            atomicOr(&oc.ctr->status, (unsigned long long)kStatusRecords);
         }
     }
     if (st.pairs) atomicAdd(&oc.ctr->count, st.pairs);

@@ -70,10 +70,10 @@ uint64_t partition_join_ctas(hj_ctx *c, int width, int agg, uint64_t expect_r);
 struct PairSink;
 // Tasks listed in `list_dev` (nov task indices) whose table did not fit in shared
 // memory: SHJ with a global table per task, into the task's join slot (slots_host
-// mirrors the device slots).  With `dense` pairs are claimed exactly; otherwise
-// warps take chunks recorded in new areas of `sink`.
+// mirrors the device slots).  Pairs are claimed exactly at the slot's count, after
+// the pairs already there.
 hj_status oversize_fallback(hj_ctx *c, int W, bool agg, bool chk, const PartTask *tasks, const uint32_t *list_dev,
-                            uint64_t nov, const std::vector<JoinSlot> &slots_host, bool dense, PairSink *sink);
+                            uint64_t nov, const std::vector<JoinSlot> &slots_host);
 
 // ------------------------------------------------------------ partition.cu
 // One radix-partition pass over nseg independent segments of `in` (segment s is
@@ -104,7 +104,9 @@ struct PairSink {
     PairSink(hj_ctx *ctx, int w) : c(ctx), width(w), pairs(ctx) {}
     hj_status reset(uint64_t cap_pairs);                 // (re)allocate the buffer, drop records
     hj_status new_area(uint64_t warps, RecArea *ra);     // record area for one launch
-    hj_status finalize(uint64_t count, uint64_t cursor);
+    // Device-planned compaction of the single record area, stream-ordered after the
+    // join: no host round trip.  Does nothing when the cursor ran past the capacity.
+    hj_status finalize_device(hj_counters *ctr);
 };
 
 // Tuple bytes of a relation of `width`-byte fields.

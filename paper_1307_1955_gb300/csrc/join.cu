@@ -711,7 +711,96 @@ template <int W> struct StageSink {
     __device__ __forceinline__ void finish() {}
 };
 
-template <int W, bool AGG, int NT, class Sink>
+// Probe of S_p against the partition's shared-memory table when no checksum is
+// wanted: the lean form of the loop below.  An insert moves past a bucket only
+// while the bucket is full and slots never empty again, so a set overflow bit
+// implies a full bucket: the overflow bit alone says whether a key's run goes on,
+// and no slot is compared with the empty marker.  Whole groups (every lane's U
+// vectors inside S_p) need no per-item validity tests; only the last group does.
+template <int W, int U, class Sink>
+__device__ __forceinline__ void probe_fast(const SoaTab<W> &tab, const typename Tup<W>::Vec *Sv, uint32_t nsv,
+                                           Sink &sink, unsigned warp, unsigned nwarps, unsigned lane) {
+    using T = typename Tup<W>::U;
+    using Vec = typename Tup<W>::Vec;
+    constexpr int PV = Tup<W>::kPerVec, IT = U * PV;
+    constexpr uint32_t G = SoaTab<W>::G;
+    const uint32_t gstride = nwarps * 32u * U;
+    uint32_t g = warp * 32u * U;
+    Vec cur[U], nxt[U];
+#pragma unroll
+    for (int u = 0; u < U; ++u) {
+        const uint32_t rel = g + u * 32u + lane;
+        if (rel < nsv) cur[u] = ld_stream(Sv + rel);
+    }
+    for (; g < nsv; g += gstride) {
+        const uint32_t gn = g + gstride;
+#pragma unroll
+        for (int u = 0; u < U; ++u) {
+            const uint32_t rel = gn + u * 32u + lane;
+            if (rel < nsv) nxt[u] = ld_stream(Sv + rel);
+        }
+        const bool whole = g + 32u * U <= nsv;
+        T k[IT], r[IT];
+        uint32_t vmask = 0;  // items inside S_p
+#pragma unroll
+        for (int u = 0; u < U; ++u) {
+            if constexpr (W == 4) {
+                k[2 * u] = cur[u].x; r[2 * u] = cur[u].y; k[2 * u + 1] = cur[u].z; r[2 * u + 1] = cur[u].w;
+            } else {
+                k[u] = cur[u].x; r[u] = cur[u].y;
+            }
+            if (whole || g + u * 32u + lane < nsv) vmask |= ((1u << PV) - 1u) << (u * PV);
+        }
+        uint32_t cnt[IT], home[IT];
+        T first[IT];
+#pragma unroll
+        for (int i = 0; i < IT; ++i) {
+            home[i] = part_bucket<W>(k[i], tab.nb);
+            T key[G];
+            tab.ld(home[i], 0, key);
+            uint32_t m = 0;
+#pragma unroll
+            for (uint32_t q = 0; q < G; ++q) m |= (uint32_t)(key[q] == k[i]) << q;
+            if (!((vmask >> i) & 1u)) m = 0;
+            T f = 0;
+            if (m) {
+                T rid[G];
+                tab.ld(home[i], 1, rid);
+                f = rid[G - 1];
+#pragma unroll
+                for (int q = (int)G - 2; q >= 0; --q)
+                    if ((m >> q) & 1u) f = rid[q];
+            }
+            uint32_t c = __popc(m);
+            if (((vmask >> i) & 1u) && tab.overflowed(home[i])) {  // the run goes on (rare)
+                const uint32_t nx = home[i] + 1 == tab.nb ? 0 : home[i] + 1;
+                T f2 = 0;
+                const uint32_t c2 = soa_lookup<W>(tab, k[i], nx, &f2);
+                if (c == 0) f = f2;
+                c += c2;
+            }
+            cnt[i] = c;
+            first[i] = f;
+        }
+        sink.template append_group<IT>(cnt, first, r);
+#pragma unroll
+        for (int i = 0; i < IT; ++i) {
+            unsigned multi = __ballot_sync(0xffffffffu, cnt[i] > 1);
+            while (multi) {
+                const int L = __ffs(multi) - 1;
+                multi &= multi - 1;
+                const T kk = __shfl_sync(0xffffffffu, k[i], L);
+                const T ss = __shfl_sync(0xffffffffu, r[i], L);
+                const uint32_t hh = __shfl_sync(0xffffffffu, home[i], L);
+                soa_coop_emit<W>(tab, kk, ss, hh, sink);
+            }
+        }
+#pragma unroll
+        for (int u = 0; u < U; ++u) cur[u] = nxt[u];
+    }
+}
+
+template <int W, bool AGG, int NT, class Sink, bool FAST>
 __global__ void __launch_bounds__(NT, 2048 / NT / 2) partition_join_kernel(
     const PartTask *tasks, uint64_t ntasks, const JoinSlot *slots, hj_counters *work, uint32_t cap_max, RecArea ra,
     uint32_t *oversize, int chk, void *stage_base, uint32_t scap) {
@@ -836,6 +925,9 @@ __global__ void __launch_bounds__(NT, 2048 / NT / 2) partition_join_kernel(
                 if (threadIdx.x == 0) oversize[atomicAdd(&work->n_oversize, 1ull)] = (uint32_t)ti;
             } else {
                 AggTab<W> atab{(const AggSlot<W> *)smem, cap, &side};
+                if constexpr (FAST) {  // no aggregate, no checksum
+                    probe_fast<W, U>(tab, Sv, nsv, sink, warp, nwarps, lane);
+                } else {
                 const uint32_t gstride = nwarps * 32 * U;
                 Vec cur[U], nxt[U];
                 uint32_t g = warp * 32 * U;
@@ -950,6 +1042,7 @@ __global__ void __launch_bounds__(NT, 2048 / NT / 2) partition_join_kernel(
 #pragma unroll
                     for (int u = 0; u < U; ++u) cur[u] = nxt[u];
                 }
+                }
             }
         }
         flush_acc(jc, acc, AGG);
@@ -1040,31 +1133,37 @@ hj_status partition_join(hj_ctx *c, int width, int agg, const PartTask *tasks, u
     const size_t smem = (size_t)(cap_max * slot_bytes) + (size_t)((cap_max / 2 / 32 + 1) * 4 + 16);
     unsigned grid = (unsigned)partition_join_ctas(c, width, agg, expect_r);
     if (grid > ntasks) grid = (unsigned)ntasks;
-#define HJ_PJ(WW, AA, NT, SK)                                                                                   \
+#define HJ_PJ(WW, AA, NT, SK, FF)                                                                               \
     do {                                                                                                        \
-        auto kern = partition_join_kernel<WW, AA, NT, SK<WW>>;                                                  \
+        auto kern = partition_join_kernel<WW, AA, NT, SK<WW>, FF>;                                              \
         HJ_CUDA(c, cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));         \
         HJ_LAUNCH(c, "partition_join", kern, grid, NT, smem, tasks, ntasks, slots, c->d_ctr, (uint32_t)cap_max, \
                   ra, oversize, checksum, stage, scap);                                                         \
     } while (0)
-#define HJ_PJ_NT(WW, AA, SK)                                   \
-    do {                                                       \
-        if (cfg.nt == 512) HJ_PJ(WW, AA, 512, SK);              \
-        else HJ_PJ(WW, AA, 1024, SK);                           \
+#define HJ_PJ_NT(WW, AA, SK, FF)                                \
+    do {                                                        \
+        if (cfg.nt == 512) HJ_PJ(WW, AA, 512, SK, FF);           \
+        else HJ_PJ(WW, AA, 1024, SK, FF);                        \
     } while (0)
-#define HJ_PJ_SK(WW, AA)                                       \
-    do {                                                       \
-        if (stage) HJ_PJ_NT(WW, AA, StageSink);                 \
-        else HJ_PJ_NT(WW, AA, ChunkSink);                       \
+#define HJ_PJ_F(WW, SK)                                         \
+    do {                                                        \
+        if (checksum) HJ_PJ_NT(WW, false, SK, false);            \
+        else HJ_PJ_NT(WW, false, SK, true);                      \
+    } while (0)
+#define HJ_PJ_SK(WW)                                            \
+    do {                                                        \
+        if (stage) HJ_PJ_F(WW, StageSink);                       \
+        else HJ_PJ_F(WW, ChunkSink);                             \
     } while (0)
     if (width == 4) {
-        if (agg) HJ_PJ_NT(4, true, ChunkSink); else HJ_PJ_SK(4, false);
+        if (agg) HJ_PJ_NT(4, true, ChunkSink, false); else HJ_PJ_SK(4);
     } else {
-        if (agg) HJ_PJ_NT(8, true, ChunkSink); else HJ_PJ_SK(8, false);
+        if (agg) HJ_PJ_NT(8, true, ChunkSink, false); else HJ_PJ_SK(8);
     }
 #undef HJ_PJ
 #undef HJ_PJ_NT
 #undef HJ_PJ_SK
+#undef HJ_PJ_F
     return HJ_OK;
 }
 

@@ -1,11 +1,14 @@
 // output.cu -- the pair buffer of a materialising join and its final compaction.
 //
 // Warps fill whole chunks of kChunkPairs slots (emit.cuh); each warp's last chunk
-// is usually partly used.  After the join kernels finish, the host reads the
-// recorded partial chunks, pairs the holes below `count` with the valid pairs at
-// or above `count`, and one small kernel moves those pairs, so that
-// pairs[0, count) is dense.  The moved volume is at most one chunk per warp.
-#include <algorithm>
+// is usually partly used.  After the join kernels finish, two small kernels make
+// pairs[0, count) dense without a round trip to the host: one CTA reads the
+// recorded partial chunks, lists the holes below `count` and the valid runs at or
+// above `count` with prefix sums over both lists, and a warp per hole then moves
+// the matching tail pairs into it.  The moved volume is at most one chunk per
+// warp.  Both kernels read count and cursor from the device counters, and leave
+// the buffer untouched when the cursor ran past the capacity (the caller then runs
+// the join again with a larger buffer).
 #include <memory>
 #include <vector>
 
@@ -14,15 +17,160 @@
 
 namespace hj {
 
-struct Move {
-    unsigned long long src, dst, len;
+// Scratch of the device-side compaction, after the records of an area:
+// [plan][tail_used: cap + 2][dst_start, dst_pref: cap + 1 each][src_start, src_pref: cap + 3 each]
+struct CompactPlan {
+    unsigned long long ndst, nsrc, total, pad;
 };
 
+static uint64_t area_bytes(uint64_t warps) {
+    return 16 + warps * sizeof(ChunkRec) + sizeof(CompactPlan) + (warps + 2) * 4 + 8 /*align*/ +
+           2 * (warps + 1) * 8 + 2 * (warps + 3) * 8;
+}
+
+struct PlanView {
+    CompactPlan *plan;
+    uint32_t *tail_used;
+    unsigned long long *dst_start, *dst_pref, *src_start, *src_pref;
+};
+
+__host__ __device__ inline PlanView plan_view(void *area, uint64_t warps) {
+    char *p = (char *)area + 16 + warps * sizeof(ChunkRec);
+    PlanView v;
+    v.plan = (CompactPlan *)p;
+    p += sizeof(CompactPlan);
+    v.tail_used = (uint32_t *)p;
+    p += ((warps + 2) * 4 + 7) / 8 * 8;
+    v.dst_start = (unsigned long long *)p;
+    v.dst_pref = v.dst_start + (warps + 1);
+    v.src_start = v.dst_pref + (warps + 1);
+    v.src_pref = v.src_start + (warps + 3);
+    return v;
+}
+
+// Block-wide exclusive scan of 64-bit values (1024 threads at most); *total gets the sum.
+__device__ unsigned long long block_scan_u64(unsigned long long v, unsigned long long *sh, unsigned long long *total) {
+    const unsigned lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = (blockDim.x + 31) >> 5;
+    unsigned long long x = v;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const unsigned long long y = __shfl_up_sync(0xffffffffu, x, o);
+        if (lane >= (unsigned)o) x += y;
+    }
+    if (lane == 31) sh[warp] = x;
+    __syncthreads();
+    if (warp == 0) {
+        unsigned long long w = lane < nw ? sh[lane] : 0ull;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const unsigned long long y = __shfl_up_sync(0xffffffffu, w, o);
+            if (lane >= (unsigned)o) w += y;
+        }
+        if (lane < nw) sh[lane] = w;  // inclusive warp totals
+    }
+    __syncthreads();
+    const unsigned long long before = warp ? sh[warp - 1] : 0ull;
+    *total = sh[nw - 1];
+    __syncthreads();
+    return before + x - v;
+}
+
+__global__ void __launch_bounds__(1024) compact_plan_kernel(const unsigned long long *nrec_p, const ChunkRec *rec,
+                                                            uint64_t cap, hj_counters *ctr, uint64_t pcap,
+                                                            PlanView pv) {
+    __shared__ unsigned long long sh[32];
+    const unsigned long long count = ctr->count, cursor = ctr->cursor;
+    if (cursor > pcap || count >= cursor) {
+        if (threadIdx.x == 0) pv.plan->ndst = pv.plan->total = 0;
+        return;
+    }
+    const uint64_t n = *nrec_p < cap ? *nrec_p : cap;
+    const uint64_t tb = count / kChunkPairs, nt = (cursor + kChunkPairs - 1) / kChunkPairs - tb;  // nt <= n + 2
+    for (uint64_t t = threadIdx.x; t < nt; t += blockDim.x) pv.tail_used[t] = kChunkPairs;
+    __syncthreads();
+    for (uint64_t i = threadIdx.x; i < n; i += blockDim.x) {
+        const uint64_t ci = rec[i].base / kChunkPairs;
+        if (ci >= tb && ci < tb + nt) pv.tail_used[ci - tb] = rec[i].used;
+    }
+    __syncthreads();
+    // holes below count, in record order
+    unsigned long long nd = 0, dp = 0;
+    for (uint64_t b = 0; b < n; b += blockDim.x) {
+        const uint64_t i = b + threadIdx.x;
+        unsigned long long s0 = 0, len = 0;
+        if (i < n) {
+            const ChunkRec r = rec[i];
+            s0 = r.base + r.used;
+            const unsigned long long e = r.base + kChunkPairs < count ? r.base + kChunkPairs : count;
+            len = s0 < e ? e - s0 : 0ull;
+        }
+        unsigned long long tf, tl;
+        const unsigned long long xf = block_scan_u64(len ? 1ull : 0ull, sh, &tf);
+        const unsigned long long xl = block_scan_u64(len, sh, &tl);
+        if (len) {
+            pv.dst_start[nd + xf] = s0;
+            pv.dst_pref[nd + xf] = dp + xl;
+        }
+        nd += tf;
+        dp += tl;
+    }
+    // valid runs of the tail chunks, in address order
+    unsigned long long ns = 0, sp = 0;
+    for (uint64_t b = 0; b < nt; b += blockDim.x) {
+        const uint64_t t = b + threadIdx.x;
+        unsigned long long a = 0, len = 0;
+        if (t < nt) {
+            const unsigned long long cb = (tb + t) * kChunkPairs, ce = cb + pv.tail_used[t];
+            a = cb > count ? cb : count;
+            const unsigned long long e = ce < cursor ? ce : cursor;
+            len = a < e ? e - a : 0ull;
+        }
+        unsigned long long tf, tl;
+        const unsigned long long xf = block_scan_u64(len ? 1ull : 0ull, sh, &tf);
+        const unsigned long long xl = block_scan_u64(len, sh, &tl);
+        if (len) {
+            pv.src_start[ns + xf] = a;
+            pv.src_pref[ns + xf] = sp + xl;
+        }
+        ns += tf;
+        sp += tl;
+    }
+    if (threadIdx.x == 0) {
+        pv.dst_pref[nd] = dp;
+        pv.src_pref[ns] = sp;
+        if (dp != sp) {  // the holes must take exactly the tail's pairs
+            atomicOr(&ctr->status, (unsigned long long)kStatusCompact);
+            nd = 0;
+        }
+        pv.plan->ndst = nd;
+        pv.plan->nsrc = ns;
+        pv.plan->total = dp;
+    }
+}
+
 template <class P>
-__global__ void move_pairs_kernel(P *pairs, const Move *moves, uint64_t nmoves) {
-    for (uint64_t m = blockIdx.x; m < nmoves; m += gridDim.x) {
-        const Move mv = moves[m];
-        for (uint64_t i = threadIdx.x; i < mv.len; i += blockDim.x) pairs[mv.dst + i] = pairs[mv.src + i];
+__global__ void compact_move_kernel(P *pairs, PlanView pv) {
+    const unsigned lane = threadIdx.x & 31;
+    const uint64_t nd = pv.plan->ndst, ns = pv.plan->nsrc;
+    const uint64_t w0 = (blockIdx.x * (uint64_t)blockDim.x + threadIdx.x) >> 5;
+    const uint64_t nw = ((uint64_t)gridDim.x * blockDim.x) >> 5;
+    for (uint64_t i = w0; i < nd; i += nw) {
+        const unsigned long long ds = pv.dst_start[i], m0 = pv.dst_pref[i], m1 = pv.dst_pref[i + 1];
+        // the source run holding move index m0: last t with src_pref[t] <= m0
+        uint64_t lo = 0, hi = ns;
+        while (hi - lo > 1) {
+            const uint64_t mid = (lo + hi) / 2;
+            if (pv.src_pref[mid] <= m0) lo = mid;
+            else hi = mid;
+        }
+        unsigned long long m = m0;
+        for (uint64_t t = lo; m < m1 && t < ns; ++t) {
+            const unsigned long long o = m - pv.src_pref[t], avail = pv.src_pref[t + 1] - m;
+            const unsigned long long k = avail < m1 - m ? avail : m1 - m;
+            const unsigned long long src = pv.src_start[t] + o, dst = ds + (m - m0);
+            for (unsigned long long j = lane; j < k; j += 32) pairs[dst + j] = pairs[src + j];
+            m += k;
+        }
     }
 }
 
@@ -35,7 +183,7 @@ hj_status PairSink::reset(uint64_t cap_pairs) {
 
 hj_status PairSink::new_area(uint64_t warps, RecArea *ra) {
     auto b = std::make_unique<DevBuf>(c);
-    HJ_TRY(b->alloc(16 + warps * sizeof(ChunkRec)));
+    HJ_TRY(b->alloc(area_bytes(warps)));
     HJ_CUDA(c, cudaMemsetAsync(b->p, 0, 16, c->stream));
     ra->n = (unsigned long long *)b->p;
     ra->rec = (ChunkRec *)((char *)b->p + 16);
@@ -45,67 +193,18 @@ hj_status PairSink::new_area(uint64_t warps, RecArea *ra) {
     return HJ_OK;
 }
 
-hj_status PairSink::finalize(uint64_t count, uint64_t cursor) {
-    if (cursor > pcap) return set_err(c, HJ_E_CUDA, "pair cursor %llu beyond capacity %llu",
-                                      (unsigned long long)cursor, (unsigned long long)pcap);
-    if (count == cursor) return HJ_OK;
-    std::vector<ChunkRec> recs;
-    for (size_t i = 0; i < areas.size(); ++i) {
-        unsigned long long n = 0;
-        HJ_CUDA(c, cudaMemcpyAsync(&n, areas[i]->p, 8, cudaMemcpyDeviceToHost, c->stream));
-        HJ_CUDA(c, cudaStreamSynchronize(c->stream));
-        n = std::min<unsigned long long>(n, caps[i]);
-        size_t old = recs.size();
-        recs.resize(old + n);
-        if (n)
-            HJ_CUDA(c, cudaMemcpyAsync(recs.data() + old, (char *)areas[i]->p + 16, n * sizeof(ChunkRec),
-                                       cudaMemcpyDeviceToHost, c->stream));
-    }
-    HJ_CUDA(c, cudaStreamSynchronize(c->stream));
-    // holes [base + used, base + kChunkPairs), sorted
-    std::vector<std::pair<uint64_t, uint64_t>> holes;
-    for (auto &r : recs)
-        if (r.used < kChunkPairs) holes.push_back({r.base + r.used, r.base + kChunkPairs});
-    std::sort(holes.begin(), holes.end());
-    // holes below count, and valid ranges in [count, cursor)
-    std::vector<std::pair<uint64_t, uint64_t>> dst, src;
-    uint64_t at = count;
-    for (auto &h : holes) {
-        if (h.first < count) dst.push_back({h.first, std::min<uint64_t>(h.second, count)});
-        uint64_t a = std::max<uint64_t>(h.first, count);
-        if (a > at) src.push_back({at, a});
-        if (h.second > at) at = std::max<uint64_t>(at, h.second);
-    }
-    if (cursor > at) src.push_back({at, cursor});
-    uint64_t nd = 0, ns = 0;
-    for (auto &d : dst) nd += d.second - d.first;
-    for (auto &s : src) ns += s.second - s.first;
-    if (nd != ns)
-        return set_err(c, HJ_E_CUDA, "output compaction mismatch: %llu holes, %llu tail pairs",
-                       (unsigned long long)nd, (unsigned long long)ns);
-    std::vector<Move> moves;
-    size_t i = 0, j = 0;
-    uint64_t di = dst.empty() ? 0 : dst[0].first, sj = src.empty() ? 0 : src[0].first;
-    while (i < dst.size() && j < src.size()) {
-        uint64_t len = std::min(dst[i].second - di, src[j].second - sj);
-        moves.push_back({sj, di, len});
-        di += len;
-        sj += len;
-        if (di == dst[i].second && ++i < dst.size()) di = dst[i].first;
-        if (sj == src[j].second && ++j < src.size()) sj = src[j].first;
-    }
-    if (moves.empty()) return HJ_OK;
-    DevBuf dm(c);
-    HJ_TRY(dm.alloc(moves.size() * sizeof(Move)));
-    HJ_CUDA(c, cudaMemcpyAsync(dm.p, moves.data(), moves.size() * sizeof(Move), cudaMemcpyHostToDevice, c->stream));
-    unsigned grid = (unsigned)std::min<size_t>(moves.size(), (size_t)num_sms(c) * 8);
+hj_status PairSink::finalize_device(hj_counters *ctr) {
+    if (areas.size() != 1) return set_err(c, HJ_E_CUDA, "device compaction takes one record area");
+    void *a = areas[0]->p;
+    const uint64_t warps = caps[0];
+    const PlanView pv = plan_view(a, warps);
+    HJ_LAUNCH(c, "pairs_plan", compact_plan_kernel, 1, 1024, 0, (const unsigned long long *)a,
+              (const ChunkRec *)((char *)a + 16), warps, ctr, pcap, pv);
+    const unsigned grid = (unsigned)num_sms(c) * 4;
     if (width == 4)
-        HJ_LAUNCH(c, "pairs_compact", move_pairs_kernel<uint2>, grid, 256, 0, (uint2 *)pairs.p, dm.as<Move>(),
-                  (uint64_t)moves.size());
+        HJ_LAUNCH(c, "pairs_compact", compact_move_kernel<uint2>, grid, 256, 0, (uint2 *)pairs.p, pv);
     else
-        HJ_LAUNCH(c, "pairs_compact", move_pairs_kernel<ulonglong2>, grid, 256, 0, (ulonglong2 *)pairs.p,
-                  dm.as<Move>(), (uint64_t)moves.size());
-    HJ_CUDA(c, cudaStreamSynchronize(c->stream));  // `moves` is a host temporary
+        HJ_LAUNCH(c, "pairs_compact", compact_move_kernel<ulonglong2>, grid, 256, 0, (ulonglong2 *)pairs.p, pv);
     return HJ_OK;
 }
 
