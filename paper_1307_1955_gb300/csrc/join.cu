@@ -617,6 +617,46 @@ template <int W> struct ChunkSink {
         }
         st.pairs += tot;
     }
+    // one append for all single-match items of a group (at most 32 * IT pairs, so
+    // at most one new chunk): item-major positions, so that each store instruction
+    // writes consecutive slots; capacity tested once per group
+    template <int IT>
+    __device__ __forceinline__ void append_runs(const uint32_t *cnt, const T *first, const T *r) {
+        const unsigned lane = threadIdx.x & 31, lt = (1u << lane) - 1u;
+        unsigned m[IT], tot = 0;
+#pragma unroll
+        for (int i = 0; i < IT; ++i) {
+            m[i] = __ballot_sync(0xffffffffu, cnt[i] == 1);
+            tot += __popc(m[i]);
+        }
+        if (!tot) return;
+        const unsigned room = kChunkPairs - st.used;
+        unsigned long long nb = 0;
+        if (tot > room) {
+            if (lane == 0) nb = atomicAdd(&oc.ctr->cursor, (unsigned long long)kChunkPairs);
+            nb = __shfl_sync(0xffffffffu, nb, 0);
+        }
+        const unsigned long long c0 = st.base + st.used;
+        const bool safe = c0 + (tot < room ? tot : room) <= oc.pcap && (tot <= room || nb + (tot - room) <= oc.pcap);
+        unsigned run = 0;
+#pragma unroll
+        for (int i = 0; i < IT; ++i) {
+            if (cnt[i] == 1) {
+                const unsigned idx = run + __popc(m[i] & lt);
+                const unsigned long long pos = idx < room ? c0 + idx : nb + (idx - room);
+                if (safe || pos < oc.pcap) PairOut<W>::put(oc.pairs, pos, first[i], r[i]);
+            }
+            run += __popc(m[i]);
+        }
+        if (tot > room) {
+            st.base = nb;
+            st.used = tot - room;
+            st.claimed = true;
+        } else {
+            st.used += tot;
+        }
+        st.pairs += tot;
+    }
     __device__ __forceinline__ hj_counters *ctr() const { return oc.ctr; }
     __device__ __forceinline__ void end_task() {}
     __device__ __forceinline__ void finish() {
@@ -696,6 +736,10 @@ template <int W> struct StageSink {
             run += __popc(m[i]);
         }
     }
+    template <int IT>
+    __device__ __forceinline__ void append_runs(const uint32_t *cnt, const T *first, const T *r) {
+        append_group<IT>(cnt, first, r);
+    }
     __device__ __forceinline__ hj_counters *ctr() const { return slots[join].ctr; }
     // all threads: claim the staged pairs' rows and copy them (contains barriers)
     __device__ __forceinline__ void end_task() {
@@ -712,18 +756,47 @@ template <int W> struct StageSink {
 };
 
 // Probe of S_p against the partition's shared-memory table when no checksum is
-// wanted: the lean form of the loop below.  An insert moves past a bucket only
-// while the bucket is full and slots never empty again, so a set overflow bit
-// implies a full bucket: the overflow bit alone says whether a key's run goes on,
-// and no slot is compared with the empty marker.  Whole groups (every lane's U
-// vectors inside S_p) need no per-item validity tests; only the last group does.
+// wanted: the lean form of the loop in partition_join_kernel.
+//   * Inserts fill a bucket's slots in order and slots never empty again, so a
+//     bucket is full exactly when its last slot is; and an insert moves past a
+//     bucket only while it is full.  A key's run therefore goes on past its home
+//     bucket only if the last slot is taken AND the overflow bit is set: one
+//     compare, and the overflow bitmap is read for full buckets only.
+//   * The first matching rid is one indexed shared load.
+//   * A warp's groups that lie wholly inside S_p skip per-item validity tests;
+//     only the last, partial group of a warp tests each item.
+template <int W, bool CHECK>
+__device__ __forceinline__ void probe_item(const SoaTab<W> &tab, typename Tup<W>::U k, bool valid, uint32_t *cnt,
+                                           typename Tup<W>::U *first) {
+    using T = typename Tup<W>::U;
+    constexpr uint32_t G = SoaTab<W>::G;
+    const uint32_t home = part_bucket<W>(k, tab.nb);
+    T key[G];
+    tab.ld(home, 0, key);
+    uint32_t m = 0;
+#pragma unroll
+    for (uint32_t q = 0; q < G; ++q) m |= (uint32_t)(key[q] == k) << q;
+    if (CHECK && !valid) m = 0;
+    T f = 0;
+    if (m) f = tab.ld1(home, 1, (uint32_t)(__ffs(m) - 1));
+    uint32_t c = __popc(m);
+    if ((!CHECK || valid) && key[G - 1] != tab.empty && tab.overflowed(home)) {  // the run goes on (rare)
+        const uint32_t nx = home + 1 == tab.nb ? 0 : home + 1;
+        T f2 = 0;
+        const uint32_t c2 = soa_lookup<W>(tab, k, nx, &f2);
+        if (c == 0) f = f2;
+        c += c2;
+    }
+    *cnt = c;
+    *first = f;
+}
+
 template <int W, int U, class Sink>
 __device__ __forceinline__ void probe_fast(const SoaTab<W> &tab, const typename Tup<W>::Vec *Sv, uint32_t nsv,
                                            Sink &sink, unsigned warp, unsigned nwarps, unsigned lane) {
     using T = typename Tup<W>::U;
     using Vec = typename Tup<W>::Vec;
     constexpr int PV = Tup<W>::kPerVec, IT = U * PV;
-    constexpr uint32_t G = SoaTab<W>::G;
     const uint32_t gstride = nwarps * 32u * U;
     uint32_t g = warp * 32u * U;
     Vec cur[U], nxt[U];
@@ -739,9 +812,7 @@ __device__ __forceinline__ void probe_fast(const SoaTab<W> &tab, const typename 
             const uint32_t rel = gn + u * 32u + lane;
             if (rel < nsv) nxt[u] = ld_stream(Sv + rel);
         }
-        const bool whole = g + 32u * U <= nsv;
         T k[IT], r[IT];
-        uint32_t vmask = 0;  // items inside S_p
 #pragma unroll
         for (int u = 0; u < U; ++u) {
             if constexpr (W == 4) {
@@ -749,40 +820,18 @@ __device__ __forceinline__ void probe_fast(const SoaTab<W> &tab, const typename 
             } else {
                 k[u] = cur[u].x; r[u] = cur[u].y;
             }
-            if (whole || g + u * 32u + lane < nsv) vmask |= ((1u << PV) - 1u) << (u * PV);
         }
-        uint32_t cnt[IT], home[IT];
+        uint32_t cnt[IT];
         T first[IT];
+        if (g + 32u * U <= nsv) {  // warp-uniform: the whole group is inside S_p
 #pragma unroll
-        for (int i = 0; i < IT; ++i) {
-            home[i] = part_bucket<W>(k[i], tab.nb);
-            T key[G];
-            tab.ld(home[i], 0, key);
-            uint32_t m = 0;
+            for (int i = 0; i < IT; ++i) probe_item<W, false>(tab, k[i], true, &cnt[i], &first[i]);
+        } else {
 #pragma unroll
-            for (uint32_t q = 0; q < G; ++q) m |= (uint32_t)(key[q] == k[i]) << q;
-            if (!((vmask >> i) & 1u)) m = 0;
-            T f = 0;
-            if (m) {
-                T rid[G];
-                tab.ld(home[i], 1, rid);
-                f = rid[G - 1];
-#pragma unroll
-                for (int q = (int)G - 2; q >= 0; --q)
-                    if ((m >> q) & 1u) f = rid[q];
-            }
-            uint32_t c = __popc(m);
-            if (((vmask >> i) & 1u) && tab.overflowed(home[i])) {  // the run goes on (rare)
-                const uint32_t nx = home[i] + 1 == tab.nb ? 0 : home[i] + 1;
-                T f2 = 0;
-                const uint32_t c2 = soa_lookup<W>(tab, k[i], nx, &f2);
-                if (c == 0) f = f2;
-                c += c2;
-            }
-            cnt[i] = c;
-            first[i] = f;
+            for (int i = 0; i < IT; ++i)
+                probe_item<W, true>(tab, k[i], g + (uint32_t)(i / PV) * 32u + lane < nsv, &cnt[i], &first[i]);
         }
-        sink.template append_group<IT>(cnt, first, r);
+        sink.template append_runs<IT>(cnt, first, r);
 #pragma unroll
         for (int i = 0; i < IT; ++i) {
             unsigned multi = __ballot_sync(0xffffffffu, cnt[i] > 1);
@@ -791,8 +840,7 @@ __device__ __forceinline__ void probe_fast(const SoaTab<W> &tab, const typename 
                 multi &= multi - 1;
                 const T kk = __shfl_sync(0xffffffffu, k[i], L);
                 const T ss = __shfl_sync(0xffffffffu, r[i], L);
-                const uint32_t hh = __shfl_sync(0xffffffffu, home[i], L);
-                soa_coop_emit<W>(tab, kk, ss, hh, sink);
+                soa_coop_emit<W>(tab, kk, ss, part_bucket<W>(kk, tab.nb), sink);
             }
         }
 #pragma unroll

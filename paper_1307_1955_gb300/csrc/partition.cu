@@ -176,36 +176,41 @@ __global__ void __launch_bounds__(kHistThreads) hist_kernel(const void *in, uint
     // tuples come from `in` (global row index), or from the segment's own array
     const void *src = seg_ptrs ? seg_ptrs[cp.s] : in;
     const uint64_t ioff = seg_ptrs ? seg_off[cp.s] : 0;
-    const uint64_t nsrc = seg_ptrs ? seg_off[cp.s + 1] - seg_off[cp.s] : n_total;
     const uint64_t lo = cp.lo - ioff, hi = cp.hi - ioff;
     __syncthreads();
-    const uint64_t va = lo / PV, vb = (hi + PV - 1) / PV;
-    const uint64_t step = (uint64_t)blockDim.x * kHistUnroll;
-    U k[kHistUnroll][2], r[kHistUnroll][2], nk[kHistUnroll][2], nr[kHistUnroll][2];
-    auto load = [&](uint64_t v0, U (*kk)[2], U (*rr)[2]) {
+    // whole vectors of the chunk: no per-tuple range tests, 32-bit indices
+    const uint64_t va = (lo + PV - 1) / PV, vb = hi / PV;
+    using Vec = typename Tup<W>::Vec;
+    const Vec *vp = (const Vec *)src + va;
+    const uint32_t nv = vb > va ? (uint32_t)(vb - va) : 0u;
+    for (uint32_t v0 = 0; v0 < nv; v0 += blockDim.x * kHistUnroll) {
+        Vec x[kHistUnroll];
 #pragma unroll
         for (int u = 0; u < kHistUnroll; ++u) {
-            uint64_t v = v0 + (uint64_t)u * blockDim.x + threadIdx.x;
-            kk[u][0] = kk[u][1] = 0;
-            if (v < vb) load_vec_p<W>(src, v, nsrc, kk[u], rr[u]);
+            const uint32_t v = v0 + (uint32_t)u * blockDim.x + threadIdx.x;
+            if (v < nv) x[u] = ld_stream(vp + v);
         }
-    };
-    if (va < vb) load(va, k, r);
-    for (uint64_t v0 = va; v0 < vb; v0 += step) {
-        if (v0 + step < vb) load(v0 + step, nk, nr);
 #pragma unroll
         for (int u = 0; u < kHistUnroll; ++u) {
-            uint64_t v = v0 + (uint64_t)u * blockDim.x + threadIdx.x;
-#pragma unroll
-            for (int e = 0; e < PV; ++e) {
-                uint64_t t = v * PV + e;
-                if (v < vb && t >= lo && t < hi) atomicAdd(&hist[digit_of(key_hash<W>(k[u][e]), shift, bits)], 1u);
+            const uint32_t v = v0 + (uint32_t)u * blockDim.x + threadIdx.x;
+            if (v < nv) {
+                if constexpr (W == 4) {
+                    atomicAdd(&hist[digit_of(key_hash<W>(x[u].x), shift, bits)], 1u);
+                    atomicAdd(&hist[digit_of(key_hash<W>(x[u].z), shift, bits)], 1u);
+                } else {
+                    atomicAdd(&hist[digit_of(key_hash<W>(x[u].x), shift, bits)], 1u);
+                }
             }
         }
-#pragma unroll
-        for (int u = 0; u < kHistUnroll; ++u) {
-            k[u][0] = nk[u][0];
-            k[u][1] = nk[u][1];
+    }
+    // rows of a 4-byte relation outside whole vectors: [lo, min(2 va, hi)) and
+    // [2 max(va, vb), hi), at most one row each
+    if constexpr (W == 4) {
+        if (threadIdx.x == 0) {
+            const uint32_t *t32 = (const uint32_t *)src;
+            const uint64_t f1 = PV * va < hi ? PV * va : hi, b0 = PV * (va > vb ? va : vb);
+            for (uint64_t t = lo; t < f1; ++t) atomicAdd(&hist[digit_of(key_hash<W>(t32[2 * t]), shift, bits)], 1u);
+            for (uint64_t t = b0; t < hi; ++t) atomicAdd(&hist[digit_of(key_hash<W>(t32[2 * t]), shift, bits)], 1u);
         }
     }
     __syncthreads();
