@@ -199,6 +199,77 @@ hj_status hj_result_free(hj_ctx *ctx, hj_result *res);
 hj_status hj_join_static(const hj_rel *R, const hj_rel *S, void *cuda_stream, void *pairs, uint64_t pairs_cap,
                          uint64_t *count, uint64_t *checksum);
 
+/* ------------------------------------------------------------------ serving
+ * A request loop over the join (the paper has no serving layer: it joins one R
+ * and one S at a time, Sec. 3.1).  Clients submit joins of any size from any
+ * thread; the server admits them in FIFO order against an HBM budget, groups the
+ * admitted ones into waves (one hj_join_batch launch sequence per wave, or hj_join
+ * for a wave of one) and runs up to `workers` waves at once, each on its own CUDA
+ * stream.  Requests that arrive while waves run are admitted as soon as a worker
+ * and budget are free (continuous batching); their work overlaps the running
+ * waves on the device.  Every result is exactly what hj_join returns for the same
+ * R, S and mode (count, checksums, the pair multiset), whatever it was batched
+ * with.
+ *
+ * Budget: a request reserves an estimate of its join workspace (partitioned R
+ * and S, pair buffer) from admission to completion; afterwards its pairs stay
+ * charged until hj_server_result_free.  A request whose estimate exceeds the whole
+ * budget is refused at submission (HJ_E_NOMEM).  All worker streams allocate from
+ * one memory pool owned by the server. */
+typedef struct hj_server hj_server;
+
+typedef struct hj_server_opts {
+    uint64_t budget_bytes; /* HBM admission budget (0: min(120 GiB, 60% of free memory)) */
+    int32_t workers;       /* waves in flight at once, one stream each (0: 3; at most 16) */
+    int32_t max_wave;      /* most requests in one wave (0: 512)                       */
+    uint64_t wave_tuples;  /* a wave stops growing past this many tuples of R and S;
+                              a request above it runs alone (0: 2^26)                 */
+    uint64_t flags;        /* HJ_FLAG_GRAPH: waves of several joins run as a CUDA graph */
+} hj_server_opts;
+
+/* Host clock (seconds since hj_server_create, steady clock) of a request's steps. */
+typedef struct hj_req_times {
+    double submit; /* hj_server_submit accepted it                          */
+    double admit;  /* its workspace was reserved and it joined a wave       */
+    double start;  /* its wave's work began                                 */
+    double done;   /* its result was complete on the device and read back   */
+} hj_req_times;
+
+typedef struct hj_server_stats {
+    uint64_t submitted, completed, waves, wave_max, queued;
+    uint64_t in_use, peak_in_use, budget; /* bytes charged now / at most / allowed */
+    uint64_t launches;                    /* kernels the workers have launched       */
+} hj_server_stats;
+
+/* Start a server on ctx's device with its own worker threads, streams and memory
+ * pool (ctx is only consulted for the device and error text). */
+hj_status hj_server_create(hj_server **srv, hj_ctx *ctx, const hj_server_opts *opts);
+
+/* Queue the join of R and S (device pointers, same width, 16-byte aligned, fewer
+ * than 2^32 - 1 tuples each) in `mode` (HJ_COUNT, HJ_COUNT_CHECKSUM,
+ * HJ_MATERIALIZE).  R and S must stay valid and unchanged until the request is
+ * collected.  *req_id identifies it for hj_server_poll / hj_server_wait. */
+hj_status hj_server_submit(hj_server *srv, const hj_rel *R, const hj_rel *S, int32_t mode, uint64_t *req_id);
+
+/* HJ_E_PENDING while the request runs.  Once done, returns the request's own
+ * status, moves its result into *out (NULL: the pairs are released at once) and
+ * its times into *t (NULL allowed), and forgets the request. */
+hj_status hj_server_poll(hj_server *srv, uint64_t req_id, hj_result *out, hj_req_times *t);
+
+/* As hj_server_poll, but blocks until the request is done or `timeout_s` seconds
+ * pass (HJ_E_PENDING; a negative timeout waits for ever). */
+hj_status hj_server_wait(hj_server *srv, uint64_t req_id, double timeout_s, hj_result *out, hj_req_times *t);
+
+/* Release the pairs of a result collected from this server (and their budget). */
+hj_status hj_server_result_free(hj_server *srv, hj_result *res);
+
+hj_status hj_server_stats_get(hj_server *srv, hj_server_stats *st);
+const char *hj_server_last_error(const hj_server *srv);
+
+/* Run every queued request to completion, stop the workers and free everything,
+ * including pairs of results not yet released (their pointers become invalid). */
+hj_status hj_server_destroy(hj_server *srv);
+
 /* Wait for all work queued on the context's stream. */
 hj_status hj_sync(hj_ctx *ctx);
 

@@ -1,5 +1,8 @@
 // ctx.cu -- context lifetime, memory pool with HBM budget, errors, profiling.
 #include <cstring>
+#include <mutex>
+#include <set>
+#include <utility>
 
 #include "ctx.cuh"
 
@@ -119,6 +122,20 @@ hj_status zero_counters(hj_ctx *c) {
     return HJ_OK;
 }
 
+hj_status allow_max_smem(hj_ctx *c, const void *func) {
+    static std::mutex mu;
+    static std::set<std::pair<int, const void *>> done;  // (device, function) pairs already set
+    std::lock_guard<std::mutex> lk(mu);
+    if (done.count({c->device, func})) return HJ_OK;
+    int optin = 0;
+    HJ_CUDA(c, cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, c->device));
+    cudaFuncAttributes fa;
+    HJ_CUDA(c, cudaFuncGetAttributes(&fa, func));
+    HJ_CUDA(c, cudaFuncSetAttribute(func, cudaFuncAttributeMaxDynamicSharedMemorySize, optin - (int)fa.sharedSizeBytes));
+    done.insert({c->device, func});
+    return HJ_OK;
+}
+
 int num_sms(hj_ctx *c) {
     int n = 0;
     cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, c->device);
@@ -132,6 +149,14 @@ using namespace hj;
 extern "C" {
 
 hj_status hj_create(hj_ctx **out, int device, void *cuda_stream, uint64_t budget) {
+    return hj::ctx_create(out, device, cuda_stream, budget, nullptr);
+}
+
+}  // extern "C"
+
+namespace hj {
+
+hj_status ctx_create(hj_ctx **out, int device, void *cuda_stream, uint64_t budget, cudaMemPool_t shared_pool) {
     if (!out) return HJ_E_INVALID;
     *out = nullptr;
     int ndev = 0;
@@ -151,7 +176,10 @@ hj_status hj_create(hj_ctx **out, int device, void *cuda_stream, uint64_t budget
             c->own_stream = true;
         }
     }
-    if (e == cudaSuccess) {
+    if (e == cudaSuccess && shared_pool) {
+        c->pool = shared_pool;
+        c->own_pool = false;
+    } else if (e == cudaSuccess) {
         cudaMemPoolProps props;
         memset(&props, 0, sizeof props);
         props.allocType = cudaMemAllocationTypePinned;
@@ -159,7 +187,7 @@ hj_status hj_create(hj_ctx **out, int device, void *cuda_stream, uint64_t budget
         props.location.id = device;
         e = cudaMemPoolCreate(&c->pool, &props);
     }
-    if (e == cudaSuccess) {
+    if (e == cudaSuccess && c->own_pool) {
         uint64_t keep = ~0ull;  // keep freed blocks for reuse by later joins
         e = cudaMemPoolSetAttribute(c->pool, cudaMemPoolAttrReleaseThreshold, &keep);
     }
@@ -168,7 +196,7 @@ hj_status hj_create(hj_ctx **out, int device, void *cuda_stream, uint64_t budget
     if (e != cudaSuccess) {
         cudaGetLastError();
         if (c->d_ctr) cudaFree(c->d_ctr);
-        if (c->pool) cudaMemPoolDestroy(c->pool);
+        if (c->pool && c->own_pool) cudaMemPoolDestroy(c->pool);
         if (c->own_stream && c->stream) cudaStreamDestroy(c->stream);
         delete c;
         return HJ_E_CUDA;
@@ -176,6 +204,10 @@ hj_status hj_create(hj_ctx **out, int device, void *cuda_stream, uint64_t budget
     *out = c;
     return HJ_OK;
 }
+
+}  // namespace hj
+
+extern "C" {
 
 hj_status hj_destroy(hj_ctx *c) {
     if (!c) return HJ_E_INVALID;
@@ -191,7 +223,7 @@ hj_status hj_destroy(hj_ctx *c) {
     for (auto e : c->spare_events) cudaEventDestroy(e);
     if (c->d_ctr) cudaFree(c->d_ctr);
     if (c->h_ctr) cudaFreeHost(c->h_ctr);
-    if (c->pool) cudaMemPoolDestroy(c->pool);
+    if (c->pool && c->own_pool) cudaMemPoolDestroy(c->pool);
     if (c->own_stream) cudaStreamDestroy(c->stream);
     delete c;
     return HJ_OK;

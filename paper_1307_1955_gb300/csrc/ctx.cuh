@@ -35,6 +35,7 @@ struct hj_ctx {
     uint64_t peak = 0;
     std::unordered_map<void *, uint64_t> allocs;
     cudaMemPool_t pool = nullptr;
+    bool own_pool = true;  // false: the pool belongs to a server that shares it among its workers
     std::string err;
     hj_counters *d_ctr = nullptr;      // device counters
     hj_counters *h_ctr = nullptr;      // pinned host mirror
@@ -77,6 +78,14 @@ hj_status read_counters(hj_ctx *c);
 hj_status zero_counters(hj_ctx *c);
 
 int num_sms(hj_ctx *c);
+
+// Let `func` take up to the device's opt-in maximum of dynamic shared memory.
+// Always the same value per function, so concurrent callers on several threads
+// (the server's workers) cannot undo each other's setting between set and launch.
+hj_status allow_max_smem(hj_ctx *c, const void *func);
+
+// hj_create with an existing memory pool (not owned: hj_destroy leaves it alone).
+hj_status ctx_create(hj_ctx **out, int device, void *cuda_stream, uint64_t budget, cudaMemPool_t shared_pool);
 
 // A device buffer from the context's pool, released when the guard goes out of
 // scope unless ownership is taken with release().

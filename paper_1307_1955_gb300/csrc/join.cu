@@ -1184,7 +1184,7 @@ hj_status partition_join(hj_ctx *c, int width, int agg, const PartTask *tasks, u
 #define HJ_PJ(WW, AA, NT, SK, FF)                                                                               \
     do {                                                                                                        \
         auto kern = partition_join_kernel<WW, AA, NT, SK<WW>, FF>;                                              \
-        HJ_CUDA(c, cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));         \
+        HJ_TRY(allow_max_smem(c, (const void *)kern));                                                         \
         HJ_LAUNCH(c, "partition_join", kern, grid, NT, smem, tasks, ntasks, slots, c->d_ctr, (uint32_t)cap_max, \
                   ra, oversize, checksum, stage, scap);                                                         \
     } while (0)

@@ -819,18 +819,18 @@ hj_status partition_pass(hj_ctx *c, int width, const void *in, uint64_t n_total,
     do {                                                                                                      \
         auto kern = scatter_kernel<WW, NT, VPT>;                                                              \
         const size_t ssmem = scatter_smem_bytes<WW, NT, VPT>((uint32_t)P);                                    \
-        HJ_CUDA(c, cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)ssmem));      \
+        HJ_TRY(allow_max_smem(c, (const void *)kern));                                                       \
         HJ_LAUNCH(c, "partition_scatter", kern, (unsigned)max_chunks, NT, ssmem, in, n_total, seg_off, nseg, cb, \
                   chunk, shift, bits, Hs, out, pad, k0, k1);                                                  \
     } while (0)
     const size_t tma_smem = width == 4 ? scatter_tma_smem_bytes<4>((uint32_t)P) : scatter_tma_smem_bytes<8>((uint32_t)P);
     if (cfg.tma) {
         if (width == 4) {
-            HJ_CUDA(c, cudaFuncSetAttribute(scatter_tma_kernel<4>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)tma_smem));
+            HJ_TRY(allow_max_smem(c, (const void *)scatter_tma_kernel<4>));
             HJ_LAUNCH(c, "partition_scatter", scatter_tma_kernel<4>, (unsigned)max_chunks, kTmaThreads, tma_smem, in,
                       n_total, seg_off, nseg, cb, chunk, shift, bits, Hs, out, pad, k0, k1, c->d_ctr, seg_ptrs);
         } else {
-            HJ_CUDA(c, cudaFuncSetAttribute(scatter_tma_kernel<8>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)tma_smem));
+            HJ_TRY(allow_max_smem(c, (const void *)scatter_tma_kernel<8>));
             HJ_LAUNCH(c, "partition_scatter", scatter_tma_kernel<8>, (unsigned)max_chunks, kTmaThreads, tma_smem, in,
                       n_total, seg_off, nseg, cb, chunk, shift, bits, Hs, out, pad, k0, k1, c->d_ctr, seg_ptrs);
         }

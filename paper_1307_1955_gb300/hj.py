@@ -49,6 +49,21 @@ class hj_result(ctypes.Structure):
                 ("radix_bits", ctypes.c_int32), ("passes", ctypes.c_int32)]
 
 
+class hj_server_opts(ctypes.Structure):
+    _fields_ = [("budget_bytes", ctypes.c_uint64), ("workers", ctypes.c_int32), ("max_wave", ctypes.c_int32),
+                ("wave_tuples", ctypes.c_uint64), ("flags", ctypes.c_uint64)]
+
+
+class hj_req_times(ctypes.Structure):
+    _fields_ = [("submit", ctypes.c_double), ("admit", ctypes.c_double), ("start", ctypes.c_double),
+                ("done", ctypes.c_double)]
+
+
+class hj_server_stats(ctypes.Structure):
+    _fields_ = [(n, ctypes.c_uint64) for n in ("submitted", "completed", "waves", "wave_max", "queued", "in_use",
+                                                "peak_in_use", "budget", "launches")]
+
+
 class hj_prof_entry(ctypes.Structure):
     _fields_ = [("name", ctypes.c_char * 48), ("launches", ctypes.c_uint64), ("ms", ctypes.c_double)]
 
@@ -87,6 +102,14 @@ def load_library(path: str = LIB_PATH):
         "hj_launch_count": (U64, [V]),
         "hj_debug_fail_alloc": (I32, [V, ctypes.c_int64]),
         "hj_debug_bytes_in_use": (U64, [V]),
+        "hj_server_create": (I32, [P(V), V, P(hj_server_opts)]),
+        "hj_server_submit": (I32, [V, P(hj_rel), P(hj_rel), I32, P(U64)]),
+        "hj_server_poll": (I32, [V, U64, P(hj_result), P(hj_req_times)]),
+        "hj_server_wait": (I32, [V, U64, ctypes.c_double, P(hj_result), P(hj_req_times)]),
+        "hj_server_result_free": (I32, [V, P(hj_result)]),
+        "hj_server_stats_get": (I32, [V, P(hj_server_stats)]),
+        "hj_server_last_error": (ctypes.c_char_p, [V]),
+        "hj_server_destroy": (I32, [V]),
     }
     for name, (res, args) in sig.items():
         f = getattr(lib, name)
@@ -124,6 +147,7 @@ class Result:
     passes: int
     _raw: hj_result
     _ctx: "Context"
+    _server: "Server | None" = None
 
     def pairs_numpy(self):
         """Copy the pairs to host: (count, 2) uint32/uint64 array of (rid_R, rid_S)."""
@@ -137,7 +161,9 @@ class Result:
         return out
 
     def free(self):
-        if self._raw is not None and self._ctx.handle:
+        if self._raw is not None and self._server is not None:
+            self._server._free(self._raw)
+        elif self._raw is not None and self._ctx.handle:
             _check(self._ctx, load_library().hj_result_free(self._ctx.handle, ctypes.byref(self._raw)))
         self._raw = None
         self.pairs_ptr = 0
@@ -353,3 +379,110 @@ def prof_read(ctx: Context) -> dict:
 
 def launch_count(ctx: Context) -> int:
     return int(load_library().hj_launch_count(ctx.handle))
+
+
+# ------------------------------------------------------------------- serving
+
+
+@dataclass
+class Times:
+    submit: float
+    admit: float
+    start: float
+    done: float
+
+
+class Server:
+    """An hj_server: submit joins from any thread, collect them with poll / wait.
+    The relations of a request are kept referenced until it is collected."""
+
+    def __init__(self, ctx: Context, budget: int = 0, workers: int = 0, max_wave: int = 0, wave_tuples: int = 0,
+                 graph: bool = False):
+        lib = load_library()
+        h = ctypes.c_void_p()
+        o = hj_server_opts(budget, workers, max_wave, wave_tuples, HJ_FLAG_GRAPH if graph else 0)
+        _check(ctx, lib.hj_server_create(ctypes.byref(h), ctx.handle, ctypes.byref(o)))
+        self.handle, self.ctx = h, ctx
+        self._keep = {}
+
+    def _check(self, st):
+        if st != HJ_OK:
+            msg = load_library().hj_server_last_error(self.handle)
+            raise HJError(st, msg.decode() if msg else "")
+
+    def submit(self, R: torch.Tensor, S: torch.Tensor, mode: int = HJ_MATERIALIZE) -> int:
+        r, s = rel_of(R), rel_of(S)
+        rid = ctypes.c_uint64()
+        self._check(load_library().hj_server_submit(self.handle, ctypes.byref(r), ctypes.byref(s), mode,
+                                                    ctypes.byref(rid)))
+        self._keep[rid.value] = (R, S)
+        return int(rid.value)
+
+    def _collect(self, st, rid, res, t):
+        if st == HJ_E_PENDING:
+            return None
+        self._keep.pop(rid, None)
+        self._check(st)
+        out = _result(self.ctx, res)
+        out._server = self
+        return out, Times(t.submit, t.admit, t.start, t.done)
+
+    def poll(self, rid: int):
+        """None while the request runs, else (Result, Times)."""
+        res, t = hj_result(), hj_req_times()
+        st = load_library().hj_server_poll(self.handle, rid, ctypes.byref(res), ctypes.byref(t))
+        return self._collect(st, rid, res, t)
+
+    def wait(self, rid: int, timeout: float = -1.0):
+        """Block until the request is done (None on timeout); returns (Result, Times)."""
+        res, t = hj_result(), hj_req_times()
+        st = load_library().hj_server_wait(self.handle, rid, timeout, ctypes.byref(res), ctypes.byref(t))
+        return self._collect(st, rid, res, t)
+
+    def _free(self, raw: hj_result):
+        self._check(load_library().hj_server_result_free(self.handle, ctypes.byref(raw)))
+
+    def stats(self) -> dict:
+        st = hj_server_stats()
+        self._check(load_library().hj_server_stats_get(self.handle, ctypes.byref(st)))
+        return {n: int(getattr(st, n)) for n, _ in hj_server_stats._fields_}
+
+    def close(self):
+        if self.handle:
+            load_library().hj_server_destroy(self.handle)
+            self.handle = None
+            self._keep.clear()
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()
+
+
+def hj_server_create(ctx: Context, **kw) -> Server:
+    return Server(ctx, **kw)
+
+
+def hj_server_submit(srv: Server, R: torch.Tensor, S: torch.Tensor, mode: int = HJ_MATERIALIZE) -> int:
+    return srv.submit(R, S, mode)
+
+
+def hj_server_poll(srv: Server, rid: int):
+    return srv.poll(rid)
+
+
+def hj_server_wait(srv: Server, rid: int, timeout: float = -1.0):
+    return srv.wait(rid, timeout)
+
+
+def hj_server_result_free(srv: Server, res: Result):
+    res.free()
+
+
+def hj_server_stats_get(srv: Server) -> dict:
+    return srv.stats()
+
+
+def hj_server_destroy(srv: Server):
+    srv.close()

@@ -45,11 +45,21 @@ def test_null_context_is_rejected_without_a_gpu(lib):
     assert lib.hj_last_error(None) == b"null context"
 
 
+def test_server_calls_reject_null_handles_without_a_gpu(lib):
+    for name, args in (("hj_server_create", (None, None, None)), ("hj_server_submit", (None, None, None, 0, None)),
+                       ("hj_server_poll", (None, 1, None, None)), ("hj_server_destroy", (None,)),
+                       ("hj_server_result_free", (None, None))):
+        f = getattr(lib, name)
+        f.restype = ctypes.c_int32
+        assert f(*args) == 1, name  # HJ_E_INVALID
+
+
 def test_binding_names_match_the_abi():
     from paper_1307_1955_gb300 import hj
 
     for name in ("hj_create", "hj_destroy", "hj_build", "hj_probe", "hj_table_free", "hj_partition", "hj_join",
-                 "hj_result_free", "hj_sync"):
+                 "hj_result_free", "hj_sync", "hj_join_batch", "hj_server_create", "hj_server_submit",
+                 "hj_server_poll", "hj_server_wait", "hj_server_result_free", "hj_server_destroy"):
         assert callable(getattr(hj, name))
 
 
