@@ -64,6 +64,8 @@ def parse():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="hj", choices=["hj", "reference"])
     ap.add_argument("--workload", default="phj_16m_256m", choices=sorted(WORKLOADS))
+    ap.add_argument("--algo", type=int, default=-1, help="0 auto, 1 SHJ, 2 PHJ (default: tuned)")
+    ap.add_argument("--no-tune", action="store_true")
     ap.add_argument("--radix-bits", type=int, default=0)
     ap.add_argument("--passes", type=int, default=0)
     ap.add_argument("--e2e-steps", type=int, default=3)
@@ -321,7 +323,13 @@ def run_hj(args, wl, ws, rank, local):
     R, S = make_inputs(wl, rank, dev)
     stream = torch.cuda.current_stream(dev)
     ctx = hj.Context(local, stream=stream)
-    kw = dict(algo=wl["algo"], radix_bits=args.radix_bits, passes=args.passes)
+    kw = dict(algo=wl["algo"] if args.algo < 0 else args.algo, radix_bits=args.radix_bits, passes=args.passes)
+    tuned = None
+    if args.algo < 0 and args.radix_bits == 0 and args.passes == 0 and not args.no_tune:
+        # the autotuner times the cost model's cheapest plans on these relations
+        # (untimed); the timed joins then run its pick through HJ_ALGO_AUTO
+        tuned = hj.hj_tune(ctx, R, S)
+        kw = dict(algo=hj.HJ_ALGO_AUTO)
 
     def step():
         res = hj.hj_join(ctx, R, S, **kw)
@@ -420,7 +428,8 @@ def run_hj(args, wl, ws, rank, local):
             "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "u32", "data": "synthetic",
             "config": {"workload": wl["desc"], "algo": {1: "SHJ", 2: "PHJ"}[algo], "radix_bits": bits,
-                       "passes": passes, "pairs_per_step": count, "parallelism": f"replicas x{ws}",
+                       "passes": passes, "plan": "hj_tune" if tuned else "forced",
+                       "tuned": tuned, "pairs_per_step": count, "parallelism": f"replicas x{ws}",
                        "l2": "inputs 2.28 GB per step exceed the 129 MB L2; no flush"
                        if wl["ns"] >= (1 << 24) else "inputs smaller than L2; warm L2 across steps"},
             "roofline": roofline, "join_roofline": join_roof, "kernels": kernels,

@@ -159,6 +159,39 @@ hj_status hj_join(hj_ctx *ctx, const hj_rel *R, const hj_rel *S, const hj_opts *
 hj_status hj_join_batch(hj_ctx *ctx, int n, const hj_rel *Rs, const hj_rel *Ss, const hj_opts *opts,
                         hj_result *outs);
 
+/* ------------------------------------------------------------ plan choice
+ * hj_join with HJ_ALGO_AUTO (and radix_bits, passes left 0) picks SHJ or PHJ, the
+ * radix bits and the pass count from a cost model of the GPU-only join: the
+ * paper's T = sum over steps of computation + memory time (Sec. 4, Eq. 1-2, with
+ * every step on the GPU so that the pipeline delay is zero), where a step's memory
+ * time is the bytes it must move over the HBM bandwidth and its computation time
+ * its per-item instruction count over the SMs' issue rate; a step costs the larger
+ * of the two.  hj_tune refines the choice on the device. */
+typedef struct hj_plan_info {
+    int32_t algo;        /* HJ_ALGO_SHJ or HJ_ALGO_PHJ                               */
+    int32_t radix_bits;  /* PHJ: total radix bits                                    */
+    int32_t passes;      /* PHJ: partition passes                                    */
+    int32_t reserved;
+    double predicted_ms; /* the model's time for the whole join                      */
+    double step_ms[4];   /* PHJ: histogram, scatter, join, 0; SHJ: 0, 0, build, probe */
+    double measured_ms;  /* hj_tune: best measured time (-1 from hj_plan)            */
+} hj_plan_info;
+
+/* The plan hj_join would run for R and S under `opts` (forced fields honoured).
+ * With ctx NULL the model uses GB300's figures and no tuned plan; no GPU work is
+ * done either way.  R and S are only read for their sizes and width. */
+hj_status hj_plan(hj_ctx *ctx, const hj_rel *R, const hj_rel *S, const hj_opts *opts, hj_plan_info *out);
+
+/* Time the model's `top_k` cheapest plans (0: 4) on R and S (each run once to warm
+ * up and twice timed, in opts->mode) and remember the fastest for their size class
+ * (width, count or pair mode, floor(log2) of |R| + 1 and of |S| + 1) on this
+ * context: later hj_join calls with HJ_ALGO_AUTO in that class run it.  `out`
+ * (NULL allowed) receives the chosen plan with its predicted and measured time. */
+hj_status hj_tune(hj_ctx *ctx, const hj_rel *R, const hj_rel *S, const hj_opts *opts, int top_k, hj_plan_info *out);
+
+/* Forget every tuned plan of the context. */
+hj_status hj_tune_clear(hj_ctx *ctx);
+
 /* End-to-end join on HOST buffers: copies R and S from host memory (page-locked
  * memory gives full link speed; pageable works) to device buffers the library
  * allocates, runs hj_join, and copies the pairs into `pairs_host` (room for

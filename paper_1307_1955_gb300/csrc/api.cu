@@ -86,30 +86,6 @@ uint64_t slot_bytes(int width, bool agg) {
     return width == 4 ? sizeof(AggSlot<4>) : sizeof(AggSlot<8>);
 }
 
-// Plan choice (the cost model's GPU-only case, Sec. 4 Eq. 1-2 with every step on
-// the GPU): SHJ while its table is small enough to stay in L2; otherwise PHJ with
-// enough radix bits that a partition of R holds about 8192 tuples (a shared-memory
-// table), in one pass up to 12 bits and two passes beyond.
-void plan(const hj_rel *R, const hj_opts &o, int *algo, int *bits, int *passes) {
-    uint64_t nR = R->n;
-    int a = o.algo;
-    if (a == HJ_ALGO_AUTO) {
-        uint64_t cap = 64;
-        while (cap < 2 * nR + 1) cap <<= 1;
-        a = cap * slot_bytes(R->width, is_agg(o.mode)) <= (32ull << 20) ? HJ_ALGO_SHJ : HJ_ALGO_PHJ;
-    }
-    *algo = a;
-    int b = o.radix_bits;
-    if (b <= 0) {
-        b = 1;
-        while (b < 24 && (nR >> b) > 8192) b++;
-    }
-    *bits = b;
-    int p = o.passes;
-    if (p <= 0) p = b <= 12 ? 1 : 2;
-    *passes = p;
-}
-
 __global__ void set_pair_kernel(uint64_t *p, uint64_t a, uint64_t b) {
     p[0] = a;
     p[1] = b;
@@ -377,7 +353,7 @@ hj_status hj_join(hj_ctx *c, const hj_rel *R, const hj_rel *S, const hj_opts *op
     if (o.radix_bits < 0 || o.radix_bits > 24) return set_err(c, HJ_E_INVALID, "radix bits %d > 24", o.radix_bits);
     *res = hj_result{};
     int algo, bits, passes;
-    plan(R, o, &algo, &bits, &passes);
+    choose_plan(c, R->width, o.mode, R->n, S->n, o.algo, o.radix_bits, o.passes, &algo, &bits, &passes);
     hj_status st = algo == HJ_ALGO_SHJ ? join_shj(c, R, S, o, res) : join_phj(c, R, S, o, bits, passes, res);
     return st;
 }

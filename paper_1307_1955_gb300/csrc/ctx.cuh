@@ -26,6 +26,19 @@ struct hj_counters {
     unsigned long long pad;
 };
 
+namespace hj {
+// Device figures the plan cost model works from (defaults: GB300).
+struct CostModel {
+    int sms = 152;
+    double sm_hz = 2.07e9;
+    double hbm_bps = 8.18e12;   // nominal: 2 x memory clock x bus width
+    double l2_bytes = 126e6;
+};
+struct TunedPlan {
+    int algo, bits, passes;
+};
+}  // namespace hj
+
 struct hj_ctx {
     int device = 0;
     cudaStream_t stream = nullptr;
@@ -49,6 +62,10 @@ struct hj_ctx {
     std::vector<cudaEvent_t> spare_events;
     std::map<std::string, std::pair<uint64_t, double>> prof_acc;
     uint64_t launches = 0;
+    // plan choice: cost model of the device, and plans measured by hj_tune per size class
+    hj::CostModel model;
+    bool model_ready = false;
+    std::map<uint64_t, hj::TunedPlan> tuned;
     // test hooks (host-side fault injection)
     int64_t fail_alloc_after = -1;  // fail the N-th allocation from now (0 = next)
 };

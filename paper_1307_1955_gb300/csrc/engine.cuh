@@ -109,6 +109,25 @@ struct PairSink {
     hj_status finalize_device(hj_counters *ctr);
 };
 
+// ----------------------------------------------------------------- tune.cu
+// Plan choice: the cost model (Sec. 4, Eq. 1-2 with every step on the GPU) and the
+// plans hj_tune measured.  A candidate is (algo, total radix bits, passes) with
+// its predicted seconds.
+struct PlanCand {
+    int algo, bits, passes;
+    double sec;
+};
+CostModel cost_model_for(int device);
+double predict_seconds(const CostModel &m, int width, bool agg, bool mat, uint64_t nR, uint64_t nS, int algo,
+                       int bits, int passes, double *steps);
+// Candidates allowed by the forced fields (0 = free), cheapest first.
+std::vector<PlanCand> plan_candidates(const CostModel &m, int width, bool agg, bool mat, uint64_t nR, uint64_t nS,
+                                      int algo, int bits, int passes);
+uint64_t plan_key(int width, bool agg, uint64_t nR, uint64_t nS);
+// The plan hj_join runs: a tuned plan for the size class if any, else the model's.
+void choose_plan(hj_ctx *c, int width, int mode, uint64_t nR, uint64_t nS, int algo, int bits, int passes,
+                 int *a_out, int *b_out, int *g_out);
+
 // Tuple bytes of a relation of `width`-byte fields.
 inline uint64_t tuple_bytes(int width) { return 2ull * (uint64_t)width; }
 

@@ -64,6 +64,12 @@ class hj_server_stats(ctypes.Structure):
                                                 "peak_in_use", "budget", "launches")]
 
 
+class hj_plan_info(ctypes.Structure):
+    _fields_ = [("algo", ctypes.c_int32), ("radix_bits", ctypes.c_int32), ("passes", ctypes.c_int32),
+                ("reserved", ctypes.c_int32), ("predicted_ms", ctypes.c_double), ("step_ms", ctypes.c_double * 4),
+                ("measured_ms", ctypes.c_double)]
+
+
 class hj_prof_entry(ctypes.Structure):
     _fields_ = [("name", ctypes.c_char * 48), ("launches", ctypes.c_uint64), ("ms", ctypes.c_double)]
 
@@ -102,6 +108,9 @@ def load_library(path: str = LIB_PATH):
         "hj_launch_count": (U64, [V]),
         "hj_debug_fail_alloc": (I32, [V, ctypes.c_int64]),
         "hj_debug_bytes_in_use": (U64, [V]),
+        "hj_plan": (I32, [V, P(hj_rel), P(hj_rel), P(hj_opts), P(hj_plan_info)]),
+        "hj_tune": (I32, [V, P(hj_rel), P(hj_rel), P(hj_opts), ctypes.c_int, P(hj_plan_info)]),
+        "hj_tune_clear": (I32, [V]),
         "hj_server_create": (I32, [P(V), V, P(hj_server_opts)]),
         "hj_server_submit": (I32, [V, P(hj_rel), P(hj_rel), I32, P(U64)]),
         "hj_server_poll": (I32, [V, U64, P(hj_result), P(hj_req_times)]),
@@ -257,6 +266,48 @@ def hj_join(ctx: Context, R: torch.Tensor, S: torch.Tensor, algo: int = HJ_ALGO_
     _check(ctx, load_library().hj_join(ctx.handle, ctypes.byref(r), ctypes.byref(s), ctypes.byref(o),
                                        ctypes.byref(res)))
     return _result(ctx, res)
+
+
+def _plan_dict(p: hj_plan_info) -> dict:
+    return {"algo": int(p.algo), "radix_bits": int(p.radix_bits), "passes": int(p.passes),
+            "predicted_ms": float(p.predicted_ms), "step_ms": [float(x) for x in p.step_ms],
+            "measured_ms": float(p.measured_ms)}
+
+
+def _size_rel(n: int, width: int) -> hj_rel:
+    return hj_rel(None, n, width, 0)
+
+
+def hj_plan(ctx: "Context | None", R, S, algo: int = HJ_ALGO_AUTO, mode: int = HJ_MATERIALIZE, radix_bits: int = 0,
+            passes: int = 0) -> dict:
+    """The plan hj_join would run.  R and S may be tensors or (n, width) size pairs
+    (only sizes are read); with ctx None the model uses GB300's figures (no GPU)."""
+    r = rel_of(R) if isinstance(R, torch.Tensor) else _size_rel(*R)
+    s = rel_of(S) if isinstance(S, torch.Tensor) else _size_rel(*S)
+    o = _opts(algo, mode, radix_bits, passes)
+    out = hj_plan_info()
+    st = load_library().hj_plan(ctx.handle if ctx is not None else None, ctypes.byref(r), ctypes.byref(s),
+                                ctypes.byref(o), ctypes.byref(out))
+    if st != HJ_OK:
+        if ctx is not None:
+            _check(ctx, st)
+        raise HJError(st, "hj_plan failed")
+    return _plan_dict(out)
+
+
+def hj_tune(ctx: Context, R: torch.Tensor, S: torch.Tensor, mode: int = HJ_MATERIALIZE, top_k: int = 0) -> dict:
+    """Time the model's cheapest plans on R and S; the fastest is cached for their
+    size class and used by later hj_join calls with algo=HJ_ALGO_AUTO."""
+    r, s = rel_of(R), rel_of(S)
+    o = _opts(mode=mode)
+    out = hj_plan_info()
+    _check(ctx, load_library().hj_tune(ctx.handle, ctypes.byref(r), ctypes.byref(s), ctypes.byref(o), top_k,
+                                       ctypes.byref(out)))
+    return _plan_dict(out)
+
+
+def hj_tune_clear(ctx: Context):
+    _check(ctx, load_library().hj_tune_clear(ctx.handle))
 
 
 def hj_join_host(ctx: Context, R: torch.Tensor, S: torch.Tensor, pairs_out: torch.Tensor | None = None,

@@ -1,0 +1,69 @@
+"""The plan cost model (Sec. 4, Eq. 1-2 with every step on the GPU) as host logic:
+no GPU is involved (hj_plan with a NULL context uses GB300's figures)."""
+import pytest
+
+from paper_1307_1955_gb300 import build as B
+
+
+@pytest.fixture(scope="module")
+def hjm():
+    B.build()
+    from paper_1307_1955_gb300 import hj
+
+    hj.load_library()
+    return hj
+
+
+def plan(hjm, nr, ns, width=4, **kw):
+    return hjm.hj_plan(None, (nr, width), (ns, width), **kw)
+
+
+def test_small_joins_use_the_simple_hash_join(hjm):
+    # a table that stays in L2 and few launches: SHJ
+    for nr, ns in ((1 << 10, 1 << 12), (1 << 16, 1 << 18), (1 << 20, 1 << 20)):
+        assert plan(hjm, nr, ns)["algo"] == hjm.HJ_ALGO_SHJ
+
+
+def test_large_joins_partition_with_enough_bits_for_shared_memory(hjm):
+    p = plan(hjm, 1 << 24, 1 << 28)
+    assert p["algo"] == hjm.HJ_ALGO_PHJ
+    assert p["passes"] == 1 and p["radix_bits"] == 11  # 8192 tuples of 8 B per partition table
+    # a partitioned plan always leaves partitions whose table fits shared memory:
+    # twice the build side, or 8-byte tuples, need at least one more bit
+    for nr, w in ((1 << 25, 4), (1 << 24, 8), (1 << 26, 4)):
+        p = plan(hjm, nr, 1 << 28, width=w, algo=hjm.HJ_ALGO_PHJ)
+        assert p["radix_bits"] >= 12, (nr, w, p)
+        assert nr >> p["radix_bits"] <= (200 * 1024 - 4096) // (4 * w), (nr, w, p)
+
+
+def test_fan_out_beyond_one_pass_takes_two_passes(hjm):
+    p = plan(hjm, 1 << 28, 1 << 29, algo=hjm.HJ_ALGO_PHJ)
+    assert p["algo"] == hjm.HJ_ALGO_PHJ and p["passes"] == 2 and p["radix_bits"] > 12
+
+
+def test_predictions_grow_with_the_input_and_split_by_step(hjm):
+    prev = 0.0
+    for lg in range(16, 29, 2):
+        p = plan(hjm, 1 << (lg - 4), 1 << lg)
+        assert p["predicted_ms"] > prev
+        assert abs(sum(p["step_ms"]) - p["predicted_ms"]) < 1e-9 * max(1.0, p["predicted_ms"])
+        prev = p["predicted_ms"]
+    # the 2^24 x 2^28 join cannot beat its bytes over the HBM bandwidth: 7.92 GB
+    p = plan(hjm, 1 << 24, 1 << 28)
+    assert p["predicted_ms"] > 7.92e9 / 8.18e12 * 1e3
+
+
+def test_forced_fields_are_honoured(hjm):
+    p = plan(hjm, 1 << 24, 1 << 28, algo=hjm.HJ_ALGO_PHJ, radix_bits=14, passes=2)
+    assert (p["algo"], p["radix_bits"], p["passes"]) == (hjm.HJ_ALGO_PHJ, 14, 2)
+    assert plan(hjm, 1 << 24, 1 << 28, algo=hjm.HJ_ALGO_SHJ)["algo"] == hjm.HJ_ALGO_SHJ
+    # two passes cost more than one at the same fan-out (twice the partition traffic)
+    one = plan(hjm, 1 << 24, 1 << 28, algo=hjm.HJ_ALGO_PHJ, radix_bits=12, passes=1)
+    two = plan(hjm, 1 << 24, 1 << 28, algo=hjm.HJ_ALGO_PHJ, radix_bits=12, passes=2)
+    assert two["predicted_ms"] > one["predicted_ms"]
+
+
+def test_count_modes_drop_the_output_bytes(hjm):
+    mat = plan(hjm, 1 << 24, 1 << 28, algo=hjm.HJ_ALGO_PHJ, radix_bits=11, passes=1)
+    cnt = plan(hjm, 1 << 24, 1 << 28, algo=hjm.HJ_ALGO_PHJ, radix_bits=11, passes=1, mode=hjm.HJ_COUNT)
+    assert cnt["predicted_ms"] <= mat["predicted_ms"]
