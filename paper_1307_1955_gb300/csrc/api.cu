@@ -81,11 +81,6 @@ bool wants_checksum(const hj_opts &o) {
     return o.mode == HJ_COUNT_CHECKSUM || (o.mode == HJ_MATERIALIZE && (o.flags & HJ_FLAG_CHECKSUM));
 }
 
-uint64_t slot_bytes(int width, bool agg) {
-    if (!agg) return 2ull * width;
-    return width == 4 ? sizeof(AggSlot<4>) : sizeof(AggSlot<8>);
-}
-
 __global__ void set_pair_kernel(uint64_t *p, uint64_t a, uint64_t b) {
     p[0] = a;
     p[1] = b;

@@ -731,6 +731,193 @@ __global__ void __launch_bounds__(kTmaThreads, 1) scatter_tma_kernel(
     }
 }
 
+
+// --------------------------------------------------------- region scatter
+// Scatter of a padded pass (every (chunk, digit) run starts on a sector) without a
+// per-tile sort.  Shared memory holds, per digit, K slots laid out position-major
+// (slot j of digit d at region[j * P + d], so that consecutive digits are
+// consecutive words); P = 2^LOG2P is a compile-time constant so that every index
+// is a shift and an or.  Tuples come straight from global memory into registers,
+// the next tile's 16-byte vectors loaded while the current tile is processed.  Per
+// tile:
+//   1. insert: every tuple takes the next slot of its digit with one shared
+//      atomicAdd; a tuple that finds its digit's K slots taken (rare for uniform
+//      keys) is written at once to the far end of the digit's run instead, at a
+//      row taken by a shared atomicSub on the run's tail cursor;
+//   2. flush: one thread per digit writes every whole sector its slots hold with
+//      one 32-byte store at the run's head cursor and moves the remaining (fewer
+//      than a sector's) tuples to the front of its slots.
+// After the last tile the gap between a run's head and tail -- its carried
+// tuples plus the padding the histogram added -- is filled tuple by tuple
+// (padding tuples hash to another digit; the join drops them).
+constexpr int kRegionThreads = 1024;
+
+template <int W, int LOG2P> struct RegionShape {
+    static constexpr uint32_t P = 1u << LOG2P;
+    static constexpr int SV = Sector<W>::kTuples;
+    static constexpr int PV = Tup<W>::kPerVec;
+    static constexpr int VPT = 4;                    // 16-byte vectors per thread per tile
+    static constexpr int IT = VPT * PV;              // tuples per thread per tile
+    static constexpr uint32_t T = kRegionThreads * IT;
+    static constexpr size_t kBudget = 227u * 1024u - 1024u;  // dynamic shared memory
+    static constexpr uint32_t K0 = (uint32_t)((kBudget - (size_t)P * 12) / ((size_t)P * 2 * W)) / SV * SV;
+    static constexpr uint32_t K = K0 > 64 ? 64 : K0; // slots per digit
+    static constexpr size_t kSmem = (size_t)K * P * 2 * W + (size_t)P * 12;
+};
+
+template <int W, int LOG2P>
+__global__ void __launch_bounds__(kRegionThreads, 1) scatter_region_kernel(
+    const void *in, uint64_t n_total, const uint64_t *seg_off, uint64_t nseg, const unsigned long long *cb,
+    uint64_t chunk, int shift, const unsigned long long *Hs, void *out, uint64_t sent_k0, uint64_t sent_k1,
+    const void *const *seg_ptrs) {
+    using U = typename Tup<W>::U;
+    using Vec = typename Tup<W>::Vec;
+    using RS = RegionShape<W, LOG2P>;
+    using Slot = typename SortSlot<W>::T;
+    constexpr uint32_t P = RS::P, K = RS::K;
+    constexpr int SV = RS::SV, PV = RS::PV, VPT = RS::VPT, NT = kRegionThreads;
+    static_assert(K >= 2 * SV, "each digit needs room for a carried partial sector and a whole one");
+    extern __shared__ __align__(16) unsigned char smem[];
+    Slot *region = (Slot *)smem;                     // K * P
+    uint32_t *fill = (uint32_t *)(region + K * P);  // P: slots taken (may pass K)
+    uint32_t *head = fill + P;                       // P: next row of whole sectors
+    uint32_t *tail = head + P;                       // P: rows at and above belong to overflow tuples
+
+    const uint64_t g = blockIdx.x;
+    if (g >= cb[nseg]) return;
+    const ChunkPos cp = chunk_pos(seg_off, nseg, cb, chunk, g);
+    const uint64_t row = cb[cp.s] * P;
+    const uint64_t seg_start = seg_off[0] + Hs[row];
+    const uint64_t obase = seg_start / SV * SV;
+    Slot *outp = (Slot *)out + obase;
+    // this chunk's tuples: rows [lo, hi) of src; lo is a whole number of vectors
+    // (chunks, segments and arrays start on 16 bytes)
+    const void *src = seg_ptrs ? seg_ptrs[cp.s] : in;
+    const uint64_t ioff = seg_ptrs ? seg_off[cp.s] : 0;
+    const Vec *vsrc = (const Vec *)src + (cp.lo - ioff) / PV;
+    const uint32_t nrows = (uint32_t)(cp.hi - cp.lo);
+    for (uint32_t d = threadIdx.x; d < P; d += NT) {
+        // the run of (this chunk, d) is [Hs[i], Hs[i + 1]): the scan is in (digit,
+        // chunk) order, so the next entry starts the next run of the pass
+        const uint64_t i = row + (uint64_t)d * cp.nch + cp.cidx;
+        head[d] = (uint32_t)(seg_off[0] + Hs[i] - obase);
+        tail[d] = (uint32_t)(seg_off[0] + Hs[i + 1] - obase);
+        fill[d] = 0;
+    }
+    // vector j of the tile [t0, lim) for this thread; a last vector holding one
+    // tuple of a 4-byte relation is read with an 8-byte load (nothing past the
+    // array end)
+    auto load = [&](uint32_t t0, uint32_t lim, Vec *v) {
+#pragma unroll
+        for (int j = 0; j < VPT; ++j) {
+            const uint32_t r0 = t0 + ((uint32_t)j * NT + threadIdx.x) * PV;
+            if (r0 + PV <= lim) v[j] = ld_stream(vsrc + r0 / PV);
+            else if (r0 < lim) {
+                if constexpr (W == 4) {
+                    const uint2 x = ((const uint2 *)vsrc)[r0];
+                    v[j] = make_uint4(x.x, x.y, 0u, 0u);
+                }
+            }
+        }
+    };
+    auto tile_end = [&](uint32_t t0) { return t0 + RS::T < nrows ? t0 + RS::T : nrows; };
+    Vec cur[VPT], nxt[VPT];
+    if (nrows) load(0, tile_end(0), cur);
+    __syncthreads();
+    for (uint32_t t0 = 0, t1; t0 < nrows; t0 = t1) {
+        t1 = tile_end(t0);
+        if (t1 < nrows) load(t1, tile_end(t1), nxt);
+        // 1. insert
+#pragma unroll
+        for (int j = 0; j < VPT; ++j) {
+#pragma unroll
+            for (int e = 0; e < PV; ++e) {
+                const uint32_t r = t0 + ((uint32_t)j * NT + threadIdx.x) * PV + e;
+                if (r >= t1) continue;
+                Slot sl;
+                U k;
+                if constexpr (W == 4) {
+                    k = e ? cur[j].z : cur[j].x;
+                    const uint32_t rid = e ? cur[j].w : cur[j].y;
+                    sl = (unsigned long long)k | ((unsigned long long)rid << 32);
+                } else {
+                    k = cur[j].x;
+                    sl = cur[j];
+                }
+                const uint32_t d = (uint32_t)(key_hash<W>(k) >> shift) & (P - 1u);
+                const uint32_t pos = atomicAdd(&fill[d], 1u);
+                if (pos < K) region[(pos << LOG2P) | d] = sl;
+                else outp[atomicSub(&tail[d], 1u) - 1u] = sl;
+            }
+        }
+        __syncthreads();
+        // 2. flush whole sectors, keep the rest at the front
+#pragma unroll
+        for (uint32_t d0 = 0; d0 < (P + NT - 1) / NT * NT; d0 += NT) {
+            const uint32_t d = d0 + threadIdx.x;
+            if (P % NT && d >= P) break;
+            const uint32_t f = fill[d];
+            const uint32_t n = f < K ? f : K;
+            if (n >= (uint32_t)SV) {
+                const uint32_t whole = n / SV * SV;
+                const uint32_t hd = head[d];
+                for (uint32_t s0 = 0; s0 < whole; s0 += SV) {
+                    Slot tup[SV];
+#pragma unroll
+                    for (int q = 0; q < SV; ++q) tup[q] = region[((s0 + q) << LOG2P) | d];
+                    st_sector(outp + hd + s0, (const unsigned long long *)tup);
+                }
+                for (uint32_t q = whole; q < n; ++q) region[((q - whole) << LOG2P) | d] = region[(q << LOG2P) | d];
+                head[d] = hd + whole;
+                fill[d] = n - whole;
+            } else if (f != n) {
+                fill[d] = n;
+            }
+        }
+        __syncthreads();
+#pragma unroll
+        for (int j = 0; j < VPT; ++j) cur[j] = nxt[j];
+    }
+    // the gap [head, tail) of every run: its carried tuples, then padding
+    for (uint32_t d = threadIdx.x; d < P; d += NT) {
+        const uint32_t hd = head[d], tl = tail[d], c = fill[d];
+        const uint64_t sk = ((uint32_t)(key_hash<W>((U)sent_k0) >> shift) & (P - 1u)) != d ? sent_k0 : sent_k1;
+        Slot pt;
+        if constexpr (W == 4) pt = (unsigned long long)(uint32_t)sk;
+        else pt = make_ulonglong2(sk, 0ull);
+        for (uint32_t r = hd; r < tl; ++r) outp[r] = r - hd < c ? region[((r - hd) << LOG2P) | d] : pt;
+    }
+}
+
+template <int W, int LOG2P>
+static hj_status launch_region(hj_ctx *c, unsigned grid, const void *in, uint64_t n_total, const uint64_t *seg_off,
+                               uint64_t nseg, const unsigned long long *cb, uint64_t chunk, int shift,
+                               const unsigned long long *Hs, void *out, uint64_t k0, uint64_t k1,
+                               const void *const *seg_ptrs) {
+    auto kern = scatter_region_kernel<W, LOG2P>;
+    const size_t smem = RegionShape<W, LOG2P>::kSmem;
+    HJ_TRY(allow_max_smem(c, (const void *)kern));
+    HJ_LAUNCH(c, "partition_scatter", kern, grid, kRegionThreads, smem, in, n_total, seg_off, nseg, cb, chunk, shift,
+              Hs, out, k0, k1, seg_ptrs);
+    return HJ_OK;
+}
+
+template <int W>
+static hj_status launch_region_bits(hj_ctx *c, int bits, unsigned grid, const void *in, uint64_t n_total,
+                                    const uint64_t *seg_off, uint64_t nseg, const unsigned long long *cb,
+                                    uint64_t chunk, int shift, const unsigned long long *Hs, void *out, uint64_t k0,
+                                    uint64_t k1, const void *const *seg_ptrs) {
+#define HJ_RG(B)                                                                                                 \
+    case B:                                                                                                      \
+        return launch_region<W, B>(c, grid, in, n_total, seg_off, nseg, cb, chunk, shift, Hs, out, k0, k1, seg_ptrs)
+    switch (bits) {
+        HJ_RG(1); HJ_RG(2); HJ_RG(3); HJ_RG(4); HJ_RG(5); HJ_RG(6);
+        HJ_RG(7); HJ_RG(8); HJ_RG(9); HJ_RG(10); HJ_RG(11);
+        default: return set_err(c, HJ_E_INVALID, "region scatter takes 1..11 bits, not %d", bits);
+    }
+#undef HJ_RG
+}
+
 // ------------------------------------------------------------------- driver
 
 // Scatter configuration (threads, vectors per thread) for a fan-out: 8192-tuple
@@ -824,7 +1011,14 @@ hj_status partition_pass(hj_ctx *c, int width, const void *in, uint64_t n_total,
                   chunk, shift, bits, Hs, out, pad, k0, k1);                                                  \
     } while (0)
     const size_t tma_smem = width == 4 ? scatter_tma_smem_bytes<4>((uint32_t)P) : scatter_tma_smem_bytes<8>((uint32_t)P);
-    if (cfg.tma) {
+    if (cfg.tma && pad) {
+        if (width == 4)
+            HJ_TRY(launch_region_bits<4>(c, bits, (unsigned)max_chunks, in, n_total, seg_off, nseg, cb, chunk, shift,
+                                         Hs, out, k0, k1, seg_ptrs));
+        else
+            HJ_TRY(launch_region_bits<8>(c, bits, (unsigned)max_chunks, in, n_total, seg_off, nseg, cb, chunk, shift,
+                                         Hs, out, k0, k1, seg_ptrs));
+    } else if (cfg.tma) {
         if (width == 4) {
             HJ_TRY(allow_max_smem(c, (const void *)scatter_tma_kernel<4>));
             HJ_LAUNCH(c, "partition_scatter", scatter_tma_kernel<4>, (unsigned)max_chunks, kTmaThreads, tma_smem, in,
