@@ -447,27 +447,28 @@ __device__ __forceinline__ typename HashT<W>::type hashw(typename Tup<W>::U k) {
 template <int W> struct SoaTab {
     using T = typename Tup<W>::U;
     static constexpr uint32_t G = 16 / W;
-    uint32_t kbase;  // shared address of the key region: 16 bytes (G keys) per bucket
-    uint32_t rbase;  // shared address of the rid region, same shape
     uint32_t nb;     // buckets
     T empty;
     const uint32_t *ovf;
 
     __device__ __forceinline__ bool overflowed(uint32_t b) const { return (ovf[b >> 5] >> (b & 31)) & 1u; }
-    // keys (half 0) or rids (half 1) of bucket b
+    // keys (half 0) or rids (half 1) of bucket b.  Plain loads through the
+    // shared-memory pointers: the compiler orders them with the barriers and may
+    // overlap the independent lookups of a thread's items.
+    const T *kptr;   // key region: G keys (16 bytes) per bucket
+    const T *rptr;   // rid region, same shape
     __device__ __forceinline__ void ld(uint32_t b, uint32_t half, T *v) const {
-        const uint32_t a = (half ? rbase : kbase) + b * 16u;
-        if constexpr (W == 4)
-            asm volatile("ld.shared.v4.u32 {%0, %1, %2, %3}, [%4];" : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]) : "r"(a));
-        else
-            asm volatile("ld.shared.v2.u64 {%0, %1}, [%2];" : "=l"(v[0]), "=l"(v[1]) : "r"(a));
+        const T *p = (half ? rptr : kptr) + b * G;
+        if constexpr (W == 4) {
+            const uint4 x = *(const uint4 *)p;
+            v[0] = x.x; v[1] = x.y; v[2] = x.z; v[3] = x.w;
+        } else {
+            const ulonglong2 x = *(const ulonglong2 *)p;
+            v[0] = x.x; v[1] = x.y;
+        }
     }
     __device__ __forceinline__ T ld1(uint32_t b, uint32_t half, uint32_t q) const {
-        T v;
-        const uint32_t a = (half ? rbase : kbase) + b * 16u + q * (uint32_t)W;
-        if constexpr (W == 4) asm volatile("ld.shared.u32 %0, [%1];" : "=r"(v) : "r"(a));
-        else asm volatile("ld.shared.u64 %0, [%1];" : "=l"(v) : "r"(a));
-        return v;
+        return (half ? rptr : kptr)[b * G + q];
     }
 };
 
@@ -862,7 +863,6 @@ __global__ void __launch_bounds__(NT, 2048 / NT / 2) partition_join_kernel(
     __shared__ int s_full;
     __shared__ unsigned long long s_p;
     __shared__ StageShared s_stage;
-    const uint32_t sbase = (uint32_t)__cvta_generic_to_shared(smem);
     const unsigned lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
 
     Sink sink;
@@ -912,7 +912,7 @@ __global__ void __launch_bounds__(NT, 2048 / NT / 2) partition_join_kernel(
         uint32_t *ovf = (uint32_t *)(smem + (size_t)cap_max * (AGG ? sizeof(AggSlot<W>) : 2 * W));
         const T top = Tup<W>::kAllOnes;
         const T empty = pf.keep(hashw<W>(top)) ? (T)tk.ek1 : top;
-        const SoaTab<W> tab{sbase, sbase + (cap / G) * 16u, cap / G, empty, ovf};
+        const SoaTab<W> tab{cap / G, empty, ovf, (const T *)smem, (const T *)smem + cap};
         if (work_p) {
             if (AGG) {
                 AggSlot<W> *sl = (AggSlot<W> *)smem;
