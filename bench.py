@@ -83,6 +83,28 @@ def dist_env():
     return ws, rank, local
 
 
+# ------------------------------------------------------------------- ranks
+
+
+def ranks_max(x: float, ws: int, dev=None) -> float:
+    """Max over ranks of a local measurement (one all-reduce of a scalar; the join
+    itself exchanges nothing between ranks)."""
+    if ws <= 1:
+        return x
+    import torch
+    import torch.distributed as dist
+
+    t = torch.tensor([x], dtype=torch.float64, device=dev)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def weak_value(units_per_rank_step: int, steps: int, ws: int, ms_max: float) -> float:
+    """Whole-job throughput of independent per-rank problems: the units every rank
+    processed over the slowest rank's time."""
+    return units_per_rank_step * steps * ws / (ms_max / 1000.0)
+
+
 # ------------------------------------------------------------------- peaks, clocks
 
 
@@ -363,13 +385,9 @@ def run_hj(args, wl, ws, rank, local):
     prof = hj.prof_read(ctx)
     hj.prof_enable(ctx, False)
     clocks = sampler.stop() if not args.no_clocks else None
-    if ws > 1:
-        t = torch.tensor([ms], device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms = float(t.item())
+    ms = ranks_max(ms, ws, dev)
     count, bits, passes, algo = info
-    tuples = (wl["nr"] + wl["ns"]) * args.steps * ws
-    value = tuples / (ms / 1000.0)
+    value = weak_value(wl["nr"] + wl["ns"], args.steps, ws, ms)
 
     # roofline of the dominant kernel (algorithmic bytes / its event-timed duration)
     peak, peak_kind = measured_peak()
@@ -408,12 +426,8 @@ def run_hj(args, wl, ws, rank, local):
         for _ in range(args.e2e_steps):
             res = hj.hj_join_host(ctx, Rh, Sh, out, **kw)
         torch.cuda.synchronize()
-        dt = time.perf_counter() - t0
-        if ws > 1:
-            t = torch.tensor([dt], device=dev)
-            dist.all_reduce(t, op=dist.ReduceOp.MAX)
-            dt = float(t.item())
-        e2e = {"value": (wl["nr"] + wl["ns"]) * args.e2e_steps * ws / dt, "unit": UNIT,
+        dt = ranks_max(time.perf_counter() - t0, ws, dev)
+        e2e = {"value": weak_value(wl["nr"] + wl["ns"], args.e2e_steps, ws, dt * 1000.0), "unit": UNIT,
                "h2d_bytes_per_step": 8 * (wl["nr"] + wl["ns"]), "d2h_bytes_per_step": 8 * m + 24,
                "api": "hj_join_host", "steps": args.e2e_steps}
         del Rh, Sh, out
@@ -514,12 +528,7 @@ def run_batch(args, wl, ws, rank, local):
             out = fn()
         e1.record(stream)
         torch.cuda.synchronize()
-        ms = e0.elapsed_time(e1)
-        if ws > 1:
-            t = torch.tensor([ms], device=dev)
-            dist.all_reduce(t, op=dist.ReduceOp.MAX)
-            ms = float(t.item())
-        return ms, out
+        return ranks_max(e0.elapsed_time(e1), ws, dev), out
 
     for _ in range(args.warmup):
         counts = batched()
@@ -532,13 +541,13 @@ def run_batch(args, wl, ws, rank, local):
     launches = hj.launch_count(ctx) - l0
     clocks = sampler.stop() if not args.no_clocks else None
     pairs = sum(counts)
-    value = tuples_step * args.steps * ws / (ms / 1000.0)
+    value = weak_value(tuples_step, args.steps, ws, ms)
 
     # the same joins one hj_join call at a time
     plain()
     psteps = max(1, min(args.steps, args.plain_steps))
     pms, _ = timed(plain, psteps)
-    plain_value = tuples_step * psteps * ws / (pms / 1000.0)
+    plain_value = weak_value(tuples_step, psteps, ws, pms)
 
     # kernel times from one profiled step without the graph (events are not captured)
     hj.prof_reset(ctx)

@@ -157,7 +157,11 @@ uint64_t first_capacity(const hj_opts &o, uint64_t nS, uint64_t warps) {
 }
 
 // ----------------------------------------------------------------------- SHJ
-hj_status probe_into(hj_ctx *c, const hj_table *t, const hj_rel *S, const hj_opts &o, hj_result *res) {
+// With `after_build` the counters hold the status of a build queued just before
+// (no host synchronisation in between): the first attempt keeps them, and a full
+// table is reported after the probe.
+hj_status probe_into(hj_ctx *c, const hj_table *t, const hj_rel *S, const hj_opts &o, hj_result *res,
+                     bool after_build = false) {
     const bool mat = o.mode == HJ_MATERIALIZE, chk = wants_checksum(o);
     const uint64_t warps = table_probe_warps(c, S->n);
     PairSink sink(c, t->width);
@@ -168,10 +172,11 @@ hj_status probe_into(hj_ctx *c, const hj_table *t, const hj_rel *S, const hj_opt
             HJ_TRY(sink.reset(cap));
             HJ_TRY(sink.new_area(warps, &ra));
         }
-        HJ_TRY(zero_counters(c));
+        if (!(after_build && attempt == 0)) HJ_TRY(zero_counters(c));
         HJ_TRY(table_probe(c, t, S->tuples, 0, S->n, S->n, sink.pairs.p, sink.pcap, chk, ra, PartFilter{0, 0, 0, 0}));
         if (mat) HJ_TRY(sink.finalize_device(c->d_ctr));
         HJ_TRY(read_counters(c));
+        if (c->h_ctr->status & kStatusTableFull) return set_err(c, HJ_E_CUDA, "hash table unexpectedly full");
         HJ_TRY(check_output_status(c));
         if (!mat || c->h_ctr->cursor <= sink.pcap) break;
         // more pairs than the capacity: run the probe again at the exact size
@@ -189,9 +194,7 @@ hj_status join_shj(hj_ctx *c, const hj_rel *R, const hj_rel *S, const hj_opts &o
     HJ_TRY(zero_counters(c));
     HJ_TRY(table_create(c, R->width, is_agg(o.mode), R->n, &tg.t));
     HJ_TRY(table_build(c, tg.t, R->tuples, 0, R->n, R->n, PartFilter{0, 0, 0, 0}));
-    HJ_TRY(read_counters(c));
-    if (c->h_ctr->status & kStatusTableFull) return set_err(c, HJ_E_CUDA, "hash table unexpectedly full");
-    return probe_into(c, tg.t, S, o, res);
+    return probe_into(c, tg.t, S, o, res, true);
 }
 
 // ----------------------------------------------------------------------- PHJ
