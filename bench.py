@@ -50,6 +50,14 @@ WORKLOADS = {
         desc="serving: 20000 join requests, Poisson arrivals, |R| log-uniform in [2^12, 2^24], |S| log-uniform "
              "in [|R|, 16|R|] (uint32 key, uint32 rid), R keys a permutation of 1..|R|, S keys uniform over "
              "[1, 2|R|] (50% match), pairs materialised; HBM admission budget 120 GiB"),
+    "zipf_4m_64m_t05": dict(
+        kind="zipf", nr=1 << 22, ns=1 << 26, ranks=1 << 20, theta_r=0.75, theta_s=0.5, algo=2, width=8, mode=1,
+        desc="skewed PHJ, |R|=2^22, |S|=2^26 (uint64 key, uint64 payload); R keys Zipf(0.75), S keys Zipf(0.5) "
+             "over the same 2^20 distinct 64-bit keys; count and checksums (about 4.9e9 pairs, not materialised)"),
+    "zipf_4m_64m_t10": dict(
+        kind="zipf", nr=1 << 22, ns=1 << 26, ranks=1 << 20, theta_r=0.75, theta_s=1.0, algo=2, width=8, mode=1,
+        desc="skewed PHJ, |R|=2^22, |S|=2^26 (uint64 key, uint64 payload); R keys Zipf(0.75), S keys Zipf(1.0) "
+             "over the same 2^20 distinct 64-bit keys; count and checksums (about 3.1e11 pairs, not materialised)"),
     "shj_1m": dict(
         nr=1 << 20, ns=1 << 20, dom=1 << 20, algo=1,
         desc="SHJ, |R|=|S|=2^20 (uint32 key, uint32 rid); R keys a permutation of 1..2^20, S keys drawn "
@@ -207,18 +215,27 @@ def traffic_record(kernel: str, workload: str):
 # ------------------------------------------------------------------- CPU oracle
 
 
-def oracle_rate(R_np, S_np):
-    """Run the oracle's hash join once; return (tuples, seconds)."""
+def oracle_rate(R_np, S_np, mode=2):
+    """Run the oracle's hash join once (pairs materialised), or its per-key
+    aggregation in the count modes; return (tuples, seconds, pairs)."""
     import oracle
 
     t0 = time.perf_counter()
-    rr, ss = oracle.hash_join(R_np, S_np, cap_hint=len(S_np))
+    if mode == 2:
+        rr, ss = oracle.hash_join(R_np, S_np, cap_hint=len(S_np))
+        m = len(rr)
+    else:
+        m = oracle.join_aggregate(R_np, S_np)[0]
     dt = time.perf_counter() - t0
-    return len(R_np) + len(S_np), dt, len(rr)
+    return len(R_np) + len(S_np), dt, m
 
 
 def make_inputs(wl, rank, device):
     from paper_1307_1955_gb300 import workload as W
+
+    if wl.get("kind") == "zipf":
+        return W.zipf_pair(wl["nr"], wl["ns"], wl["theta_r"], wl["theta_s"], wl["ranks"], W.DEFAULT_SEED, device,
+                           ids=(3, int(wl["theta_s"] * 10), rank))
 
     return W.unique_and_uniform(wl["nr"], wl["ns"], wl["dom"], W.DEFAULT_SEED, device, ids=(2, rank))
 
@@ -227,17 +244,19 @@ def cpu_sample(wl, R, S, target_s: float):
     """Oracle on a bounded sample: all of R and a prefix of S sized to about target_s."""
     from paper_1307_1955_gb300 import workload as W
 
+    mode = wl.get("mode", 2)
     Rn = W.to_numpy_u(R)
     ns0 = min(len(S), 1 << 20)
-    n, dt, _ = oracle_rate(Rn, W.to_numpy_u(S[:ns0]))
+    n, dt, _ = oracle_rate(Rn, W.to_numpy_u(S[:ns0]), mode)
     # time per S tuple beyond the build, from one calibration run
     rate = max(n / dt, 1.0)
     want = int(min(len(S), max(ns0, rate * target_s - len(Rn))))
     Ss = W.to_numpy_u(S[:want])
-    n, dt, m = oracle_rate(Rn, Ss)
+    n, dt, m = oracle_rate(Rn, Ss, mode)
+    what = f"{m} pairs materialised" if mode == 2 else f"{m} pairs counted by per-key aggregation"
     return {"value": n / dt, "unit": UNIT, "cores": 1, "kind": "oracle",
             "sample": f"all |R|={len(Rn)} tuples, first {want} of |S|={len(S)} tuples "
-                      f"({m} pairs materialised), single-threaded C oracle, {dt:.1f} s"}
+                      f"({what}), single-threaded C oracle, {dt:.1f} s"}
 
 
 # ------------------------------------------------------------------- arms
@@ -255,8 +274,11 @@ def run_reference(args, wl, ws, rank):
     oracle.build()
     total = args.steps + args.warmup
     per_step = max(0.05, min(20.0, 150.0 / max(total, 1)))
-    if wl.get("kind") == "batch":
+    if wl.get("kind") in ("batch", "serve"):
         run_reference_batch(args, wl, ws, per_step)
+        return
+    if wl.get("kind") == "zipf":
+        run_reference_prefix(args, wl, ws, per_step)
         return
     # Scale the workload down (|S| / |R| and the key-domain ratio kept) so that one
     # step takes about per_step seconds: time the oracle at 1/256 and extrapolate.
@@ -290,15 +312,52 @@ def run_reference(args, wl, ws, rank):
     print(json.dumps(line), flush=True)
 
 
-def run_reference_batch(args, wl, ws, per_step):
-    """Oracle on the batch's joins in order: each step joins the first joins of the
-    batch whose oracle time adds up to about per_step seconds."""
+def run_reference_prefix(args, wl, ws, per_step):
+    """Oracle on the workload's own relations: all of R and the prefix of S whose
+    oracle time is about per_step seconds (count modes: per-key aggregation)."""
     from paper_1307_1955_gb300 import workload as W
 
-    specs = W.batched_specs(wl["njoins"], W.DEFAULT_SEED)
+    mode = wl.get("mode", 2)
+    R, S = make_inputs(wl, 0, "cpu")
+    Rn = W.to_numpy_u(R)
+    ns0 = min(len(S), 1 << 20)
+    n, dt, _ = oracle_rate(Rn, W.to_numpy_u(S[:ns0]), mode)
+    want = int(min(len(S), max(ns0, max(n / dt, 1.0) * per_step - len(Rn))))
+    Sn = W.to_numpy_u(S[:want])
+    for _ in range(args.warmup):
+        oracle_rate(Rn, Sn, mode)
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        oracle_rate(Rn, Sn, mode)
+    dt = time.perf_counter() - t0
+    value = (len(Rn) + len(Sn)) * args.steps / dt
+    sample = (f"all |R|={len(Rn)} tuples and the first {want} of |S|={len(S)} tuples, single-threaded C oracle, "
+              + ("pairs materialised" if mode == 2 else "count and checksums by per-key aggregation"))
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": 1000 * dt / max(args.steps, 1), "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "u32" if wl.get("width", 4) == 4 else "u64",
+        "data": "synthetic", "config": {"workload": wl["desc"], "sample": sample},
+        "cpu_baseline": {"value": value, "unit": UNIT, "kind": "oracle", "cores": 1, "sample": sample},
+        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+
+
+def run_reference_batch(args, wl, ws, per_step):
+    """Oracle on the batch's (or the request stream's) joins in order: each step
+    joins the first joins whose oracle time adds up to about per_step seconds."""
+    from paper_1307_1955_gb300 import workload as W
+
+    if wl.get("kind") == "serve":
+        specs = W.serving_specs(wl["nreq"], W.DEFAULT_SEED, 1.0)
+        gen_ids = lambda j: (5, j)  # noqa: E731
+    else:
+        specs = W.batched_specs(wl["njoins"], W.DEFAULT_SEED)
+        gen_ids = lambda j: (4, j)  # noqa: E731
     sample, acc = [], 0.0
     for j, sp in enumerate(specs):
-        R, S = W.unique_and_uniform(sp.n_r, sp.n_s, sp.s_domain, W.DEFAULT_SEED, "cpu", ids=(4, j))
+        R, S = W.unique_and_uniform(sp.n_r, sp.n_s, sp.s_domain, W.DEFAULT_SEED, "cpu", ids=gen_ids(j))
         sample.append((W.to_numpy_u(R), W.to_numpy_u(S)))
         acc += oracle_rate(*sample[-1])[1]
         if acc >= per_step:
@@ -345,13 +404,16 @@ def run_hj(args, wl, ws, rank, local):
     R, S = make_inputs(wl, rank, dev)
     stream = torch.cuda.current_stream(dev)
     ctx = hj.Context(local, stream=stream)
-    kw = dict(algo=wl["algo"] if args.algo < 0 else args.algo, radix_bits=args.radix_bits, passes=args.passes)
+    mode = wl.get("mode", hj.HJ_MATERIALIZE)
+    w = wl.get("width", 4)
+    kw = dict(algo=wl["algo"] if args.algo < 0 else args.algo, radix_bits=args.radix_bits, passes=args.passes,
+              mode=mode)
     tuned = None
     if args.algo < 0 and args.radix_bits == 0 and args.passes == 0 and not args.no_tune:
         # the autotuner times the cost model's cheapest plans on these relations
         # (untimed); the timed joins then run its pick through HJ_ALGO_AUTO
-        tuned = hj.hj_tune(ctx, R, S)
-        kw = dict(algo=hj.HJ_ALGO_AUTO)
+        tuned = hj.hj_tune(ctx, R, S, mode=mode)
+        kw = dict(algo=hj.HJ_ALGO_AUTO, mode=mode)
 
     def step():
         res = hj.hj_join(ctx, R, S, **kw)
@@ -391,10 +453,10 @@ def run_hj(args, wl, ws, rank, local):
 
     # roofline of the dominant kernel (algorithmic bytes / its event-timed duration)
     peak, peak_kind = measured_peak()
-    w = 4
+    out_pairs = count if mode == hj.HJ_MATERIALIZE else 0
     dom_name, (dom_launches, dom_ms) = max(prof.items(), key=lambda kv: kv[1][1])
     g = max(passes, 1) if algo == 2 else 0
-    bytes_k = kernel_bytes(dom_name, wl, w, g, count) * args.steps
+    bytes_k = kernel_bytes(dom_name, wl, w, g, out_pairs) * args.steps
     achieved = bytes_k / (dom_ms / 1000.0) / 1e9 if dom_ms > 0 else 0.0
     per_launch_bytes = bytes_k / max(dom_launches, 1)
     roofline = {"bound": "hbm", "kernel": dom_name, "achieved": achieved, "peak": peak, "unit": "GB/s",
@@ -403,9 +465,9 @@ def run_hj(args, wl, ws, rank, local):
                 "avg_launch_ms": dom_ms / max(dom_launches, 1),
                 "traffic": traffic_record(dom_name, args.workload)}
     # whole-join roofline: (2g + 1) w (|R| + |S|) + o M bytes per step (PHJ), w (|R|+|S|) + o M (SHJ)
-    n = wl["nr"] + wl["ns"]
-    join_bytes = ((2 * g + 1) * 8 * n if algo == 2 else 8 * n) + 8 * count
-    join_bytes_g1 = 3 * 8 * n + 8 * count if algo == 2 else join_bytes
+    n, tb = wl["nr"] + wl["ns"], 2 * w
+    join_bytes = ((2 * g + 1) * tb * n if algo == 2 else tb * n) + tb * out_pairs
+    join_bytes_g1 = 3 * tb * n + tb * out_pairs if algo == 2 else join_bytes
     step_s = ms / 1000.0 / args.steps
     join_roof = {"bytes_per_step": join_bytes, "achieved_gbs": join_bytes / step_s / 1e9,
                  "frac": join_bytes / step_s / 1e9 / peak, "frac_vs_g1": join_bytes_g1 / step_s / 1e9 / peak}
@@ -417,7 +479,8 @@ def run_hj(args, wl, ws, rank, local):
     if not args.no_e2e:
         Rh = R.cpu().pin_memory()
         Sh = S.cpu().pin_memory()
-        out = torch.empty((wl["ns"] + (1 << 20), 2), dtype=torch.int32).pin_memory()
+        out = (torch.empty((wl["ns"] + (1 << 20), 2), dtype=R.dtype).pin_memory()
+               if mode == hj.HJ_MATERIALIZE else None)
         res = hj.hj_join_host(ctx, Rh, Sh, out, **kw)
         m = res.count
         if ws > 1:
@@ -428,7 +491,8 @@ def run_hj(args, wl, ws, rank, local):
         torch.cuda.synchronize()
         dt = ranks_max(time.perf_counter() - t0, ws, dev)
         e2e = {"value": weak_value(wl["nr"] + wl["ns"], args.e2e_steps, ws, dt * 1000.0), "unit": UNIT,
-               "h2d_bytes_per_step": 8 * (wl["nr"] + wl["ns"]), "d2h_bytes_per_step": 8 * m + 24,
+               "h2d_bytes_per_step": tb * (wl["nr"] + wl["ns"]),
+               "d2h_bytes_per_step": (tb * m if mode == hj.HJ_MATERIALIZE else 0) + 24,
                "api": "hj_join_host", "steps": args.e2e_steps}
         del Rh, Sh, out
 
@@ -440,12 +504,13 @@ def run_hj(args, wl, ws, rank, local):
         line = {
             "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True, "scaling": "weak",
-            "vs_baseline": None, "dtype": "u32", "data": "synthetic",
+            "vs_baseline": None, "dtype": "u32" if w == 4 else "u64", "data": "synthetic",
             "config": {"workload": wl["desc"], "algo": {1: "SHJ", 2: "PHJ"}[algo], "radix_bits": bits,
+                       "mode": {0: "count", 1: "count+checksum", 2: "pairs materialised"}[mode],
                        "passes": passes, "plan": "hj_tune" if tuned else "forced",
                        "tuned": tuned, "pairs_per_step": count, "parallelism": f"replicas x{ws}",
-                       "l2": "inputs 2.28 GB per step exceed the 129 MB L2; no flush"
-                       if wl["ns"] >= (1 << 24) else "inputs smaller than L2; warm L2 across steps"},
+                       "l2": f"inputs {tb * n / 1e9:.2f} GB per step exceed the 129 MB L2; no flush"
+                       if tb * n > 129e6 else "inputs smaller than L2; warm L2 across steps"},
             "roofline": roofline, "join_roofline": join_roof, "kernels": kernels,
             "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches, "clocks": clocks,
         }

@@ -206,8 +206,8 @@ __global__ void set_slot_kernel(JoinSlot *s, void *pairs, unsigned long long pca
 }
 
 hj_status run_partition_join(hj_ctx *c, const hj_rel *R, const hj_rel *S, const hj_opts &o, const void *Rp,
-                             const uint64_t *roff, const void *Sp, const uint64_t *soff, uint64_t NP, int b1, int b2,
-                             PairSink *sink, uint32_t *oversize, PartTask *tasks, JoinSlot *slot_dev) {
+                             const uint64_t *roff, const void *Sp, const uint64_t *soff, uint64_t NP, uint64_t ntasks,
+                             int b1, int b2, PairSink *sink, uint32_t *oversize, PartTask *tasks, JoinSlot *slot_dev) {
     const bool agg = is_agg(o.mode), chk = wants_checksum(o), mat = o.mode == HJ_MATERIALIZE;
     const int W = R->width;
     RecArea ra{nullptr, nullptr, 0};
@@ -217,7 +217,7 @@ hj_status run_partition_join(hj_ctx *c, const hj_rel *R, const hj_rel *S, const 
     const uint64_t pcap = mat ? sink->pcap : 0;
     HJ_LAUNCH(c, "set_slot", set_slot_kernel, 1, 1, 0, slot_dev, pairs, (unsigned long long)pcap, c->d_ctr);
     const uint64_t expect = NP ? (R->n + NP - 1) / NP : 0;
-    HJ_TRY(partition_join(c, W, agg, tasks, NP, slot_dev, expect, chk, oversize, ra, nullptr, 0));
+    HJ_TRY(partition_join(c, W, agg, tasks, ntasks, slot_dev, expect, chk, oversize, ra, nullptr, 0));
     if (mat) HJ_TRY(sink->finalize_device(c->d_ctr));
     HJ_TRY(read_counters(c));
     HJ_TRY(check_output_status(c));
@@ -244,17 +244,18 @@ hj_status join_phj(hj_ctx *c, const hj_rel *R, const hj_rel *S, const hj_opts &o
     uint64_t r_rows = 0, s_rows = 0;
     HJ_TRY(partition_rel(c, R, b1, b2, 1, Rp, roff, &r_rows));
     HJ_TRY(partition_rel(c, S, b1, b2, 1, Sp, soff, &s_rows));
-    HJ_TRY(oversize.alloc(NP * 4));
-    HJ_TRY(tasks.alloc(NP * sizeof(PartTask)));
+    const uint64_t slice = task_slice_rows(R->width, S->n, NP), ntasks = max_tasks(NP, s_rows, slice);
+    HJ_TRY(oversize.alloc(ntasks * 4));
+    HJ_TRY(tasks.alloc(ntasks * sizeof(PartTask) + 8));
     HJ_TRY(slot.alloc(sizeof(JoinSlot)));
-    HJ_TRY(make_tasks(c, Rp.p, roff.as<uint64_t>(), Sp.p, soff.as<uint64_t>(), NP, 0, b1, b2, R->width,
+    HJ_TRY(make_tasks(c, Rp.p, roff.as<uint64_t>(), Sp.p, soff.as<uint64_t>(), NP, 0, b1, b2, R->width, slice, ntasks,
                       tasks.as<PartTask>()));
     const uint64_t warps = partition_join_warps(c);
     uint64_t cap = mat ? first_capacity(o, S->n, warps) : 0;
     for (int attempt = 0; attempt < 2; ++attempt) {
         if (mat) HJ_TRY(sink.reset(cap));
-        HJ_TRY(run_partition_join(c, R, S, o, Rp.p, roff.as<uint64_t>(), Sp.p, soff.as<uint64_t>(), NP, b1, b2, &sink,
-                                  oversize.as<uint32_t>(), tasks.as<PartTask>(), slot.as<JoinSlot>()));
+        HJ_TRY(run_partition_join(c, R, S, o, Rp.p, roff.as<uint64_t>(), Sp.p, soff.as<uint64_t>(), NP, ntasks, b1, b2,
+                                  &sink, oversize.as<uint32_t>(), tasks.as<PartTask>(), slot.as<JoinSlot>()));
         if (!mat || (c->h_ctr->cursor <= sink.pcap && c->h_ctr->count <= sink.pcap)) break;
         // more pairs than the buffer holds: the count is exact, run again at that size
         cap = c->h_ctr->count + warps * kChunkPairs;

@@ -51,9 +51,15 @@ struct JoinSlot {
     unsigned long long pad;
 };
 uint64_t empty_key2(int width, int b1, int b2);
-// Tasks for one join's NP partitions (device array `tasks`).
+// Tasks for one join's NP partitions (device array `tasks` of `ntasks` entries
+// plus 8 bytes, ntasks = max_tasks(NP, S rows, slice)): one per slice of at most
+// `slice` S rows of every partition; unused entries are empty.
+uint64_t task_slice_rows(int width, uint64_t n_s, uint64_t NP);
+uint64_t max_tasks(uint64_t NP, uint64_t s_rows, uint64_t slice);
 hj_status make_tasks(hj_ctx *c, const void *Rp, const uint64_t *roff, const void *Sp, const uint64_t *soff,
-                     uint64_t NP, uint32_t join, int b1, int b2, int width, PartTask *tasks);
+                     uint64_t NP, uint32_t join, int b1, int b2, int width, uint64_t slice, uint64_t ntasks,
+                     PartTask *tasks);
+
 
 // Per-partition join (Alg. 2's "apply SHJ on each partition pair") with the
 // table in shared memory; persistent CTAs take tasks from c->d_ctr->work (which

@@ -427,6 +427,13 @@ template <> __device__ __forceinline__ uint32_t part_bucket<8>(uint64_t k, uint3
     return __umulhi((uint32_t)((k * 0x9E3779B97F4A7C15ull) >> 32), nb);
 }
 
+// Bucket hash of a partition's shared-memory aggregate table (the value that
+// bucket_of<W> scales to the table): a Fibonacci multiply of the key, for the same
+// reason as part_bucket.
+template <int W> __device__ __forceinline__ uint64_t part_agg_hash(typename Tup<W>::U k);
+template <> __device__ __forceinline__ uint64_t part_agg_hash<4>(uint32_t k) { return (uint32_t)(k * 0x9E3779B1u); }
+template <> __device__ __forceinline__ uint64_t part_agg_hash<8>(uint64_t k) { return k * 0x9E3779B97F4A7C15ull; }
+
 template <int W>
 __device__ __forceinline__ typename HashT<W>::type hashw(typename Tup<W>::U k) {
     if constexpr (W == 4) return murmur2_u32(k);
@@ -946,7 +953,7 @@ __global__ void __launch_bounds__(NT, 2048 / NT / 2) partition_join_kernel(
                     if (!pf.keep(h)) continue;
                     bool ok = false;
                     if constexpr (AGG) {
-                        ok = agg_insert<W>((AggSlot<W> *)smem, cap, &side, k[e], mix_a(r[e]), h);
+                        ok = agg_insert<W>((AggSlot<W> *)smem, cap, &side, k[e], mix_a(r[e]), part_agg_hash<W>(k[e]));
                     } else {
                         T *kv = (T *)smem;
                         uint32_t bkt = part_bucket<W>(k[e], tab.nb);
@@ -1007,10 +1014,11 @@ __global__ void __launch_bounds__(NT, 2048 / NT / 2) partition_join_kernel(
                     if constexpr (AGG) {
 #pragma unroll
                         for (int i = 0; i < IT; ++i) {
-                            const Hh h = hashw<W>(k[i]);
-                            if (!val[i] || !pf.keep(h)) continue;
+                            // no partition filter: a padding tuple's key hashes to another
+                            // partition, so it is in neither the table nor the side aggregate
+                            if (!val[i]) continue;
                             uint64_t n, sa;
-                            atab.lookup(k[i], h, &n, &sa);
+                            atab.lookup(k[i], part_agg_hash<W>(k[i]), &n, &sa);
                             acc.cnt += n;
                             if (chk && n) {
                                 const uint64_t bb = mix_b(r[i]);
@@ -1102,29 +1110,58 @@ __global__ void __launch_bounds__(NT, 2048 / NT / 2) partition_join_kernel(
 
 // Tasks of one join partitioned into NP padded partitions: task p covers rows
 // [roff[p], roff[p+1]) of Rp and [soff[p], soff[p+1]) of Sp.
+// Tasks of one join partitioned into NP padded partitions.  Partition p covers
+// rows [roff[p], roff[p+1]) of Rp and [soff[p], soff[p+1]) of Sp.  Its S rows are
+// cut into slices of at most `slice` rows (a multiple of the sector's tuples, so
+// every slice starts on a sector), one task per slice, all with the whole R_p: a
+// partition that skew made large is probed by several CTAs at once, each building
+// its own copy of the (small) R_p table.  Task p is the first slice of partition
+// p; further slices take indices from NP on, handed out by a counter (*next,
+// zero at launch; their order does not matter).
 __global__ void make_tasks_kernel(const void *Rp, const uint64_t *roff, const void *Sp, const uint64_t *soff,
-                                  uint64_t NP, uint32_t join, int b1, int b2, uint64_t ek1, int tb, PartTask *tasks) {
+                                  uint64_t NP, uint64_t slice, unsigned long long *next, uint32_t join, int b1,
+                                  int b2, uint64_t ek1, int tb, PartTask *tasks) {
     for (uint64_t p = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; p < NP; p += (uint64_t)gridDim.x * blockDim.x) {
         PartTask t;
         t.R = (const char *)Rp + roff[p] * tb;
-        t.S = (const char *)Sp + soff[p] * tb;
         t.nr = (uint32_t)(roff[p + 1] - roff[p]);
-        t.ns = (uint32_t)(soff[p + 1] - soff[p]);
         t.join = join;
         t.p = (uint32_t)p;
         t.b1 = (uint16_t)b1;
         t.b2 = (uint16_t)b2;
         t.pad = 0;
         t.ek1 = ek1;
-        tasks[p] = t;
+        const uint64_t s0 = soff[p], ns = soff[p + 1] - s0;
+        const uint64_t extra = ns > slice ? (ns + slice - 1) / slice - 1 : 0;
+        const uint64_t base = extra ? NP + atomicAdd(next, (unsigned long long)extra) : 0;
+        for (uint64_t i = 0, at = 0; i == 0 || at < ns; ++i, at += slice) {
+            t.S = (const char *)Sp + (s0 + at) * tb;
+            t.ns = (uint32_t)(ns - at < slice ? ns - at : slice);
+            tasks[i == 0 ? p : base + i - 1] = t;
+        }
     }
 }
 
+uint64_t task_slice_rows(int width, uint64_t n_s, uint64_t NP) {
+    // four times the mean partition, at least 2^16 rows, whole sectors
+    const uint64_t sv = 32 / tuple_bytes(width);
+    uint64_t sl = 4 * ((n_s + NP - 1) / (NP ? NP : 1));
+    if (sl < (1ull << 16)) sl = 1ull << 16;
+    return (sl + sv - 1) / sv * sv;
+}
+
+uint64_t max_tasks(uint64_t NP, uint64_t s_rows, uint64_t slice) { return NP + s_rows / slice + 1; }
+
 hj_status make_tasks(hj_ctx *c, const void *Rp, const uint64_t *roff, const void *Sp, const uint64_t *soff,
-                     uint64_t NP, uint32_t join, int b1, int b2, int width, PartTask *tasks) {
+                     uint64_t NP, uint32_t join, int b1, int b2, int width, uint64_t slice, uint64_t ntasks,
+                     PartTask *tasks) {
     const unsigned grid = (unsigned)((NP + 255) / 256);
-    HJ_LAUNCH(c, "make_tasks", make_tasks_kernel, grid ? grid : 1, 256, 0, Rp, roff, Sp, soff, NP, join, b1, b2,
-              empty_key2(width, b1, b2), (int)tuple_bytes(width), tasks);
+    // unused task slots stay empty (no rows; the join skips them), and the slice
+    // counter just past the array starts at zero
+    HJ_CUDA(c, cudaMemsetAsync(tasks, 0, ntasks * sizeof(PartTask) + 8, c->stream));
+    HJ_LAUNCH(c, "make_tasks", make_tasks_kernel, grid ? grid : 1, 256, 0, Rp, roff, Sp, soff, NP, slice,
+              (unsigned long long *)(tasks + ntasks), join, b1, b2, empty_key2(width, b1, b2), (int)tuple_bytes(width),
+              tasks);
     return HJ_OK;
 }
 

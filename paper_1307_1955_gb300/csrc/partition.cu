@@ -76,7 +76,7 @@ __global__ void __launch_bounds__(kScanThreads) scan_apply_kernel(const uint32_t
     }
 }
 
-static hj_status scan_u32_u64(hj_ctx *c, const uint32_t *in, uint64_t n, unsigned long long *out) {
+static hj_status scan_counts(hj_ctx *c, const uint32_t *in, uint64_t n, unsigned long long *out) {
     uint64_t nb = (n + kScanBlock - 1) / kScanBlock;
     if (nb == 0) nb = 1;
     DevBuf partial(c);
@@ -987,13 +987,13 @@ hj_status partition_pass(hj_ctx *c, int width, const void *in, uint64_t n_total,
 
     int g1 = (int)std::min<uint64_t>((nseg + 255) / 256, 4096);
     HJ_LAUNCH(c, "seg_chunks", seg_chunks_kernel, g1 ? g1 : 1, 256, 0, seg_off, nseg, chunk, nch);
-    HJ_TRY(scan_u32_u64(c, nch, nseg, cb));
+    HJ_TRY(scan_counts(c, nch, nseg, cb));
     size_t hsmem = P * 4;
     if (width == 4)
         HJ_LAUNCH(c, "partition_hist", hist_kernel<4>, (unsigned)max_chunks, kHistThreads, hsmem, in, n_total, seg_off, nseg, cb, chunk, shift, bits, pad, H, seg_ptrs);
     else
         HJ_LAUNCH(c, "partition_hist", hist_kernel<8>, (unsigned)max_chunks, kHistThreads, hsmem, in, n_total, seg_off, nseg, cb, chunk, shift, bits, pad, H, seg_ptrs);
-    HJ_TRY(scan_u32_u64(c, H, max_chunks * P, Hs));
+    HJ_TRY(scan_counts(c, H, max_chunks * P, Hs));
     {
         uint64_t n = nseg * P + 1;
         int g = (int)std::min<uint64_t>((n + 255) / 256, (uint64_t)num_sms(c) * 8);
