@@ -58,6 +58,12 @@ WORKLOADS = {
         kind="zipf", nr=1 << 22, ns=1 << 26, ranks=1 << 20, theta_r=0.75, theta_s=1.0, algo=2, width=8, mode=1,
         desc="skewed PHJ, |R|=2^22, |S|=2^26 (uint64 key, uint64 payload); R keys Zipf(0.75), S keys Zipf(1.0) "
              "over the same 2^20 distinct 64-bit keys; count and checksums (about 3.1e11 pairs, not materialised)"),
+    "sweep_16m": dict(
+        kind="sweep", nr=1 << 24, ns=1 << 24, dom=1 << 24, algo=0,
+        desc="the paper's sweeps on GB300: |S| = 2^24 with |R| = 2^16 .. 2^24 (R keys a permutation of 1..|R|, "
+             "S keys uniform over them: every S tuple matches once), and selectivity 12.5 / 50 / 100 % at "
+             "|R| = |S| = 2^24 (S keys uniform over [1, |R| / selectivity]); uint32 key/rid, pairs materialised, "
+             "each point autotuned; value = the 2^24 x 2^24 point at 100 %"),
     "shj_1m": dict(
         nr=1 << 20, ns=1 << 20, dom=1 << 20, algo=1,
         desc="SHJ, |R|=|S|=2^20 (uint32 key, uint32 rid); R keys a permutation of 1..2^20, S keys drawn "
@@ -725,7 +731,7 @@ def run_serve(args, wl, ws, rank, local):
                     if d > 0:
                         time.sleep(d)
                 R, S = reqs[order[i]]
-                ids[i] = srv.submit(R, S)
+                ids[i] = srv.submit(R, S, sync=False)  # inputs were synchronised before the run
                 posted[i].set()
 
         th = threading.Thread(target=client)
@@ -750,7 +756,7 @@ def run_serve(args, wl, ws, rank, local):
         # warm-up: the first requests of the stream
         for _ in range(args.warmup):
             for R, S in reqs[:min(K, 64)]:
-                srv.wait(srv.submit(R, S))[0].free()
+                srv.wait(srv.submit(R, S, sync=False))[0].free()
         sampler = ClockSampler(local)
         if not args.no_clocks:
             sampler.start()
@@ -809,6 +815,62 @@ def run_serve(args, wl, ws, rank, local):
         dist.destroy_process_group()
 
 
+def run_sweep(args, wl, ws, rank, local):
+    """Throughput of the join over the paper's size and selectivity sweeps (each
+    point autotuned, inputs resident, CUDA events around the timed joins)."""
+    import torch
+
+    import __graft_entry__
+
+    torch.cuda.set_device(local)
+    if rank == 0:
+        __graft_entry__.build()
+    from paper_1307_1955_gb300 import hj
+    from paper_1307_1955_gb300 import workload as W
+
+    dev = torch.device("cuda", local)
+    stream = torch.cuda.current_stream(dev)
+    ctx = hj.Context(local, stream=stream)
+    ns = wl["ns"]
+    points = [(1 << lg, ns, 1 << lg, "size") for lg in (16, 18, 20, 22, 24)]
+    points += [(wl["nr"], ns, int(wl["nr"] / sel), f"selectivity {sel:g}") for sel in (0.125, 0.5)]
+    out, launches = [], 0
+    steps = max(1, min(args.steps, 20))
+    for nr, nsp, dom, kind in points:
+        R, S = W.unique_and_uniform(nr, nsp, dom, W.DEFAULT_SEED + rank, dev, ids=(6, nr, dom))
+        plan = hj.hj_tune(ctx, R, S)
+        for _ in range(args.warmup):
+            hj.hj_join(ctx, R, S).free()
+        torch.cuda.synchronize()
+        l0 = hj.launch_count(ctx)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(steps):
+            res = hj.hj_join(ctx, R, S)
+            m = res.count
+            res.free()
+        e1.record(stream)
+        torch.cuda.synchronize()
+        launches += hj.launch_count(ctx) - l0
+        ms = e0.elapsed_time(e1) / steps
+        out.append({"sweep": kind, "nr": nr, "ns": nsp, "selectivity": round(min(1.0, nr / dom), 4), "pairs": m,
+                    "algo": {1: "SHJ", 2: "PHJ"}[plan["algo"]], "radix_bits": plan["radix_bits"],
+                    "passes": plan["passes"], "ms": ms, "tuples_per_s": (nr + nsp) / (ms / 1000.0)})
+        del R, S
+    head = [p for p in out if p["nr"] == wl["nr"] and p["selectivity"] == 1.0][0]
+    if rank == 0:
+        line = {
+            "metric": METRIC, "value": head["tuples_per_s"], "unit": UNIT, "n_gpus": ws, "steps": steps,
+            "warmup": args.warmup, "ms_per_step": head["ms"], "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "u32", "data": "synthetic",
+            "config": {"workload": wl["desc"], "parallelism": f"replicas x{ws}",
+                       "l2": "the larger points exceed the 129 MB L2; no flush"},
+            "points": out, "roofline": None, "cpu_baseline": None, "e2e": None, "gpu_launches": launches,
+        }
+        print(json.dumps(line), flush=True)
+    ctx.close()
+
+
 def main():
     args = parse()
     ws, rank, local = dist_env()
@@ -817,6 +879,8 @@ def main():
         run_reference(args, wl, ws, rank)
     elif wl.get("kind") == "serve":
         run_serve(args, wl, ws, rank, local)
+    elif wl.get("kind") == "sweep":
+        run_sweep(args, wl, ws, rank, local)
     elif wl.get("kind") == "batch":
         run_batch(args, wl, ws, rank, local)
     else:

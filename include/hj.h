@@ -103,7 +103,11 @@ typedef struct hj_ctx hj_ctx;
 typedef struct hj_table hj_table;
 
 /* Create a context on `device`.  `cuda_stream` is a cudaStream_t to order work on
- * (NULL: the library creates its own non-blocking stream).  `hbm_budget_bytes`
+ * (NULL: the library creates its own non-blocking stream, which is NOT ordered
+ * after work on the legacy default stream -- pass cudaStreamLegacy to order the
+ * context's work with that stream, e.g. after kernels that produced the inputs
+ * there).  Any stream may be given, the legacy one included: the library captures
+ * CUDA graphs on private streams.  `hbm_budget_bytes`
  * caps the device memory the library holds at once (0: no cap).  Every later call
  * on the context must run with that device current or will make it current. */
 hj_status hj_create(hj_ctx **ctx, int device, void *cuda_stream, uint64_t hbm_budget_bytes);
@@ -280,8 +284,10 @@ hj_status hj_server_create(hj_server **srv, hj_ctx *ctx, const hj_server_opts *o
 
 /* Queue the join of R and S (device pointers, same width, 16-byte aligned, fewer
  * than 2^32 - 1 tuples each) in `mode` (HJ_COUNT, HJ_COUNT_CHECKSUM,
- * HJ_MATERIALIZE).  R and S must stay valid and unchanged until the request is
- * collected.  *req_id identifies it for hj_server_poll / hj_server_wait. */
+ * HJ_MATERIALIZE).  The workers run on streams of their own: R and S must be
+ * completely written when this is called (synchronise the stream that produced
+ * them), and must stay valid and unchanged until the request is collected.
+ * *req_id identifies it for hj_server_poll / hj_server_wait. */
 hj_status hj_server_submit(hj_server *srv, const hj_rel *R, const hj_rel *S, int32_t mode, uint64_t *req_id);
 
 /* HJ_E_PENDING while the request runs.  Once done, returns the request's own

@@ -283,14 +283,24 @@ extern "C" hj_status hj_join_batch(hj_ctx *c, int n, const hj_rel *Rs, const hj_
             return st;
         }
         if (graph) {
+            // The wave is captured on a private stream (the context's stream may be
+            // the legacy default stream, which cannot be captured) and the graph is
+            // launched on the context's stream, after the work already queued there.
             const bool prof = c->prof;
             c->prof = false;
             cudaGraph_t g = nullptr;
-            HJ_CUDA(c, cudaStreamBeginCapture(c->stream, cudaStreamCaptureModeThreadLocal));
-            st = launch_wave(c, W, slots.as<JoinSlot>(), agg, chk, w, stage);
-            cudaError_t e = cudaStreamEndCapture(c->stream, &g);
+            cudaStream_t orig = c->stream, cap = nullptr;
+            HJ_CUDA(c, cudaStreamCreateWithFlags(&cap, cudaStreamNonBlocking));
+            c->stream = cap;
+            cudaError_t e = cudaStreamBeginCapture(cap, cudaStreamCaptureModeThreadLocal);
+            if (e == cudaSuccess) {
+                st = launch_wave(c, W, slots.as<JoinSlot>(), agg, chk, w, stage);
+                e = cudaStreamEndCapture(cap, &g);
+            }
+            c->stream = orig;
+            cudaStreamDestroy(cap);
             c->prof = prof;
-            if (st == HJ_OK && e != cudaSuccess) st = cuda_err(c, e, "cudaStreamEndCapture");
+            if (st == HJ_OK && e != cudaSuccess) st = cuda_err(c, e, "wave capture");
             cudaGraphExec_t ge = nullptr;
             if (st == HJ_OK) {
                 e = cudaGraphInstantiate(&ge, g, 0);

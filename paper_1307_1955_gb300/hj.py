@@ -183,13 +183,29 @@ def _result(ctx, r: hj_result) -> Result:
                   int(r.width), int(r.algo), int(r.radix_bits), int(r.passes), r, ctx)
 
 
-class Context:
-    """An hj_ctx bound to a CUDA device and stream."""
+# cudaStreamLegacy: the legacy default stream, which torch uses as its default
+# stream (handle 0 on the torch side; NULL means "a stream of its own" to hj_create).
+_CUDA_STREAM_LEGACY = 1
 
-    def __init__(self, device: int = 0, stream: torch.cuda.Stream | None = None, budget: int = 0):
+
+def stream_handle(stream: torch.cuda.Stream) -> int:
+    """The cudaStream_t to give the library for a torch stream."""
+    return stream.cuda_stream or _CUDA_STREAM_LEGACY
+
+
+class Context:
+    """An hj_ctx bound to a CUDA device and stream.  By default the context orders
+    its work on torch's current stream of the device, so that it follows the
+    kernels that produced its inputs; pass `own_stream=True` for a separate stream
+    (the caller then synchronises its inputs first)."""
+
+    def __init__(self, device: int = 0, stream: torch.cuda.Stream | None = None, budget: int = 0,
+                 own_stream: bool = False):
         lib = load_library()
         h = ctypes.c_void_p()
-        s = stream.cuda_stream if stream is not None else None
+        if stream is None and not own_stream:
+            stream = torch.cuda.current_stream(device)
+        s = stream_handle(stream) if stream is not None else None
         st = lib.hj_create(ctypes.byref(h), device, s, budget)
         if st != HJ_OK:
             raise HJError(st, "hj_create failed")
@@ -372,8 +388,8 @@ def hj_join_static(R: torch.Tensor, S: torch.Tensor, pairs: torch.Tensor | None,
     chk = (ctypes.c_uint64 * 2)()
     ptr = pairs.data_ptr() if pairs is not None and pairs.numel() else None
     cap = pairs.shape[0] if pairs is not None else 0
-    st = load_library().hj_join_static(ctypes.byref(r), ctypes.byref(s), stream.cuda_stream if stream else None, ptr,
-                                       cap, ctypes.byref(cnt), chk)
+    st = load_library().hj_join_static(ctypes.byref(r), ctypes.byref(s), stream_handle(stream) if stream else None,
+                                       ptr, cap, ctypes.byref(cnt), chk)
     if st != HJ_OK:
         e = HJError(st, "hj_join_static failed")
         e.count = int(cnt.value)
@@ -461,7 +477,12 @@ class Server:
             msg = load_library().hj_server_last_error(self.handle)
             raise HJError(st, msg.decode() if msg else "")
 
-    def submit(self, R: torch.Tensor, S: torch.Tensor, mode: int = HJ_MATERIALIZE) -> int:
+    def submit(self, R: torch.Tensor, S: torch.Tensor, mode: int = HJ_MATERIALIZE, sync: bool = True) -> int:
+        """Queue a join.  The server's workers run on streams of their own, so R and S
+        must be complete: with sync (the default) torch's current stream is
+        synchronised first; pass sync=False for inputs known to be ready."""
+        if sync:
+            torch.cuda.current_stream(R.device).synchronize()
         r, s = rel_of(R), rel_of(S)
         rid = ctypes.c_uint64()
         self._check(load_library().hj_server_submit(self.handle, ctypes.byref(r), ctypes.byref(s), mode,

@@ -121,6 +121,18 @@ def test_phj_zipf_u64_count_full_size(hjm, ctx):
     assert cnt > 10 ** 11
 
 
+@pytest.mark.parametrize("algo", [1, 2])
+def test_join_is_ordered_after_the_kernels_that_made_its_inputs(hjm, algo):
+    # A default context orders its work on torch's current stream: a join queued
+    # right after the (asynchronous) generation of its inputs sees them complete.
+    # Every S key is an R key and R keys are unique, so the count is exactly |S|.
+    with hjm.Context(0) as c:
+        for _ in range(3):
+            R, S = W.unique_and_uniform(1 << 22, 1 << 24, 1 << 22, SEED, DEV, ids=(7, algo))
+            r = hjm.hj_join(c, R, S, algo=algo, mode=hjm.HJ_COUNT)
+            assert r.count == 1 << 24
+
+
 def test_phj_full_size_properties(hjm, ctx):
     # |R| = 2^24 unique keys, |S| = 2^28 keys uniform over [1, 2^25], the launch the
     # bench times (automatic plan).  Each S tuple whose key is <= 2^24 matches
