@@ -649,11 +649,10 @@ template <int W> struct ChunkSink {
         unsigned run = 0;
 #pragma unroll
         for (int i = 0; i < IT; ++i) {
-            if (cnt[i] == 1) {
-                const unsigned idx = run + __popc(m[i] & lt);
-                const unsigned long long pos = idx < room ? c0 + idx : nb + (idx - room);
-                if (safe || pos < oc.pcap) PairOut<W>::put(oc.pairs, pos, first[i], r[i]);
-            }
+            // positions computed by every lane, only the store is predicated
+            const unsigned idx = run + __popc(m[i] & lt);
+            const unsigned long long pos = idx < room ? c0 + idx : nb + (idx - room);
+            if (cnt[i] == 1 && (safe || pos < oc.pcap)) PairOut<W>::put(oc.pairs, pos, first[i], r[i]);
             run += __popc(m[i]);
         }
         if (tot > room) {
@@ -785,8 +784,9 @@ __device__ __forceinline__ void probe_item(const SoaTab<W> &tab, typename Tup<W>
 #pragma unroll
     for (uint32_t q = 0; q < G; ++q) m |= (uint32_t)(key[q] == k) << q;
     if (CHECK && !valid) m = 0;
-    T f = 0;
-    if (m) f = tab.ld1(home, 1, (uint32_t)(__ffs(m) - 1));
+    // the first match's rid, read without a branch (slot G - 1 when nothing matched)
+    const T fr = tab.ld1(home, 1, (uint32_t)(__ffs(m | (1u << (G - 1))) - 1));
+    T f = m ? fr : T(0);
     uint32_t c = __popc(m);
     if ((!CHECK || valid) && key[G - 1] != tab.empty && tab.overflowed(home)) {  // the run goes on (rare)
         const uint32_t nx = home + 1 == tab.nb ? 0 : home + 1;
