@@ -98,6 +98,12 @@ __global__ void seg_chunks_kernel(const uint64_t *seg_off, uint64_t nseg, uint64
     }
 }
 
+// chunk_base of a single segment: {0, ceil(len / chunk)} in one launch.
+__global__ void one_seg_chunks_kernel(const uint64_t *seg_off, uint64_t chunk, unsigned long long *cb) {
+    cb[0] = 0;
+    cb[1] = (seg_off[1] - seg_off[0] + chunk - 1) / chunk;
+}
+
 // Segment that owns global chunk g: the last s with chunk_base[s] <= g.
 __device__ __forceinline__ uint64_t seg_of_chunk(const unsigned long long *cb, uint64_t nseg, uint64_t g) {
     uint64_t lo = 0, hi = nseg;  // invariant: cb[lo] <= g < cb[hi]
@@ -986,8 +992,12 @@ hj_status partition_pass(hj_ctx *c, int width, const void *in, uint64_t n_total,
     unsigned long long *cb = b_cb.as<unsigned long long>(), *Hs = b_Hs.as<unsigned long long>();
 
     int g1 = (int)std::min<uint64_t>((nseg + 255) / 256, 4096);
-    HJ_LAUNCH(c, "seg_chunks", seg_chunks_kernel, g1 ? g1 : 1, 256, 0, seg_off, nseg, chunk, nch);
-    HJ_TRY(scan_counts(c, nch, nseg, cb));
+    if (nseg == 1) {
+        HJ_LAUNCH(c, "seg_chunks", one_seg_chunks_kernel, 1, 1, 0, seg_off, chunk, cb);
+    } else {
+        HJ_LAUNCH(c, "seg_chunks", seg_chunks_kernel, g1 ? g1 : 1, 256, 0, seg_off, nseg, chunk, nch);
+        HJ_TRY(scan_counts(c, nch, nseg, cb));
+    }
     size_t hsmem = P * 4;
     if (width == 4)
         HJ_LAUNCH(c, "partition_hist", hist_kernel<4>, (unsigned)max_chunks, kHistThreads, hsmem, in, n_total, seg_off, nseg, cb, chunk, shift, bits, pad, H, seg_ptrs);
