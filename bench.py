@@ -221,18 +221,44 @@ def traffic_record(kernel: str, workload: str):
 # ------------------------------------------------------------------- CPU oracle
 
 
+class OneCore:
+    """Run the single-threaded oracle pinned to one host core (Linux affinity),
+    restoring the process's affinity afterwards; records the host's core count."""
+
+    def __enter__(self):
+        self.saved = None
+        try:
+            self.saved = os.sched_getaffinity(0)
+            os.sched_setaffinity(0, {max(self.saved)})
+        except (AttributeError, OSError):
+            pass
+        return self
+
+    def __exit__(self, *exc):
+        if self.saved:
+            try:
+                os.sched_setaffinity(0, self.saved)
+            except OSError:
+                pass
+
+
+def host_cores() -> int:
+    return os.cpu_count() or 0
+
+
 def oracle_rate(R_np, S_np, mode=2):
     """Run the oracle's hash join once (pairs materialised), or its per-key
     aggregation in the count modes; return (tuples, seconds, pairs)."""
     import oracle
 
-    t0 = time.perf_counter()
-    if mode == 2:
-        rr, ss = oracle.hash_join(R_np, S_np, cap_hint=len(S_np))
-        m = len(rr)
-    else:
-        m = oracle.join_aggregate(R_np, S_np)[0]
-    dt = time.perf_counter() - t0
+    with OneCore():
+        t0 = time.perf_counter()
+        if mode == 2:
+            rr, ss = oracle.hash_join(R_np, S_np, cap_hint=len(S_np))
+            m = len(rr)
+        else:
+            m = oracle.join_aggregate(R_np, S_np)[0]
+        dt = time.perf_counter() - t0
     return len(R_np) + len(S_np), dt, m
 
 
@@ -260,7 +286,7 @@ def cpu_sample(wl, R, S, target_s: float):
     Ss = W.to_numpy_u(S[:want])
     n, dt, m = oracle_rate(Rn, Ss, mode)
     what = f"{m} pairs materialised" if mode == 2 else f"{m} pairs counted by per-key aggregation"
-    return {"value": n / dt, "unit": UNIT, "cores": 1, "kind": "oracle",
+    return {"value": n / dt, "unit": UNIT, "cores": 1, "host_cores": host_cores(), "kind": "oracle",
             "sample": f"all |R|={len(Rn)} tuples, first {want} of |S|={len(S)} tuples "
                       f"({what}), single-threaded C oracle, {dt:.1f} s"}
 
@@ -310,7 +336,7 @@ def run_reference(args, wl, ws, rank):
         "warmup": args.warmup, "ms_per_step": 1000 * dt / max(args.steps, 1), "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "u32", "data": "synthetic",
         "config": {"workload": wl["desc"], "sample_scale": f"1/{scale} of |R| and |S|"},
-        "cpu_baseline": {"value": value, "unit": UNIT, "kind": "oracle", "cores": 1,
+        "cpu_baseline": {"value": value, "unit": UNIT, "kind": "oracle", "cores": 1, "host_cores": host_cores(),
                          "sample": f"|R|={len(Rn)}, |S|={len(Sn)} (the workload scaled by 1/{scale}), "
                                    f"single-threaded C oracle hash join, pairs materialised"},
         "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
@@ -344,7 +370,7 @@ def run_reference_prefix(args, wl, ws, per_step):
         "warmup": args.warmup, "ms_per_step": 1000 * dt / max(args.steps, 1), "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "u32" if wl.get("width", 4) == 4 else "u64",
         "data": "synthetic", "config": {"workload": wl["desc"], "sample": sample},
-        "cpu_baseline": {"value": value, "unit": UNIT, "kind": "oracle", "cores": 1, "sample": sample},
+        "cpu_baseline": {"value": value, "unit": UNIT, "kind": "oracle", "cores": 1, "host_cores": host_cores(), "sample": sample},
         "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
     print(json.dumps(line), flush=True)
@@ -383,7 +409,7 @@ def run_reference_batch(args, wl, ws, per_step):
         "warmup": args.warmup, "ms_per_step": 1000 * dt / max(args.steps, 1), "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "u32", "data": "synthetic",
         "config": {"workload": wl["desc"], "sample": f"the first {len(sample)} of {len(specs)} joins"},
-        "cpu_baseline": {"value": value, "unit": UNIT, "kind": "oracle", "cores": 1,
+        "cpu_baseline": {"value": value, "unit": UNIT, "kind": "oracle", "cores": 1, "host_cores": host_cores(),
                          "sample": f"the first {len(sample)} joins of the batch ({tuples} tuples), "
                                    f"single-threaded C oracle hash join, pairs materialised"},
         "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
@@ -548,7 +574,7 @@ def batch_cpu_sample(Rs, Ss, target_s: float):
         dt += t
         pairs += m
         k += 1
-    return {"value": tuples / dt, "unit": UNIT, "cores": 1, "kind": "oracle",
+    return {"value": tuples / dt, "unit": UNIT, "cores": 1, "host_cores": host_cores(), "kind": "oracle",
             "sample": f"the first {k} of {len(Rs)} joins ({tuples} tuples, {pairs} pairs materialised), "
                       f"single-threaded C oracle, {dt:.1f} s"}
 
@@ -785,6 +811,10 @@ def run_serve(args, wl, ws, rank, local):
     peak, peak_kind = measured_peak()
     pairs = sum(want[j] for j in order)
     alg = 3 * 8 * total + 8 * pairs
+    cpu = None
+    if rank == 0 and not args.no_cpu_baseline:
+        # the oracle over the stream's requests in order, about 12 s of work
+        cpu = batch_cpu_sample([reqs[j][0] for j in order[:K]], [reqs[j][1] for j in order[:K]], 12.0)
     if rank == 0:
         line = {
             "metric": METRIC, "value": sat, "unit": UNIT, "n_gpus": ws, "steps": 1, "warmup": args.warmup,
@@ -806,7 +836,7 @@ def run_serve(args, wl, ws, rank, local):
             "roofline": {"bound": "hbm", "kernel": "whole join (all kernels)", "achieved": alg / span / 1e9,
                          "peak": peak, "unit": "GB/s", "frac": alg / span / 1e9 / peak, "peak_kind": peak_kind,
                          "traffic": None},
-            "cpu_baseline": None, "e2e": None, "gpu_launches": launches, "clocks": clocks,
+            "cpu_baseline": cpu, "e2e": None, "gpu_launches": launches, "clocks": clocks,
         }
         print(json.dumps(line), flush=True)
     del keep
