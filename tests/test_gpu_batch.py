@@ -103,3 +103,42 @@ def test_batch_oversize_partition_and_overflow(hjm, ctx):
         assert res[j].count == len(want), j
         assert np.array_equal(_sorted(res[j].pairs_numpy()), want), j
         res[j].free()
+
+
+def test_batch_full_size_counts_and_sampled_pairs(hjm, ctx):
+    # The 4096-join batch at full size (|R| log-uniform in [2^10, 2^22], |S| = 4 |R|, about
+    # 1.1e10 tuples), in the launch configuration the bench times (pairs materialised,
+    # one CUDA graph per wave).  R keys are exactly 1..|R|, so an S tuple matches once
+    # if its key is at most |R| and never otherwise: every join's count is checked
+    # against that property, and sampled joins' pairs against the oracle.
+    specs = W.batched_specs(4096, W.DEFAULT_SEED)
+    R_all, S_all, rs, ss = W.batched_relations(specs, W.DEFAULT_SEED, DEV)
+    n = len(specs)
+    Rs = [R_all[rs[j]:rs[j] + sp.n_r] for j, sp in enumerate(specs)]
+    Ss = [S_all[ss[j]:ss[j] + sp.n_s] for j, sp in enumerate(specs)]
+    # expected counts, chunk by chunk over S_all (padding rows between joins are skipped)
+    starts = torch.tensor(ss, dtype=torch.int64, device=DEV)
+    ends = starts + torch.tensor([sp.n_s for sp in specs], dtype=torch.int64, device=DEV)
+    nr = torch.tensor([sp.n_r for sp in specs], dtype=torch.int64, device=DEV)
+    want = torch.zeros(n, dtype=torch.int64, device=DEV)
+    step = 1 << 27
+    for a in range(0, S_all.shape[0], step):
+        row = torch.arange(a, min(a + step, S_all.shape[0]), dtype=torch.int64, device=DEV)
+        j = torch.searchsorted(starts, row, right=True) - 1
+        live = row < ends[j]
+        key = S_all[a:a + len(row), 0].to(torch.int64) & 0xFFFFFFFF
+        want.index_add_(0, j, (live & (key <= nr[j])).to(torch.int64))
+    want = want.cpu().tolist()
+    ra, sa = hjm.rel_array(Rs), hjm.rel_array(Ss)
+    outs = hjm.hj_join_batch(ctx, ra, sa, graph=True, raw=True)
+    try:
+        for j in range(n):
+            assert outs[j].count == want[j], j
+        order = sorted(range(n), key=lambda j: specs[j].n_r)
+        for j in order[:4] + order[n // 2:n // 2 + 1] + order[-1:]:
+            res = hjm._result(ctx, outs[j])
+            got = res.pairs_numpy().astype(np.uint64)
+            r, s = W.to_numpy_u(Rs[j]), W.to_numpy_u(Ss[j])
+            assert np.array_equal(_sorted(got), oracle.sorted_pairs(*oracle.hash_join(r, s))), j
+    finally:
+        hjm.hj_results_free(ctx, outs, n)
