@@ -206,6 +206,24 @@ hj_status hj_tune_clear(hj_ctx *ctx);
 hj_status hj_join_host(hj_ctx *ctx, const hj_rel *R_host, const hj_rel *S_host, const hj_opts *opts,
                        void *pairs_host, uint64_t pairs_host_cap, hj_result *out);
 
+/* Join of relations in HOST memory that need not fit the device -- the paper's
+ * larger-than-buffer join (App. A): each relation is streamed to the device in
+ * chunks, split there on hash bits [20, 20 + bt) (bt <= 8, chosen so that every
+ * partition pair of a uniform split fits) and copied back into page-locked host
+ * partitions; then every partition pair is gathered onto the device and joined by
+ * the PHJ (whose digits use hash bits below 20), its pairs copied into
+ * `pairs_host`.  A pair whose S side is too large next to its R partition (skew)
+ * is joined in S groups.  The device memory used stays within `device_bytes` (0:
+ * 40% of free memory); when everything fits at once this is hj_join_host.  `out`
+ * receives count and checksums (out->radix_bits = bt, out->pairs = NULL); the
+ * pairs land in `pairs_host` (room for pairs_host_cap pairs; HJ_E_OVERFLOW with
+ * the full count if too small).  HJ_E_INVALID if device_bytes is below twice
+ * the fixed workspace of one join (64 MiB, plus 2^20 pairs when materialising);
+ * HJ_E_NOMEM if a partition of R with an S group of 2^16 tuples exceeds it.  Host
+ * memory: one page-locked copy of R and of S. */
+hj_status hj_join_host_large(hj_ctx *ctx, const hj_rel *R_host, const hj_rel *S_host, const hj_opts *opts,
+                             uint64_t device_bytes, void *pairs_host, uint64_t pairs_host_cap, hj_result *out);
+
 /* Release a result's pairs (no-op for the count modes) and zero the struct. */
 hj_status hj_result_free(hj_ctx *ctx, hj_result *res);
 

@@ -99,6 +99,7 @@ def load_library(path: str = LIB_PATH):
         "hj_result_free": (I32, [V, P(hj_result)]),
         "hj_join_host": (I32, [V, P(hj_rel), P(hj_rel), P(hj_opts), V, U64, P(hj_result)]),
         "hj_join_static": (I32, [P(hj_rel), P(hj_rel), V, V, U64, P(U64), P(U64)]),
+        "hj_join_host_large": (I32, [V, P(hj_rel), P(hj_rel), P(hj_opts), U64, V, U64, P(hj_result)]),
         "hj_join_batch": (I32, [V, ctypes.c_int, P(hj_rel), P(hj_rel), P(hj_opts), P(hj_result)]),
         "hj_sync": (I32, [V]),
         "hj_copy": (I32, [V, V, V, U64]),
@@ -340,6 +341,23 @@ def hj_join_host(ctx: Context, R: torch.Tensor, S: torch.Tensor, pairs_out: torc
     cap = pairs_out.shape[0] if pairs_out is not None else 0
     _check(ctx, load_library().hj_join_host(ctx.handle, ctypes.byref(r), ctypes.byref(s), ctypes.byref(o), ptr,
                                             cap, ctypes.byref(res)))
+    return _result(ctx, res)
+
+
+def hj_join_host_large(ctx: Context, R: torch.Tensor, S: torch.Tensor, pairs_out: torch.Tensor | None = None,
+                       device_bytes: int = 0, mode: int = HJ_MATERIALIZE, checksum: bool = False) -> Result:
+    """The join of CPU tensors that need not fit the device (partitioned through a
+    device budget of device_bytes); pairs land in `pairs_out` ((m, 2) CPU tensor of
+    R's dtype, m >= the pair count)."""
+    if R.device.type != "cpu" or S.device.type != "cpu":
+        raise ValueError("hj_join_host_large takes CPU tensors")
+    r, s = rel_of(R), rel_of(S)
+    o = _opts(mode=mode, checksum=checksum)
+    res = hj_result()
+    ptr = pairs_out.data_ptr() if pairs_out is not None and pairs_out.numel() else None
+    cap = pairs_out.shape[0] if pairs_out is not None else 0
+    _check(ctx, load_library().hj_join_host_large(ctx.handle, ctypes.byref(r), ctypes.byref(s), ctypes.byref(o),
+                                                  device_bytes, ptr, cap, ctypes.byref(res)))
     return _result(ctx, res)
 
 
