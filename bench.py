@@ -64,6 +64,11 @@ WORKLOADS = {
              "S keys uniform over them: every S tuple matches once), and selectivity 12.5 / 50 / 100 % at "
              "|R| = |S| = 2^24 (S keys uniform over [1, |R| / selectivity]); uint32 key/rid, pairs materialised, "
              "each point autotuned; value = the 2^24 x 2^24 point at 100 %"),
+    "outcore_16m_256m": dict(
+        kind="outcore", nr=1 << 24, ns=1 << 28, dom=1 << 25, algo=2, budget=1 << 30,
+        desc="larger-than-device join from host memory: the 2^24 x 2^28 PHJ workload (uint32 key/rid, ~50% "
+             "match) in page-locked host memory, joined through a 1 GiB device budget (chunked top-level split on "
+             "the device, host partitions, partition pairs joined on the device), pairs copied to host memory"),
     "shj_1m": dict(
         nr=1 << 20, ns=1 << 20, dom=1 << 20, algo=1,
         desc="SHJ, |R|=|S|=2^20 (uint32 key, uint32 rid); R keys a permutation of 1..2^20, S keys drawn "
@@ -901,6 +906,59 @@ def run_sweep(args, wl, ws, rank, local):
     ctx.close()
 
 
+def run_outcore(args, wl, ws, rank, local):
+    """hj_join_host_large on pinned host relations with a device budget far below
+    their size; the whole call (copies both ways, partitioning, joins) is timed."""
+    import torch
+
+    import __graft_entry__
+
+    torch.cuda.set_device(local)
+    if rank == 0:
+        __graft_entry__.build()
+    from paper_1307_1955_gb300 import hj
+    from paper_1307_1955_gb300 import workload as W
+
+    dev = torch.device("cuda", local)
+    R, S = make_inputs(wl, rank, dev)
+    Rh, Sh = R.cpu().pin_memory(), S.cpu().pin_memory()
+    del R, S
+    ctx = hj.Context(local)
+    out = torch.empty((wl["ns"] + (1 << 20), 2), dtype=torch.int32).pin_memory()
+    for _ in range(args.warmup):
+        res = hj.hj_join_host_large(ctx, Rh, Sh, out, device_bytes=wl["budget"])
+    steps = max(1, min(args.steps, 5))
+    l0 = hj.launch_count(ctx)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for _ in range(steps):
+        res = hj.hj_join_host_large(ctx, Rh, Sh, out, device_bytes=wl["budget"])
+    torch.cuda.synchronize()
+    dt = ranks_max(time.perf_counter() - t0, ws, dev)
+    value = weak_value(wl["nr"] + wl["ns"], steps, ws, dt * 1000.0)
+    cpu = None
+    if rank == 0 and not args.no_cpu_baseline:
+        cpu = cpu_sample(wl, Rh, Sh, target_s=12.0)
+    if rank == 0:
+        tb = 8
+        line = {
+            "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": steps, "warmup": args.warmup,
+            "ms_per_step": dt * 1000.0 / steps, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": "u32", "data": "synthetic",
+            "config": {"workload": wl["desc"], "device_bytes": wl["budget"], "top_bits": res.radix_bits,
+                       "pairs_per_step": res.count, "parallelism": f"replicas x{ws}",
+                       "l2": "host-resident inputs of 2.28 GB; no flush"},
+            "host_traffic_per_step": {"h2d_bytes": 2 * tb * (wl["nr"] + wl["ns"]),
+                                      "d2h_bytes": tb * (wl["nr"] + wl["ns"]) + tb * res.count},
+            "roofline": None, "cpu_baseline": cpu,
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 2 * tb * (wl["nr"] + wl["ns"]),
+                    "d2h_bytes_per_step": tb * (wl["nr"] + wl["ns"]) + tb * res.count, "api": "hj_join_host_large"},
+            "gpu_launches": hj.launch_count(ctx) - l0,
+        }
+        print(json.dumps(line), flush=True)
+    ctx.close()
+
+
 def main():
     args = parse()
     ws, rank, local = dist_env()
@@ -911,6 +969,8 @@ def main():
         run_serve(args, wl, ws, rank, local)
     elif wl.get("kind") == "sweep":
         run_sweep(args, wl, ws, rank, local)
+    elif wl.get("kind") == "outcore":
+        run_outcore(args, wl, ws, rank, local)
     elif wl.get("kind") == "batch":
         run_batch(args, wl, ws, rank, local)
     else:

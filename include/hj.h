@@ -220,7 +220,8 @@ hj_status hj_join_host(hj_ctx *ctx, const hj_rel *R_host, const hj_rel *S_host, 
  * the full count if too small).  HJ_E_INVALID if device_bytes is below twice
  * the fixed workspace of one join (64 MiB, plus 2^20 pairs when materialising);
  * HJ_E_NOMEM if a partition of R with an S group of 2^16 tuples exceeds it.  Host
- * memory: one page-locked copy of R and of S. */
+ * memory: one page-locked copy of R and of S, kept by the context for later calls
+ * (released by hj_destroy). */
 hj_status hj_join_host_large(hj_ctx *ctx, const hj_rel *R_host, const hj_rel *S_host, const hj_opts *opts,
                              uint64_t device_bytes, void *pairs_host, uint64_t pairs_host_cap, hj_result *out);
 

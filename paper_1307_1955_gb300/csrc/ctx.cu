@@ -223,6 +223,8 @@ hj_status hj_destroy(hj_ctx *c) {
     for (auto e : c->spare_events) cudaEventDestroy(e);
     if (c->d_ctr) cudaFree(c->d_ctr);
     if (c->h_ctr) cudaFreeHost(c->h_ctr);
+    for (void *hb : c->host_buf)
+        if (hb) cudaFreeHost(hb);
     if (c->pool && c->own_pool) cudaMemPoolDestroy(c->pool);
     if (c->own_stream) cudaStreamDestroy(c->stream);
     delete c;

@@ -66,6 +66,9 @@ struct hj_ctx {
     hj::CostModel model;
     bool model_ready = false;
     std::map<uint64_t, hj::TunedPlan> tuned;
+    // page-locked host buffers kept for hj_join_host_large (R side, S side)
+    void *host_buf[2] = {nullptr, nullptr};
+    uint64_t host_cap[2] = {0, 0};
     // test hooks (host-side fault injection)
     int64_t fail_alloc_after = -1;  // fail the N-th allocation from now (0 = next)
 };

@@ -45,11 +45,8 @@ struct HostPart {
     // one relation split into 2^bt partitions, chunk by chunk
     std::vector<uint64_t> chunk_row;               // first row of chunk c in `rows`
     std::vector<std::vector<uint64_t>> off;        // off[c][p]: offsets inside chunk c (2^bt + 1)
-    void *rows = nullptr;                          // page-locked, the partitioned chunks back to back
+    void *rows = nullptr;                          // page-locked (the context's), partitioned chunks back to back
     uint64_t n = 0;
-    ~HostPart() {
-        if (rows) cudaFreeHost(rows);
-    }
     uint64_t part_rows(uint32_t p) const {
         uint64_t t = 0;
         for (size_t c = 0; c < off.size(); ++c) t += off[c][p + 1] - off[c][p];
@@ -59,11 +56,19 @@ struct HostPart {
 
 // Stream `in` (host) through the device in chunks of at most `chunk` tuples and
 // split it on bits [kTopShift, kTopShift + bt).
-hj_status split_host(hj_ctx *c, const hj_rel *in, int bt, uint64_t chunk, HostPart &hp) {
+hj_status split_host(hj_ctx *c, const hj_rel *in, int bt, uint64_t chunk, int side, HostPart &hp) {
     const uint64_t tb = tuple_bytes(in->width), P = 1ull << bt;
     hp.n = in->n;
     if (in->n == 0) return HJ_OK;
-    HJ_CUDA(c, cudaMallocHost(&hp.rows, in->n * tb));
+    // the context keeps one page-locked buffer per side, grown when too small
+    if (c->host_cap[side] < in->n * tb) {
+        if (c->host_buf[side]) cudaFreeHost(c->host_buf[side]);
+        c->host_buf[side] = nullptr;
+        c->host_cap[side] = 0;
+        HJ_CUDA(c, cudaMallocHost(&c->host_buf[side], in->n * tb));
+        c->host_cap[side] = in->n * tb;
+    }
+    hp.rows = c->host_buf[side];
     DevBuf d_in(c), d_out(c), d_off(c), d_seg(c);
     const uint64_t out_rows = partition_out_rows(c, in->width, chunk, 1, bt, 0);
     HJ_TRY(d_in.alloc(chunk * tb + 64));
@@ -139,8 +144,8 @@ extern "C" hj_status hj_join_host_large(hj_ctx *c, const hj_rel *Rh, const hj_re
     while (bt < kTopMaxBits && 3 * join_bytes(Rh->n >> bt, Sh->n >> bt, tb, mat) / 2 > device_bytes) ++bt;
     const uint64_t chunk = std::max<uint64_t>(1ull << 16, device_bytes / (3 * tb) / 1024 * 1024);
     HostPart hr, hs;
-    HJ_TRY(split_host(c, Rh, bt, chunk, hr));
-    HJ_TRY(split_host(c, Sh, bt, chunk, hs));
+    HJ_TRY(split_host(c, Rh, bt, chunk, 0, hr));
+    HJ_TRY(split_host(c, Sh, bt, chunk, 1, hs));
     // join every partition pair (PHJ: its digits use hash bits below kTopShift)
     hj_opts oj = o;
     oj.algo = HJ_ALGO_PHJ;
