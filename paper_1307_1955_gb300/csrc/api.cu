@@ -1,6 +1,7 @@
 // api.cu -- the C ABI of include/hj.h: argument checks, plan choice, and the
 // SHJ / PHJ drivers that sequence the kernels of join.cu and partition.cu.
 #include <algorithm>
+#include <memory>
 #include <cmath>
 #include <vector>
 
@@ -267,6 +268,187 @@ hj_status join_phj(hj_ctx *c, const hj_rel *R, const hj_rel *S, const hj_opts &o
     return HJ_OK;
 }
 
+
+// ------------------------------------------------------- pipelined host join
+// hj_join_host for a large S: R is copied and partitioned once; S travels in
+// chunks through two device buffers, and each chunk is partitioned and joined
+// against the partitioned R while the next chunk is copied in (copy stream) and
+// the previous chunk's pairs are copied out (output stream):
+//
+//   copy stream   H2D(0)  H2D(1)        H2D(2)        ...
+//   ctx stream            join(0)       join(1)       join(2)
+//   out stream                          D2H(0)        D2H(1)
+//
+// A chunk whose pairs overflow its buffer, or that needed the global-table
+// fallback, is joined again on its own afterwards.
+constexpr uint64_t kHostChunk = 1ull << 24;  // S rows per chunk
+
+struct PipeSet {
+    explicit PipeSet(hj_ctx *c, int w) : sink(c, w), dS(c) {}
+    PairSink sink;
+    DevBuf dS;
+    hj_counters *h = nullptr;  // page-locked copy of the chunk's counters
+    cudaEvent_t arrived = nullptr, computed = nullptr, drained = nullptr;
+    uint64_t chunk = ~0ull, n = 0;
+    bool taken = false;  // the chunk's counters were read (and its pairs sent home or queued for a rerun)
+};
+
+hj_status join_host_pipelined(hj_ctx *c, const hj_rel *Rh, const hj_rel *Sh, const hj_opts &o, int bits,
+                              void *pairs_host, uint64_t pairs_host_cap, hj_result *res) {
+    const int W = Rh->width;
+    const uint64_t tb = tuple_bytes(W), NP = 1ull << bits;
+    const bool mat = o.mode == HJ_MATERIALIZE;
+    cudaStream_t &cs = c->pipe_in, &os = c->pipe_out;
+    std::vector<std::unique_ptr<PipeSet>> sets;
+    std::vector<uint64_t> redo;
+    uint64_t count = 0, c0 = 0, c1 = 0, written = 0;
+    hj_status st = HJ_OK;
+    DevBuf dR(c), Rp(c), roff(c);
+    uint64_t r_rows = 0;
+    // streams, events and counter copies are the context's, kept across calls
+    auto cleanup = [&]() {
+        if (cs) cudaStreamSynchronize(cs);
+        if (os) cudaStreamSynchronize(os);
+        cudaStreamSynchronize(c->stream);
+        sets.clear();
+    };
+    // take a finished chunk: counters, then its pairs to the host (output stream)
+    auto drain = [&](PipeSet &ps) -> hj_status {
+        HJ_CUDA(c, cudaEventSynchronize(ps.computed));
+        ps.taken = true;
+        const hj_counters &h = *ps.h;
+        if (h.status & (kStatusTimeout | kStatusBadInput | kStatusRecords | kStatusCompact | kStatusTableFull))
+            return set_err(c, HJ_E_CUDA, "chunk %llu: kernel status %llu", (unsigned long long)ps.chunk,
+                           (unsigned long long)h.status);
+        if (h.n_oversize || (mat && (h.cursor > ps.sink.pcap || h.count > ps.sink.pcap))) {
+            redo.push_back(ps.chunk);  // joined again on its own below
+            return HJ_OK;
+        }
+        count += h.count;
+        c0 += h.c0;
+        c1 += h.c1;
+        if (mat && h.count) {
+            const uint64_t n = written < pairs_host_cap ? std::min<uint64_t>(h.count, pairs_host_cap - written) : 0;
+            HJ_CUDA(c, cudaStreamWaitEvent(os, ps.computed, 0));
+            if (n && pairs_host)
+                HJ_CUDA(c, cudaMemcpyAsync((char *)pairs_host + written * tb, ps.sink.pairs.p, n * tb,
+                                           cudaMemcpyDeviceToHost, os));
+            written += n;
+        }
+        HJ_CUDA(c, cudaEventRecord(ps.drained, os));
+        return HJ_OK;
+    };
+    auto body = [&]() -> hj_status {
+        if (!cs) HJ_CUDA(c, cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking));
+        if (!os) HJ_CUDA(c, cudaStreamCreateWithFlags(&os, cudaStreamNonBlocking));
+        if (!c->pipe_h) HJ_CUDA(c, cudaMallocHost(&c->pipe_h, 2 * sizeof(hj_counters)));
+        for (int i = 0; i < 2; ++i) {
+            for (cudaEvent_t &e : c->pipe_ev[i])
+                if (!e) HJ_CUDA(c, cudaEventCreateWithFlags(&e, cudaEventDisableTiming));
+            // a fresh call must not wait on the last call's events: record them here
+            for (cudaEvent_t e : c->pipe_ev[i]) HJ_CUDA(c, cudaEventRecord(e, c->stream));
+            sets.push_back(std::make_unique<PipeSet>(c, W));
+            PipeSet &ps = *sets.back();
+            ps.arrived = c->pipe_ev[i][0];
+            ps.computed = c->pipe_ev[i][1];
+            ps.drained = c->pipe_ev[i][2];
+            ps.h = (hj_counters *)c->pipe_h + i;
+            HJ_TRY(ps.dS.alloc(kHostChunk * tb + 64));
+        }
+        // R: copied and partitioned once
+        HJ_TRY(dR.alloc(Rh->n * tb + 64));
+        HJ_TRY(copy_wide(c, dR.p, Rh->tuples, Rh->n * tb, cudaMemcpyHostToDevice));
+        hj_rel R = *Rh;
+        R.tuples = dR.p;
+        HJ_TRY(partition_rel(c, &R, bits, 0, 1, Rp, roff, &r_rows));
+        const uint64_t nchunks = (Sh->n + kHostChunk - 1) / kHostChunk;
+        const uint64_t warps = partition_join_warps(c);
+        for (uint64_t k = 0; k < nchunks; ++k) {
+            PipeSet &ps = *sets[k & 1];
+            if (ps.chunk != ~0ull && !ps.taken) HJ_TRY(drain(ps));
+            const uint64_t r0 = k * kHostChunk, n = std::min(kHostChunk, Sh->n - r0);
+            // the set's S buffer is free once chunk k - 2's join is done
+            HJ_CUDA(c, cudaStreamWaitEvent(cs, ps.computed, 0));
+            HJ_CUDA(c, cudaMemcpyAsync(ps.dS.p, (const char *)Sh->tuples + r0 * tb, n * tb, cudaMemcpyHostToDevice,
+                                       cs));
+            HJ_CUDA(c, cudaEventRecord(ps.arrived, cs));
+            ps.chunk = k;
+            ps.n = n;
+            ps.taken = false;
+            // join of chunk k on the context's stream, after its copy and after the
+            // set's pairs of chunk k - 2 have left for the host
+            HJ_CUDA(c, cudaStreamWaitEvent(c->stream, ps.arrived, 0));
+            HJ_CUDA(c, cudaStreamWaitEvent(c->stream, ps.drained, 0));
+            hj_rel S{ps.dS.p, n, W, 0};
+            DevBuf Sp(c), soff(c), tasks(c), oversize(c), slot(c);
+            uint64_t s_rows = 0;
+            HJ_TRY(partition_rel(c, &S, bits, 0, 1, Sp, soff, &s_rows));
+            const uint64_t slice = task_slice_rows(W, n, NP), ntasks = max_tasks(NP, s_rows, slice);
+            HJ_TRY(oversize.alloc(ntasks * 4));
+            HJ_TRY(tasks.alloc(ntasks * sizeof(PartTask) + 8));
+            HJ_TRY(slot.alloc(sizeof(JoinSlot)));
+            HJ_TRY(make_tasks(c, Rp.p, roff.as<uint64_t>(), Sp.p, soff.as<uint64_t>(), NP, 0, bits, 0, W, slice,
+                              ntasks, tasks.as<PartTask>()));
+            if (mat) HJ_TRY(ps.sink.reset(n + warps * kChunkPairs));
+            RecArea ra{nullptr, nullptr, 0};
+            if (mat) HJ_TRY(ps.sink.new_area(warps, &ra));
+            HJ_TRY(zero_counters(c));
+            HJ_LAUNCH(c, "set_slot", set_slot_kernel, 1, 1, 0, slot.as<JoinSlot>(), mat ? ps.sink.pairs.p : nullptr,
+                      (unsigned long long)(mat ? ps.sink.pcap : 0), c->d_ctr);
+            HJ_TRY(partition_join(c, W, is_agg(o.mode), tasks.as<PartTask>(), ntasks, slot.as<JoinSlot>(),
+                                  (Rh->n + NP - 1) / NP, wants_checksum(o), oversize.as<uint32_t>(), ra, nullptr, 0));
+            if (mat) HJ_TRY(ps.sink.finalize_device(c->d_ctr));
+            HJ_CUDA(c, cudaMemcpyAsync(ps.h, c->d_ctr, sizeof(hj_counters), cudaMemcpyDeviceToHost, c->stream));
+            HJ_CUDA(c, cudaEventRecord(ps.computed, c->stream));
+            // the previous chunk is done or nearly: send its pairs home
+            if (k >= 1) HJ_TRY(drain(*sets[(k - 1) & 1]));
+        }
+        if (nchunks) HJ_TRY(drain(*sets[(nchunks - 1) & 1]));
+        HJ_CUDA(c, cudaStreamSynchronize(os));
+        // chunks that did not fit their pair buffer: on their own, exact capacity
+        for (uint64_t k : redo) {
+            const uint64_t r0 = k * kHostChunk, n = std::min(kHostChunk, Sh->n - r0);
+            DevBuf dS(c);
+            HJ_TRY(dS.alloc(n * tb + 64));
+            HJ_CUDA(c, cudaMemcpyAsync(dS.p, (const char *)Sh->tuples + r0 * tb, n * tb, cudaMemcpyHostToDevice,
+                                       c->stream));
+            hj_rel S{dS.p, n, W, 0};
+            hj_result r{};
+            HJ_TRY(join_phj(c, &R, &S, o, bits, 1, &r));
+            count += r.count;
+            c0 += r.checksum[0];
+            c1 += r.checksum[1];
+            if (mat && r.count) {
+                const uint64_t m = written < pairs_host_cap ? std::min<uint64_t>(r.count, pairs_host_cap - written) : 0;
+                if (m && pairs_host)
+                    HJ_CUDA(c, cudaMemcpyAsync((char *)pairs_host + written * tb, r.pairs, m * tb,
+                                               cudaMemcpyDeviceToHost, c->stream));
+                HJ_CUDA(c, cudaStreamSynchronize(c->stream));
+                written += m;
+            }
+            dfree(c, r.pairs);
+        }
+        return HJ_OK;
+    };
+    st = body();
+    cleanup();
+    if (st != HJ_OK) return st;
+    res->count = count;
+    res->checksum[0] = c0;
+    res->checksum[1] = c1;
+    res->width = W;
+    res->algo = HJ_ALGO_PHJ;
+    res->radix_bits = bits;
+    res->passes = 1;
+    res->pairs = nullptr;
+    res->pairs_cap = 0;
+    if (mat && count > pairs_host_cap)
+        return set_err(c, HJ_E_OVERFLOW, "%llu pairs do not fit in %llu", (unsigned long long)count,
+                       (unsigned long long)pairs_host_cap);
+    if (mat && count && !pairs_host) return set_err(c, HJ_E_INVALID, "pairs_host is NULL but the join produced pairs");
+    return HJ_OK;
+}
+
 }  // namespace
 
 extern "C" {
@@ -375,11 +557,40 @@ hj_status hj_join_host(hj_ctx *c, const hj_rel *Rh, const hj_rel *Sh, const hj_o
     if (Rh->width != Sh->width) return set_err(c, HJ_E_INVALID, "R and S widths differ");
     if ((Rh->n && !Rh->tuples) || (Sh->n && !Sh->tuples)) return set_err(c, HJ_E_INVALID, "NULL host tuples");
     const uint64_t tb = tuple_bytes(Rh->width);
+    {
+        // a large S: chunked, copies overlapping a one-pass PHJ
+        hj_opts o = opts ? *opts : default_opts();
+        int algo, bits, passes;
+        choose_plan(c, Rh->width, o.mode, Rh->n, Sh->n, o.algo, o.radix_bits, o.passes, &algo, &bits, &passes);
+        bool pipe = algo == HJ_ALGO_PHJ && passes == 1;
+        if (!pipe && o.algo == HJ_ALGO_AUTO && o.passes <= 0) {
+            // the in-memory plan is SHJ or two passes; the chunked join is bound by
+            // the host link, so a one-pass PHJ serves as well when R's partitions
+            // fit shared memory at some fan-out
+            if (!c->model_ready) {
+                c->model = cost_model_for(c->device);
+                c->model_ready = true;
+            }
+            const bool mat = o.mode == HJ_MATERIALIZE;
+            std::vector<PlanCand> pcs = plan_candidates(c->model, Rh->width, !mat, mat, Rh->n,
+                                                        std::min<uint64_t>(Sh->n, kHostChunk), HJ_ALGO_PHJ,
+                                                        o.radix_bits, 1);
+            if (!pcs.empty() && pcs[0].passes == 1) {
+                pipe = true;
+                bits = pcs[0].bits;
+            }
+        }
+        if (pipe && Sh->n >= 2 * kHostChunk && Rh->n < 0xFFFFFFFFull && o.mode >= HJ_COUNT &&
+            o.mode <= HJ_MATERIALIZE) {
+            *res = hj_result{};
+            return join_host_pipelined(c, Rh, Sh, o, bits, pairs_host, pairs_host_cap, res);
+        }
+    }
     DevBuf dR(c), dS(c);
     HJ_TRY(dR.alloc(Rh->n * tb + 64));
     HJ_TRY(dS.alloc(Sh->n * tb + 64));
-    if (Rh->n) HJ_CUDA(c, cudaMemcpyAsync(dR.p, Rh->tuples, Rh->n * tb, cudaMemcpyHostToDevice, c->stream));
-    if (Sh->n) HJ_CUDA(c, cudaMemcpyAsync(dS.p, Sh->tuples, Sh->n * tb, cudaMemcpyHostToDevice, c->stream));
+    if (Rh->n) HJ_TRY(copy_wide(c, dR.p, Rh->tuples, Rh->n * tb, cudaMemcpyHostToDevice));
+    if (Sh->n) HJ_TRY(copy_wide(c, dS.p, Sh->tuples, Sh->n * tb, cudaMemcpyHostToDevice));
     hj_rel R = *Rh, S = *Sh;
     R.tuples = dR.p;
     S.tuples = dS.p;
@@ -391,7 +602,7 @@ hj_status hj_join_host(hj_ctx *c, const hj_rel *Rh, const hj_rel *Sh, const hj_o
     if (pairs.p && res->count) {
         if (!pairs_host) return set_err(c, HJ_E_INVALID, "pairs_host is NULL but the join produced pairs");
         uint64_t n = std::min(res->count, pairs_host_cap);
-        if (n) HJ_CUDA(c, cudaMemcpyAsync(pairs_host, pairs.p, n * tb, cudaMemcpyDeviceToHost, c->stream));
+        if (n) HJ_TRY(copy_wide(c, pairs_host, pairs.p, n * tb, cudaMemcpyDeviceToHost));
         HJ_CUDA(c, cudaStreamSynchronize(c->stream));
         if (n < res->count)
             return set_err(c, HJ_E_OVERFLOW, "%llu pairs do not fit in %llu", (unsigned long long)res->count,

@@ -136,6 +136,30 @@ hj_status allow_max_smem(hj_ctx *c, const void *func) {
     return HJ_OK;
 }
 
+hj_status copy_wide(hj_ctx *c, void *dst, const void *src, uint64_t bytes, cudaMemcpyKind kind) {
+    constexpr int K = hj_ctx::kCopyStreams;
+    if (bytes < (64ull << 20)) {
+        HJ_CUDA(c, cudaMemcpyAsync(dst, src, bytes, kind, c->stream));
+        return HJ_OK;
+    }
+    if (!c->cstream[0]) {
+        for (int i = 0; i < K; ++i) HJ_CUDA(c, cudaStreamCreateWithFlags(&c->cstream[i], cudaStreamNonBlocking));
+        for (int i = 0; i <= K; ++i) HJ_CUDA(c, cudaEventCreateWithFlags(&c->cev[i], cudaEventDisableTiming));
+    }
+    HJ_CUDA(c, cudaEventRecord(c->cev[K], c->stream));
+    const uint64_t piece = (bytes / K + 255) & ~uint64_t(255);
+    for (int i = 0; i < K; ++i) {
+        const uint64_t off = (uint64_t)i * piece;
+        if (off >= bytes) break;
+        const uint64_t len = bytes - off < piece ? bytes - off : piece;
+        HJ_CUDA(c, cudaStreamWaitEvent(c->cstream[i], c->cev[K], 0));
+        HJ_CUDA(c, cudaMemcpyAsync((char *)dst + off, (const char *)src + off, len, kind, c->cstream[i]));
+        HJ_CUDA(c, cudaEventRecord(c->cev[i], c->cstream[i]));
+        HJ_CUDA(c, cudaStreamWaitEvent(c->stream, c->cev[i], 0));
+    }
+    return HJ_OK;
+}
+
 int num_sms(hj_ctx *c) {
     int n = 0;
     cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, c->device);
@@ -225,6 +249,16 @@ hj_status hj_destroy(hj_ctx *c) {
     if (c->h_ctr) cudaFreeHost(c->h_ctr);
     for (void *hb : c->host_buf)
         if (hb) cudaFreeHost(hb);
+    if (c->pipe_in) cudaStreamDestroy(c->pipe_in);
+    if (c->pipe_out) cudaStreamDestroy(c->pipe_out);
+    for (auto &row : c->pipe_ev)
+        for (cudaEvent_t e : row)
+            if (e) cudaEventDestroy(e);
+    if (c->pipe_h) cudaFreeHost(c->pipe_h);
+    for (int i = 0; i < hj_ctx::kCopyStreams; ++i)
+        if (c->cstream[i]) cudaStreamDestroy(c->cstream[i]);
+    for (int i = 0; i <= hj_ctx::kCopyStreams; ++i)
+        if (c->cev[i]) cudaEventDestroy(c->cev[i]);
     if (c->pool && c->own_pool) cudaMemPoolDestroy(c->pool);
     if (c->own_stream) cudaStreamDestroy(c->stream);
     delete c;

@@ -66,6 +66,16 @@ struct hj_ctx {
     hj::CostModel model;
     bool model_ready = false;
     std::map<uint64_t, hj::TunedPlan> tuned;
+    // side streams and events that split large host<->device copies over several
+    // copy engines (created on first use)
+    static constexpr int kCopyStreams = 4;
+    cudaStream_t cstream[kCopyStreams] = {};
+    cudaEvent_t cev[kCopyStreams + 1] = {};
+    // pipelined host joins: copy-in and copy-out streams, per-buffer-set events
+    // and page-locked counter copies (created on first use)
+    cudaStream_t pipe_in = nullptr, pipe_out = nullptr;
+    cudaEvent_t pipe_ev[2][3] = {};
+    void *pipe_h = nullptr;
     // page-locked host buffers kept for hj_join_host_large (R side, S side)
     void *host_buf[2] = {nullptr, nullptr};
     uint64_t host_cap[2] = {0, 0};
@@ -103,6 +113,11 @@ int num_sms(hj_ctx *c);
 // Always the same value per function, so concurrent callers on several threads
 // (the server's workers) cannot undo each other's setting between set and launch.
 hj_status allow_max_smem(hj_ctx *c, const void *func);
+
+// cudaMemcpyAsync of a large host<->device range, ordered on the context's
+// stream, split into pieces copied concurrently on side streams (several copy
+// engines); small copies go straight to the context's stream.
+hj_status copy_wide(hj_ctx *c, void *dst, const void *src, uint64_t bytes, cudaMemcpyKind kind);
 
 // hj_create with an existing memory pool (not owned: hj_destroy leaves it alone).
 hj_status ctx_create(hj_ctx **out, int device, void *cuda_stream, uint64_t budget, cudaMemPool_t shared_pool);

@@ -856,6 +856,101 @@ __device__ __forceinline__ void probe_fast(const SoaTab<W> &tab, const typename 
     }
 }
 
+// Bytes per slot of a partition's shared-memory aggregate table: the key, the
+// number of build tuples with that key and, with checksums, the sum of A(rid) over
+// them.
+__host__ __device__ constexpr uint32_t agg_slot_bytes(int width, int chk) {
+    return (uint32_t)width + 4u + (chk ? 8u : 0u);
+}
+
+// Aggregate table of one partition in shared memory (Sec. 3.1's key list with each
+// rid list folded into a count and a sum): the bucket layout of SoaTab -- G keys
+// per 16-byte bucket, a key that hashes to another partition as the empty marker,
+// runs that move linearly over buckets with overflow bits -- but one slot per
+// distinct key, so a lookup finds at most one slot.  Regions: keys (cap x W
+// bytes), sums (cap x 8, with checksums only), counts (cap x 4).
+template <int W> struct AggSoa {
+    using T = typename Tup<W>::U;
+    static constexpr uint32_t G = 16 / W;
+    uint32_t nb;
+    T empty;
+    uint32_t *ovf;
+    T *keys;
+    unsigned long long *suma;  // null without checksums
+    uint32_t *cnt;
+
+    __device__ static AggSoa at(unsigned char *base, uint32_t cap, T empty, uint32_t *ovf, bool chk) {
+        AggSoa t;
+        t.nb = cap / G;
+        t.empty = empty;
+        t.ovf = ovf;
+        t.keys = (T *)base;
+        t.suma = chk ? (unsigned long long *)(base + (size_t)cap * W) : nullptr;
+        t.cnt = (uint32_t *)(base + (size_t)cap * (W + (chk ? 8 : 0)));
+        return t;
+    }
+    __device__ __forceinline__ bool overflowed(uint32_t b) const { return (ovf[b >> 5] >> (b & 31)) & 1u; }
+    __device__ __forceinline__ void ld(uint32_t b, T *v) const {
+        if constexpr (W == 4) {
+            const uint4 x = *(const uint4 *)(keys + b * G);
+            v[0] = x.x; v[1] = x.y; v[2] = x.z; v[3] = x.w;
+        } else {
+            const ulonglong2 x = *(const ulonglong2 *)(keys + b * G);
+            v[0] = x.x; v[1] = x.y;
+        }
+    }
+    // Add one build tuple of key k (a = A(rid), used with checksums).  The slot
+    // of k is the first slot of its run that holds k, else the first empty one,
+    // claimed by CAS: slots only ever go from empty to a key, so two inserts of
+    // the same key always meet in one slot.  False if every bucket is full.
+    __device__ __forceinline__ bool insert(T k, uint64_t a) const {
+        uint32_t b = part_bucket<W>(k, nb);
+        for (uint32_t it = 0; it < nb; ++it) {
+            volatile T *kb = keys + b * G;
+            // each failed CAS follows one more slot of the bucket being filled
+            for (uint32_t tries = 0; tries <= G; ++tries) {
+                int hit = -1, emp = -1;
+#pragma unroll
+                for (uint32_t q = 0; q < G; ++q) {
+                    const T x = kb[q];
+                    if (x == k && hit < 0) hit = (int)q;
+                    if (x == empty && emp < 0) emp = (int)q;
+                }
+                if (hit < 0 && emp >= 0) {
+                    const T old = cas_key<W>(keys + b * G + emp, empty, k);
+                    if (old != empty && old != k) continue;
+                    hit = emp;
+                }
+                if (hit < 0) break;  // full bucket without k
+                atomicAdd(&cnt[b * G + hit], 1u);
+                if (suma) atomicAdd(&suma[b * G + hit], (unsigned long long)a);
+                return true;
+            }
+            atomicOr(&ovf[b >> 5], 1u << (b & 31));
+            b = b + 1 == nb ? 0 : b + 1;
+        }
+        return false;
+    }
+    // Slot of key k from bucket b on (the run's continuation), or ~0u.
+    __device__ __forceinline__ uint32_t find_from(T k, uint32_t b) const {
+        for (uint32_t it = 0; it < nb; ++it) {
+            T key[G];
+            ld(b, key);
+            uint32_t m = 0;
+            bool e = false;
+#pragma unroll
+            for (uint32_t q = 0; q < G; ++q) {
+                m |= (uint32_t)(key[q] == k) << q;
+                e |= key[q] == empty;
+            }
+            if (m) return b * G + (uint32_t)(__ffs(m) - 1);
+            if (e || !overflowed(b)) return ~0u;
+            b = b + 1 == nb ? 0 : b + 1;
+        }
+        return ~0u;
+    }
+};
+
 template <int W, bool AGG, int NT, class Sink, bool FAST>
 __global__ void __launch_bounds__(NT, 2048 / NT / 2) partition_join_kernel(
     const PartTask *tasks, uint64_t ntasks, const JoinSlot *slots, hj_counters *work, uint32_t cap_max, RecArea ra,
@@ -904,7 +999,9 @@ __global__ void __launch_bounds__(NT, 2048 / NT / 2) partition_join_kernel(
         uint32_t cap = 0;
         if (work_p) {
             if (AGG) {
-                const uint64_t want = 2 * nr + 32;
+                // about three slots per build row, whole buckets; with duplicate
+                // keys fewer slots than rows may do, so no early fallback
+                const uint64_t want = (3 * nr + 127) / 128 * 128;
                 cap = want < cap_max ? (uint32_t)want : cap_max;
             } else {
                 // about three slots per build row (load factor 1/3), whole buckets
@@ -916,22 +1013,20 @@ __global__ void __launch_bounds__(NT, 2048 / NT / 2) partition_join_kernel(
                 }
             }
         }
-        uint32_t *ovf = (uint32_t *)(smem + (size_t)cap_max * (AGG ? sizeof(AggSlot<W>) : 2 * W));
+        uint32_t *ovf = (uint32_t *)(smem + (size_t)cap_max * (AGG ? agg_slot_bytes(W, chk) : 2 * W));
         const T top = Tup<W>::kAllOnes;
         const T empty = pf.keep(hashw<W>(top)) ? (T)tk.ek1 : top;
         const SoaTab<W> tab{cap / G, empty, ovf, (const T *)smem, (const T *)smem + cap};
+        const AggSoa<W> at = AggSoa<W>::at(smem, cap, empty, ovf, chk != 0);
         if (work_p) {
+            T *kv = (T *)smem;  // key region: cap keys; the rid (or sum and count) regions follow
+            for (uint32_t i = threadIdx.x; i < cap; i += blockDim.x) kv[i] = empty;
+            for (uint32_t i = threadIdx.x; i < (cap / G + 31) / 32; i += blockDim.x) ovf[i] = 0;
             if (AGG) {
-                AggSlot<W> *sl = (AggSlot<W> *)smem;
                 for (uint32_t i = threadIdx.x; i < cap; i += blockDim.x) {
-                    sl[i].key = Tup<W>::kAllOnes;
-                    sl[i].cnt = 0;
-                    sl[i].suma = 0;
+                    at.cnt[i] = 0;
+                    if (chk) at.suma[i] = 0;
                 }
-            } else {
-                T *kv = (T *)smem;  // key region: cap keys; the rid region follows
-                for (uint32_t i = threadIdx.x; i < cap; i += blockDim.x) kv[i] = empty;
-                for (uint32_t i = threadIdx.x; i < (cap / G + 31) / 32; i += blockDim.x) ovf[i] = 0;
             }
             if (threadIdx.x == 0) {
                 side.n_allones = side.agg_cnt = side.agg_suma = side.full = 0;
@@ -953,7 +1048,7 @@ __global__ void __launch_bounds__(NT, 2048 / NT / 2) partition_join_kernel(
                     if (!pf.keep(h)) continue;
                     bool ok = false;
                     if constexpr (AGG) {
-                        ok = agg_insert<W>((AggSlot<W> *)smem, cap, &side, k[e], mix_a(r[e]), part_agg_hash<W>(k[e]));
+                        ok = at.insert(k[e], chk ? mix_a(r[e]) : 0);
                     } else {
                         T *kv = (T *)smem;
                         uint32_t bkt = part_bucket<W>(k[e], tab.nb);
@@ -979,7 +1074,6 @@ __global__ void __launch_bounds__(NT, 2048 / NT / 2) partition_join_kernel(
             if (s_full) {
                 if (threadIdx.x == 0) oversize[atomicAdd(&work->n_oversize, 1ull)] = (uint32_t)ti;
             } else {
-                AggTab<W> atab{(const AggSlot<W> *)smem, cap, &side};
                 if constexpr (FAST) {  // no aggregate, no checksum
                     probe_fast<W, U>(tab, Sv, nsv, sink, warp, nwarps, lane);
                 } else {
@@ -1012,18 +1106,38 @@ __global__ void __launch_bounds__(NT, 2048 / NT / 2) partition_join_kernel(
                         }
                     }
                     if constexpr (AGG) {
+                        // home buckets of all items first; no partition filter: a padding
+                        // tuple's key hashes to another partition, so it matches no slot
+                        uint32_t home[IT];
+                        T kb[IT][G];
 #pragma unroll
                         for (int i = 0; i < IT; ++i) {
-                            // no partition filter: a padding tuple's key hashes to another
-                            // partition, so it is in neither the table nor the side aggregate
-                            if (!val[i]) continue;
-                            uint64_t n, sa;
-                            atab.lookup(k[i], part_agg_hash<W>(k[i]), &n, &sa);
-                            acc.cnt += n;
-                            if (chk && n) {
-                                const uint64_t bb = mix_b(r[i]);
-                                acc.c0 += sa * bb;
-                                acc.c1 += sa + n * bb;
+                            home[i] = part_bucket<W>(k[i], at.nb);
+#pragma unroll
+                            for (uint32_t q = 0; q < G; ++q) kb[i][q] = at.empty;
+                            if (val[i]) at.ld(home[i], kb[i]);
+                        }
+#pragma unroll
+                        for (int i = 0; i < IT; ++i) {
+                            uint32_t mm = 0;
+                            bool e = false;
+#pragma unroll
+                            for (uint32_t q = 0; q < G; ++q) {
+                                mm |= (uint32_t)(kb[i][q] == k[i]) << q;
+                                e |= kb[i][q] == at.empty;
+                            }
+                            // (a lane past the slice's end holds a stale key: no slot)
+                            uint32_t sl = val[i] && mm ? home[i] * G + (uint32_t)(__ffs(mm) - 1) : ~0u;
+                            if (val[i] && !mm && !e && at.overflowed(home[i]))  // the run continues (rare)
+                                sl = at.find_from(k[i], home[i] + 1 == at.nb ? 0 : home[i] + 1);
+                            if (sl != ~0u) {
+                                const uint64_t n = at.cnt[sl];
+                                acc.cnt += n;
+                                if (chk) {
+                                    const uint64_t sa = at.suma[sl], bb = mix_b(r[i]);
+                                    acc.c0 += sa * bb;
+                                    acc.c1 += sa + n * bb;
+                                }
                             }
                         }
                     } else {
@@ -1188,8 +1302,11 @@ struct JoinCfg {
     int nt;
     uint64_t smem_limit;
 };
-static JoinCfg join_cfg(int width, int agg, uint64_t expect_r) {
-    const uint64_t slot = agg ? (width == 4 ? sizeof(AggSlot<4>) : sizeof(AggSlot<8>)) : 2ull * width;
+static uint64_t join_slot_bytes(int width, int agg, int checksum) {
+    return agg ? agg_slot_bytes(width, checksum) : 2ull * width;
+}
+static JoinCfg join_cfg(int width, int agg, int checksum, uint64_t expect_r) {
+    const uint64_t slot = join_slot_bytes(width, agg, checksum);
     const uint64_t need = 3 * (expect_r + 6 * (uint64_t)__builtin_sqrt((double)expect_r + 1.0) + 64) * slot;
     if (need <= (100ull << 10)) return JoinCfg{512, 100ull << 10};
     return JoinCfg{1024, 200ull << 10};
@@ -1197,15 +1314,15 @@ static JoinCfg join_cfg(int width, int agg, uint64_t expect_r) {
 
 uint64_t partition_join_warps(hj_ctx *c) { return (uint64_t)num_sms(c) * 32; }
 uint64_t partition_join_ctas(hj_ctx *c, int width, int agg, uint64_t expect_r) {
-    return (uint64_t)num_sms(c) * (2048 / join_cfg(width, agg, expect_r).nt / 2);
+    return (uint64_t)num_sms(c) * (2048 / join_cfg(width, agg, 1, expect_r).nt / 2);
 }
 
 hj_status partition_join(hj_ctx *c, int width, int agg, const PartTask *tasks, uint64_t ntasks, const JoinSlot *slots,
                          uint64_t expect_r, int checksum, uint32_t *oversize, RecArea ra, void *stage,
                          uint32_t scap) {
     if (ntasks == 0) return HJ_OK;
-    const uint64_t slot_bytes = agg ? (width == 4 ? sizeof(AggSlot<4>) : sizeof(AggSlot<8>)) : 2ull * width;
-    const JoinCfg cfg = join_cfg(width, agg, expect_r);
+    const uint64_t slot_bytes = join_slot_bytes(width, agg, checksum);
+    const JoinCfg cfg = join_cfg(width, agg, checksum, expect_r);
     // Capacity: room for a partition of the expected size plus six standard
     // deviations at load factor 1/3 (whole buckets), within the shape's budget.
     const double mean = (double)expect_r;
@@ -1216,7 +1333,7 @@ hj_status partition_join(hj_ctx *c, int width, int agg, const PartTask *tasks, u
     uint64_t cap_max = want < max_slots ? want : max_slots;
     if (cap_max < 128) cap_max = 128;
     const size_t smem = (size_t)(cap_max * slot_bytes) + (size_t)((cap_max / 2 / 32 + 1) * 4 + 16);
-    unsigned grid = (unsigned)partition_join_ctas(c, width, agg, expect_r);
+    unsigned grid = (unsigned)num_sms(c) * (2048 / cfg.nt / 2);
     if (grid > ntasks) grid = (unsigned)ntasks;
 #define HJ_PJ(WW, AA, NT, SK, FF)                                                                               \
     do {                                                                                                        \

@@ -80,11 +80,10 @@ hj_status split_host(hj_ctx *c, const hj_rel *in, int bt, uint64_t chunk, int si
         const uint64_t n = std::min(chunk, in->n - r0);
         const uint64_t seg[2] = {0, n};
         HJ_CUDA(c, cudaMemcpyAsync(d_seg.p, seg, 16, cudaMemcpyHostToDevice, c->stream));
-        HJ_CUDA(c, cudaMemcpyAsync(d_in.p, (const char *)in->tuples + r0 * tb, n * tb, cudaMemcpyHostToDevice,
-                                   c->stream));
+        HJ_TRY(copy_wide(c, d_in.p, (const char *)in->tuples + r0 * tb, n * tb, cudaMemcpyHostToDevice));
         HJ_TRY(partition_pass(c, in->width, d_in.p, n, d_seg.as<uint64_t>(), 1, kTopShift, bt, d_out.p,
                               d_off.as<uint64_t>(), 0));
-        HJ_CUDA(c, cudaMemcpyAsync((char *)hp.rows + r0 * tb, d_out.p, n * tb, cudaMemcpyDeviceToHost, c->stream));
+        HJ_TRY(copy_wide(c, (char *)hp.rows + r0 * tb, d_out.p, n * tb, cudaMemcpyDeviceToHost));
         HJ_CUDA(c, cudaMemcpyAsync(off.data(), d_off.p, (P + 1) * 8, cudaMemcpyDeviceToHost, c->stream));
         HJ_CUDA(c, cudaStreamSynchronize(c->stream));
         hp.chunk_row.push_back(r0);
@@ -178,8 +177,7 @@ extern "C" hj_status hj_join_host_large(hj_ctx *c, const hj_rel *Rh, const hj_re
             if (mat && r.count && r.pairs) {
                 const uint64_t n = written < pairs_host_cap ? std::min(r.count, pairs_host_cap - written) : 0;
                 if (n && pairs_host)
-                    HJ_CUDA(c, cudaMemcpyAsync((char *)pairs_host + written * tb, r.pairs, n * tb,
-                                               cudaMemcpyDeviceToHost, c->stream));
+                    HJ_TRY(copy_wide(c, (char *)pairs_host + written * tb, r.pairs, n * tb, cudaMemcpyDeviceToHost));
                 HJ_CUDA(c, cudaStreamSynchronize(c->stream));
                 written += n;
             }

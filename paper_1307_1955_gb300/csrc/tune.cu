@@ -75,7 +75,8 @@ static double bw(const CostModel &m) { return m.hbm_bps * kCopyFraction; }
 // Largest mean build partition whose shared-memory table stays at most half full
 // (the join kernel's biggest shape: 200 KiB of slots).
 static double fit_tuples(int width, bool agg) {
-    const double slot = agg ? (width == 4 ? 16.0 : 32.0) : 2.0 * width;
+    // aggregate slots: key, count and (with checksums, assumed) a 64-bit sum
+    const double slot = agg ? width + 12.0 : 2.0 * width;
     return (200.0 * 1024 - 4096) / slot / 2.0;
 }
 

@@ -1,7 +1,8 @@
-"""hj_join_host_large: relations in host memory joined through a device budget far
-smaller than they are (the paper's larger-than-buffer join, App. A).  The result
-must be the oracle's (bit-exact), whatever the number of top-level partitions and
-S groups the budget forces."""
+"""Joins of relations in host memory.  hj_join_host_large joins them through a
+device budget far smaller than they are (the paper's larger-than-buffer join,
+App. A); hj_join_host streams a large S through the device in chunks whose copies
+overlap the joins.  The result must be the oracle's (bit-exact), whatever the
+number of top-level partitions, S groups or chunks."""
 import numpy as np
 import pytest
 import torch
@@ -76,3 +77,64 @@ def test_large_join_overflow_reports_the_count(hjm, ctx):
     with pytest.raises(hjm.HJError) as e:
         hjm.hj_join_host_large(ctx, R, S, out, device_bytes=32 << 20)
     assert e.value.status == hjm.HJ_E_INVALID
+
+
+def _pairs_u64(t):
+    return _sorted(t.numpy().view(np.uint32 if t.dtype == torch.int32 else np.uint64).astype(np.uint64))
+
+
+def test_host_join_in_chunks_equals_device_join(hjm, ctx):
+    # hj_join_host on a large S runs chunk by chunk, copies overlapping the joins
+    # (several chunks, the last ragged); its pair multiset is the device join's and
+    # its count and checksums the oracle's.
+    R, S = W.unique_and_uniform(1 << 21, (1 << 25) + 12345, 1 << 22, W.DEFAULT_SEED, "cpu", ids=(43,))
+    cnt, c0, c1 = oracle.join_aggregate(W.to_numpy_u(R), W.to_numpy_u(S))
+    Rh, Sh = R.pin_memory(), S.pin_memory()
+    out = torch.empty((cnt + 16, 2), dtype=torch.int32).pin_memory()
+    res = hjm.hj_join_host(ctx, Rh, Sh, out, checksum=True)
+    assert (res.count, *res.checksum) == (cnt, c0, c1)
+    dev = hjm.hj_join(ctx, R.cuda(), S.cuda())
+    assert np.array_equal(_pairs_u64(out[:res.count]), _sorted(dev.pairs_numpy()))
+    dev.free()
+    cm = hjm.hj_join_host(ctx, Rh, Sh, None, mode=hjm.HJ_COUNT_CHECKSUM)
+    assert (cm.count, *cm.checksum) == (cnt, c0, c1)
+
+
+def test_host_join_in_chunks_u64_all_modes(hjm, ctx):
+    # 8-byte tuples through the chunked host join: counts and checksums in every
+    # mode are the oracle's, and every materialised pair joins equal keys.
+    R, S = W.unique_and_uniform(1 << 20, (1 << 25) + 777, 1 << 21, W.DEFAULT_SEED, "cpu", width=8, ids=(44,))
+    Ru, Su = W.to_numpy_u(R), W.to_numpy_u(S)
+    cnt, c0, c1 = oracle.join_aggregate(Ru, Su)
+    Rh, Sh = R.pin_memory(), S.pin_memory()
+    assert hjm.hj_join_host(ctx, Rh, Sh, None, mode=hjm.HJ_COUNT).count == cnt
+    cm = hjm.hj_join_host(ctx, Rh, Sh, None, mode=hjm.HJ_COUNT_CHECKSUM)
+    assert (cm.count, *cm.checksum) == (cnt, c0, c1)
+    out = torch.empty((cnt + 16, 2), dtype=torch.int64).pin_memory()
+    res = hjm.hj_join_host(ctx, Rh, Sh, out, checksum=True)
+    assert (res.count, *res.checksum) == (cnt, c0, c1)
+    got = out[:res.count].numpy().view(np.uint64)
+    assert np.array_equal(Ru[got[:, 0].astype(np.int64), 0], Su[got[:, 1].astype(np.int64), 0])
+
+
+def test_host_join_chunk_overflowing_its_buffer_is_rejoined(hjm, ctx):
+    # The first chunk of S matches twice per tuple (R holds every key of its range
+    # twice): more pairs than that chunk's buffer, so it is joined again on its own.
+    n = 1 << 20
+    keys = np.concatenate([np.arange(1, n + 1), np.arange(1, (n >> 2) + 1)]).astype(np.uint32)
+    R = torch.from_numpy(np.stack([keys, np.arange(len(keys), dtype=np.uint32)], 1).view(np.int32))
+    ns = (1 << 25) + 99
+    rng = np.random.default_rng(5)
+    sk = rng.integers(1, n + 1, ns).astype(np.uint32)
+    sk[:1 << 24] = rng.integers(1, (n >> 2) + 1, 1 << 24).astype(np.uint32)
+    S = torch.from_numpy(np.stack([sk, np.arange(ns, dtype=np.uint32)], 1).view(np.int32))
+    cnt, c0, c1 = oracle.join_aggregate(W.to_numpy_u(R), W.to_numpy_u(S))
+    assert cnt > (1 << 24) * 2
+    out = torch.empty((cnt + 16, 2), dtype=torch.int32).pin_memory()
+    res = hjm.hj_join_host(ctx, R.pin_memory(), S.pin_memory(), out, checksum=True)
+    assert (res.count, *res.checksum) == (cnt, c0, c1)
+    got = out[:res.count].numpy().view(np.uint32)
+    # every pair joins equal keys, and no pair appears twice
+    assert np.array_equal(keys[got[:, 0]], sk[got[:, 1]])
+    code = np.sort(got[:, 0].astype(np.uint64) << np.uint64(32) | got[:, 1].astype(np.uint64))
+    assert not np.any(code[1:] == code[:-1])
