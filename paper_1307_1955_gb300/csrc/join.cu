@@ -11,6 +11,7 @@
 // probe loop).  A probe key with several build matches (duplicate R keys) is
 // walked by the whole warp, 32 consecutive slots at a time -- the GPU answer to
 // the divergence that skew causes in steps b3/p3 (Sec. 3.3, workload divergence).
+#include <algorithm>
 #include <type_traits>
 
 #include "common.cuh"
@@ -762,51 +763,113 @@ template <int W> struct StageSink {
     __device__ __forceinline__ void finish() {}
 };
 
-// Probe of S_p against the partition's shared-memory table when no checksum is
-// wanted: the lean form of the loop in partition_join_kernel.
-//   * Inserts fill a bucket's slots in order and slots never empty again, so a
-//     bucket is full exactly when its last slot is; and an insert moves past a
-//     bucket only while it is full.  A key's run therefore goes on past its home
-//     bucket only if the last slot is taken AND the overflow bit is set: one
-//     compare, and the overflow bitmap is read for full buckets only.
-//   * The first matching rid is one indexed shared load.
-//   * A warp's groups that lie wholly inside S_p skip per-item validity tests;
-//     only the last, partial group of a warp tests each item.
-template <int W, bool CHECK>
-__device__ __forceinline__ void probe_item(const SoaTab<W> &tab, typename Tup<W>::U k, bool valid, uint32_t *cnt,
-                                           typename Tup<W>::U *first) {
+// One group of IT probe items against the table, in phases so that the items'
+// shared-memory loads overlap: every item's home bucket (keys), then the match
+// masks and the first match's rid (one indexed load).  cnt[i] and first[i] cover
+// the home bucket only.  Inserts fill a bucket's slots in order and slots never
+// empty again, and an insert moves past a bucket only while it is full, so a run
+// goes on past the home bucket only if the bucket's last slot is taken AND its
+// overflow bit is set: bit i of the returned mask marks such an item (with at
+// most one home match; an item with several takes the whole-run walk instead).
+// Items with live[i] false match nothing.
+template <int W, int IT>
+__device__ __forceinline__ uint32_t probe_items(const SoaTab<W> &tab, const typename Tup<W>::U *k, const bool *live,
+                                                uint32_t *cnt, typename Tup<W>::U *first) {
     using T = typename Tup<W>::U;
     constexpr uint32_t G = SoaTab<W>::G;
-    const uint32_t home = part_bucket<W>(k, tab.nb);
-    T key[G];
-    tab.ld(home, 0, key);
-    uint32_t m = 0;
+    uint32_t home[IT];
+    T kb[IT][G];
 #pragma unroll
-    for (uint32_t q = 0; q < G; ++q) m |= (uint32_t)(key[q] == k) << q;
-    if (CHECK && !valid) m = 0;
-    // the first match's rid, read without a branch (slot G - 1 when nothing matched)
-    const T fr = tab.ld1(home, 1, (uint32_t)(__ffs(m | (1u << (G - 1))) - 1));
-    T f = m ? fr : T(0);
-    uint32_t c = __popc(m);
-    if ((!CHECK || valid) && key[G - 1] != tab.empty && tab.overflowed(home)) {  // the run goes on (rare)
-        const uint32_t nx = home + 1 == tab.nb ? 0 : home + 1;
-        T f2 = 0;
-        const uint32_t c2 = soa_lookup<W>(tab, k, nx, &f2);
-        if (c == 0) f = f2;
-        c += c2;
+    for (int i = 0; i < IT; ++i) {
+        home[i] = part_bucket<W>(k[i], tab.nb);  // < nb for any key: the load is in bounds
+        tab.ld(home[i], 0, kb[i]);
     }
-    *cnt = c;
-    *first = f;
+    uint32_t walk = 0;
+#pragma unroll
+    for (int i = 0; i < IT; ++i) {
+        uint32_t m = 0;
+#pragma unroll
+        for (uint32_t q = 0; q < G; ++q) m |= (uint32_t)(kb[i][q] == k[i]) << q;
+        if (!live[i]) m = 0;
+        // the first match's rid, read without a branch (slot G - 1 when nothing matched)
+        const T fr = tab.ld1(home[i], 1, (uint32_t)(__ffs(m | (1u << (G - 1))) - 1));
+        first[i] = m ? fr : T(0);
+        cnt[i] = __popc(m);
+        walk |= (uint32_t)(live[i] && cnt[i] <= 1 && kb[i][G - 1] != tab.empty && tab.overflowed(home[i])) << i;
+    }
+    return walk;
+}
+
+// Entries per warp of the queue of pending run walks (probe keys and rids whose
+// run goes on past a full home bucket).
+constexpr uint32_t kWalkQ = 64;
+
+// Shared-memory layout of the join kernel: table slots (cap_max x slot bytes),
+// the overflow bitmap, then each warp's walk queue (kWalkQ keys, kWalkQ rids).
+__host__ __device__ constexpr uint32_t walkq_offset(uint32_t cap_max, uint32_t slot_bytes) {
+    return (cap_max * slot_bytes + (cap_max / 2 / 32 + 1) * 4 + 16 + 15) / 16 * 16;
+}
+
+// The walks of n <= 32 queued items, one per lane: each lane follows its key's run
+// from the bucket after its home and emits every match found there.  A walk is
+// rare (a few per cent of probes), so walking them one lane at a time as they
+// come would cost a whole warp pass each; batched, 32 walks cost about one.
+template <int W, class Sink>
+__device__ __forceinline__ void drain_walks(const SoaTab<W> &tab, const typename Tup<W>::U *qk,
+                                            const typename Tup<W>::U *qr, uint32_t n, Sink &sink) {
+    using T = typename Tup<W>::U;
+    constexpr uint32_t G = SoaTab<W>::G;
+    const unsigned lane = threadIdx.x & 31;
+    bool active = lane < n;
+    const T kk = active ? qk[lane] : tab.empty;
+    const T rr = active ? qr[lane] : T(0);
+    __syncwarp();  // entries read before the queue is refilled
+    uint32_t b = 0;
+    if (active) {
+        const uint32_t h = part_bucket<W>(kk, tab.nb);
+        b = h + 1 == tab.nb ? 0 : h + 1;
+    }
+    for (uint32_t it = 0; it < tab.nb; ++it) {
+        if (!__any_sync(0xffffffffu, active)) break;
+        uint32_t m = 0;
+        bool e = false;
+        if (active) {
+            T key[G];
+            tab.ld(b, 0, key);
+#pragma unroll
+            for (uint32_t q = 0; q < G; ++q) {
+                m |= (uint32_t)(key[q] == kk) << q;
+                e |= key[q] == tab.empty;
+            }
+        }
+        // the matches of this bucket, one append per round (several only for
+        // duplicate build keys)
+        for (uint32_t q = 0; q < G; ++q) {
+            const bool hm = m != 0;
+            if (!__any_sync(0xffffffffu, hm)) break;
+            T v = 0;
+            if (hm) {
+                v = tab.ld1(b, 1, (uint32_t)(__ffs(m) - 1));
+                m &= m - 1;
+            }
+            sink.append(hm, v, rr);
+        }
+        active = active && !e && tab.overflowed(b);
+        b = b + 1 == tab.nb ? 0 : b + 1;
+    }
 }
 
 template <int W, int U, class Sink>
 __device__ __forceinline__ void probe_fast(const SoaTab<W> &tab, const typename Tup<W>::Vec *Sv, uint32_t nsv,
-                                           Sink &sink, unsigned warp, unsigned nwarps, unsigned lane) {
+                                           Sink &sink, unsigned warp, unsigned nwarps, unsigned lane,
+                                           typename Tup<W>::U *wqk, typename Tup<W>::U *wqr) {
     using T = typename Tup<W>::U;
     using Vec = typename Tup<W>::Vec;
     constexpr int PV = Tup<W>::kPerVec, IT = U * PV;
     const uint32_t gstride = nwarps * 32u * U;
+    const unsigned lt = (1u << lane) - 1u;
     uint32_t g = warp * 32u * U;
+    uint32_t qn = 0;  // queued walks (warp-uniform)
     Vec cur[U], nxt[U];
 #pragma unroll
     for (int u = 0; u < U; ++u) {
@@ -821,38 +884,66 @@ __device__ __forceinline__ void probe_fast(const SoaTab<W> &tab, const typename 
             if (rel < nsv) nxt[u] = ld_stream(Sv + rel);
         }
         T k[IT], r[IT];
+        bool live[IT];
 #pragma unroll
         for (int u = 0; u < U; ++u) {
+            const bool in = g + (uint32_t)u * 32u + lane < nsv;
             if constexpr (W == 4) {
                 k[2 * u] = cur[u].x; r[2 * u] = cur[u].y; k[2 * u + 1] = cur[u].z; r[2 * u + 1] = cur[u].w;
+                live[2 * u] = in;
+                live[2 * u + 1] = in;
             } else {
                 k[u] = cur[u].x; r[u] = cur[u].y;
+                live[u] = in;
             }
         }
         uint32_t cnt[IT];
         T first[IT];
-        if (g + 32u * U <= nsv) {  // warp-uniform: the whole group is inside S_p
-#pragma unroll
-            for (int i = 0; i < IT; ++i) probe_item<W, false>(tab, k[i], true, &cnt[i], &first[i]);
-        } else {
-#pragma unroll
-            for (int i = 0; i < IT; ++i)
-                probe_item<W, true>(tab, k[i], g + (uint32_t)(i / PV) * 32u + lane < nsv, &cnt[i], &first[i]);
-        }
+        const uint32_t walk = probe_items<W, IT>(tab, k, live, cnt, first);
         sink.template append_runs<IT>(cnt, first, r);
+        // several home matches (duplicate build keys): the whole warp walks each such run
+        bool multi_any = false;
 #pragma unroll
-        for (int i = 0; i < IT; ++i) {
-            unsigned multi = __ballot_sync(0xffffffffu, cnt[i] > 1);
-            while (multi) {
-                const int L = __ffs(multi) - 1;
-                multi &= multi - 1;
-                const T kk = __shfl_sync(0xffffffffu, k[i], L);
-                const T ss = __shfl_sync(0xffffffffu, r[i], L);
-                soa_coop_emit<W>(tab, kk, ss, part_bucket<W>(kk, tab.nb), sink);
+        for (int i = 0; i < IT; ++i) multi_any |= cnt[i] > 1;
+        if (__any_sync(0xffffffffu, multi_any)) {
+#pragma unroll
+            for (int i = 0; i < IT; ++i) {
+                unsigned multi = __ballot_sync(0xffffffffu, cnt[i] > 1);
+                while (multi) {
+                    const int L = __ffs(multi) - 1;
+                    multi &= multi - 1;
+                    const T kk = __shfl_sync(0xffffffffu, k[i], L);
+                    const T ss = __shfl_sync(0xffffffffu, r[i], L);
+                    soa_coop_emit<W>(tab, kk, ss, part_bucket<W>(kk, tab.nb), sink);
+                }
+            }
+        }
+        // runs that go on past the home bucket: queued, walked 32 at a time
+        if (__any_sync(0xffffffffu, walk != 0)) {
+#pragma unroll
+            for (int i = 0; i < IT; ++i) {
+                const bool w = (walk >> i) & 1u;
+                const unsigned wm = __ballot_sync(0xffffffffu, w);
+                if (!wm) continue;
+                if (w) {
+                    const uint32_t pos = qn + (uint32_t)__popc(wm & lt);
+                    wqk[pos] = k[i];
+                    wqr[pos] = r[i];
+                }
+                qn += (uint32_t)__popc(wm);
+                if (qn >= 32) {
+                    __syncwarp();
+                    drain_walks<W>(tab, wqk + (qn - 32), wqr + (qn - 32), 32, sink);
+                    qn -= 32;
+                }
             }
         }
 #pragma unroll
         for (int u = 0; u < U; ++u) cur[u] = nxt[u];
+    }
+    if (qn) {
+        __syncwarp();
+        drain_walks<W>(tab, wqk, wqr, qn, sink);
     }
 }
 
@@ -1075,7 +1166,11 @@ __global__ void __launch_bounds__(NT, 2048 / NT / 2) partition_join_kernel(
                 if (threadIdx.x == 0) oversize[atomicAdd(&work->n_oversize, 1ull)] = (uint32_t)ti;
             } else {
                 if constexpr (FAST) {  // no aggregate, no checksum
-                    probe_fast<W, U>(tab, Sv, nsv, sink, warp, nwarps, lane);
+                    // one vector per thread and group (two 4-byte tuples, one 8-byte):
+                    // fewer live registers than U, which leaves the batched walks room
+                    constexpr int FU = 1;
+                    T *wq = (T *)(smem + walkq_offset(cap_max, 2 * W)) + (size_t)warp * 2 * kWalkQ;
+                    probe_fast<W, FU>(tab, Sv, nsv, sink, warp, nwarps, lane, wq, wq + kWalkQ);
                 } else {
                 const uint32_t gstride = nwarps * 32 * U;
                 Vec cur[U], nxt[U];
@@ -1329,10 +1424,15 @@ hj_status partition_join(hj_ctx *c, int width, int agg, const PartTask *tasks, u
     uint64_t want = (uint64_t)(3.0 * (mean + 6.0 * __builtin_sqrt(mean + 1.0) + 64.0));
     want = (want + 127) / 128 * 128;
     const uint64_t bitmap_bytes = 4096;
-    uint64_t max_slots = (cfg.smem_limit - bitmap_bytes) / slot_bytes / 128 * 128;
+    // the fast probe (no aggregate, no checksum) adds each warp's walk queue, within
+    // what the shape's CTAs per SM can have (two 512-thread CTAs share an SM)
+    const uint64_t qbytes = (!agg && !checksum) ? (uint64_t)(cfg.nt / 32) * kWalkQ * 2 * width : 0;
+    const uint64_t total_max = cfg.nt == 512 ? (112ull << 10) : (222ull << 10);
+    const uint64_t budget = std::min<uint64_t>(cfg.smem_limit + qbytes, total_max) - qbytes;
+    uint64_t max_slots = (budget - bitmap_bytes) / slot_bytes / 128 * 128;
     uint64_t cap_max = want < max_slots ? want : max_slots;
     if (cap_max < 128) cap_max = 128;
-    const size_t smem = (size_t)(cap_max * slot_bytes) + (size_t)((cap_max / 2 / 32 + 1) * 4 + 16);
+    const size_t smem = (size_t)walkq_offset((uint32_t)cap_max, (uint32_t)slot_bytes) + (size_t)qbytes;
     unsigned grid = (unsigned)num_sms(c) * (2048 / cfg.nt / 2);
     if (grid > ntasks) grid = (unsigned)ntasks;
 #define HJ_PJ(WW, AA, NT, SK, FF)                                                                               \
