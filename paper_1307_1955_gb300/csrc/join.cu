@@ -648,13 +648,31 @@ template <int W> struct ChunkSink {
         const unsigned long long c0 = st.base + st.used;
         const bool safe = c0 + (tot < room ? tot : room) <= oc.pcap && (tot <= room || nb + (tot - room) <= oc.pcap);
         unsigned run = 0;
+        if (safe) {  // (warp-uniform) every position is inside the buffer
+            // pair idx of the group goes to c0 + idx in the open chunk, else to
+            // nb + (idx - room) in the new one: one base address per item (the
+            // second base is only used for idx >= room, so its wrap is harmless)
+            using P = typename std::conditional<W == 4, uint2, ulonglong2>::type;
+            const uint64_t a0 = (uint64_t)oc.pairs + c0 * sizeof(P);
+            const uint64_t a1 = (uint64_t)oc.pairs + (nb - room) * sizeof(P);
 #pragma unroll
-        for (int i = 0; i < IT; ++i) {
-            // positions computed by every lane, only the store is predicated
-            const unsigned idx = run + __popc(m[i] & lt);
-            const unsigned long long pos = idx < room ? c0 + idx : nb + (idx - room);
-            if (cnt[i] == 1 && (safe || pos < oc.pcap)) PairOut<W>::put(oc.pairs, pos, first[i], r[i]);
-            run += __popc(m[i]);
+            for (int i = 0; i < IT; ++i) {
+                const unsigned idx = run + __popc(m[i] & lt);
+                P *dst = (P *)((idx < room ? a0 : a1) + (uint64_t)idx * sizeof(P));
+                if (cnt[i] == 1) {
+                    if constexpr (W == 4) *dst = make_uint2(first[i], r[i]);
+                    else *dst = make_ulonglong2(first[i], r[i]);
+                }
+                run += __popc(m[i]);
+            }
+        } else {
+#pragma unroll
+            for (int i = 0; i < IT; ++i) {
+                const unsigned idx = run + __popc(m[i] & lt);
+                const unsigned long long pos = idx < room ? c0 + idx : nb + (idx - room);
+                if (cnt[i] == 1 && pos < oc.pcap) PairOut<W>::put(oc.pairs, pos, first[i], r[i]);
+                run += __popc(m[i]);
+            }
         }
         if (tot > room) {
             st.base = nb;
@@ -866,6 +884,9 @@ __device__ __forceinline__ void probe_fast(const SoaTab<W> &tab, const typename 
     using T = typename Tup<W>::U;
     using Vec = typename Tup<W>::Vec;
     constexpr int PV = Tup<W>::kPerVec, IT = U * PV;
+    // the walk queue serves the chunk sink; the staging sink (batches of joins),
+    // whose appends need more registers, walks each item at once
+    constexpr bool kQueue = std::is_same<Sink, ChunkSink<W>>::value;
     const uint32_t gstride = nwarps * 32u * U;
     const unsigned lt = (1u << lane) - 1u;
     uint32_t g = warp * 32u * U;
@@ -900,6 +921,21 @@ __device__ __forceinline__ void probe_fast(const SoaTab<W> &tab, const typename 
         uint32_t cnt[IT];
         T first[IT];
         const uint32_t walk = probe_items<W, IT>(tab, k, live, cnt, first);
+        if constexpr (!kQueue) {
+            // walked at once: the run's further matches join the item's count (and
+            // an item with several then takes the whole-run walk below)
+            if (walk) {
+#pragma unroll
+                for (int i = 0; i < IT; ++i) {
+                    if (!((walk >> i) & 1u)) continue;
+                    const uint32_t h = part_bucket<W>(k[i], tab.nb);
+                    T f2 = 0;
+                    const uint32_t c2 = soa_lookup<W>(tab, k[i], h + 1 == tab.nb ? 0 : h + 1, &f2);
+                    if (cnt[i] == 0) first[i] = f2;
+                    cnt[i] += c2;
+                }
+            }
+        }
         sink.template append_runs<IT>(cnt, first, r);
         // several home matches (duplicate build keys): the whole warp walks each such run
         bool multi_any = false;
@@ -919,7 +955,7 @@ __device__ __forceinline__ void probe_fast(const SoaTab<W> &tab, const typename 
             }
         }
         // runs that go on past the home bucket: queued, walked 32 at a time
-        if (__any_sync(0xffffffffu, walk != 0)) {
+        if (kQueue && __any_sync(0xffffffffu, walk != 0)) {
 #pragma unroll
             for (int i = 0; i < IT; ++i) {
                 const bool w = (walk >> i) & 1u;
@@ -941,7 +977,7 @@ __device__ __forceinline__ void probe_fast(const SoaTab<W> &tab, const typename 
 #pragma unroll
         for (int u = 0; u < U; ++u) cur[u] = nxt[u];
     }
-    if (qn) {
+    if (kQueue && qn) {
         __syncwarp();
         drain_walks<W>(tab, wqk, wqr, qn, sink);
     }
@@ -1424,9 +1460,10 @@ hj_status partition_join(hj_ctx *c, int width, int agg, const PartTask *tasks, u
     uint64_t want = (uint64_t)(3.0 * (mean + 6.0 * __builtin_sqrt(mean + 1.0) + 64.0));
     want = (want + 127) / 128 * 128;
     const uint64_t bitmap_bytes = 4096;
-    // the fast probe (no aggregate, no checksum) adds each warp's walk queue, within
-    // what the shape's CTAs per SM can have (two 512-thread CTAs share an SM)
-    const uint64_t qbytes = (!agg && !checksum) ? (uint64_t)(cfg.nt / 32) * kWalkQ * 2 * width : 0;
+    // the fast probe (no aggregate, no checksum) into the chunk sink adds each
+    // warp's walk queue, within what the shape's CTAs per SM can have (two
+    // 512-thread CTAs share an SM)
+    const uint64_t qbytes = (!agg && !checksum && !stage) ? (uint64_t)(cfg.nt / 32) * kWalkQ * 2 * width : 0;
     const uint64_t total_max = cfg.nt == 512 ? (112ull << 10) : (222ull << 10);
     const uint64_t budget = std::min<uint64_t>(cfg.smem_limit + qbytes, total_max) - qbytes;
     uint64_t max_slots = (budget - bitmap_bytes) / slot_bytes / 128 * 128;
