@@ -348,6 +348,11 @@ typedef struct hj_prof_entry {
     double ms;
 } hj_prof_entry;
 hj_status hj_prof_enable(hj_ctx *ctx, int on);
+/* Restrict the event brackets to launches of the kernel named `name` (as reported
+ * by hj_prof_read); NULL or "" brackets every launch again.  Timing one kernel
+ * costs two event records per launch of it and nothing for the others.  Copies
+ * the name; HJ_E_INVALID for a NULL context or a name of 48 chars or more. */
+hj_status hj_prof_only(hj_ctx *ctx, const char *name);
 hj_status hj_prof_reset(hj_ctx *ctx);
 hj_status hj_prof_read(hj_ctx *ctx, hj_prof_entry *entries, int cap, int *n_out);
 uint64_t hj_launch_count(const hj_ctx *ctx);

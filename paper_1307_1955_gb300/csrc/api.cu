@@ -164,24 +164,23 @@ uint64_t first_capacity(const hj_opts &o, uint64_t nS, uint64_t warps) {
 hj_status probe_into(hj_ctx *c, const hj_table *t, const hj_rel *S, const hj_opts &o, hj_result *res,
                      bool after_build = false) {
     const bool mat = o.mode == HJ_MATERIALIZE, chk = wants_checksum(o);
-    const uint64_t warps = table_probe_warps(c, S->n);
     PairSink sink(c, t->width);
-    uint64_t cap = mat ? first_capacity(o, S->n, warps) : 0;
+    // exact output leaves no holes: the caller's hint, else one pair per probe tuple
+    uint64_t cap = mat ? std::max<uint64_t>(o.out_capacity ? o.out_capacity : S->n, 1) : 0;
     for (int attempt = 0; attempt < 2; ++attempt) {
+        // warps stage their pairs in shared memory and claim exact rows: the
+        // output is dense as written, no compaction pass
         RecArea ra{nullptr, nullptr, 0};
-        if (mat) {
-            HJ_TRY(sink.reset(cap));
-            HJ_TRY(sink.new_area(warps, &ra));
-        }
+        if (mat) HJ_TRY(sink.reset(cap));
         if (!(after_build && attempt == 0)) HJ_TRY(zero_counters(c));
-        HJ_TRY(table_probe(c, t, S->tuples, 0, S->n, S->n, sink.pairs.p, sink.pcap, chk, ra, PartFilter{0, 0, 0, 0}));
-        if (mat) HJ_TRY(sink.finalize_device(c->d_ctr));
+        HJ_TRY(table_probe(c, t, S->tuples, 0, S->n, S->n, sink.pairs.p, sink.pcap, chk, ra, PartFilter{0, 0, 0, 0},
+                           nullptr, 2));
         HJ_TRY(read_counters(c));
         if (c->h_ctr->status & kStatusTableFull) return set_err(c, HJ_E_CUDA, "hash table unexpectedly full");
         HJ_TRY(check_output_status(c));
-        if (!mat || c->h_ctr->cursor <= sink.pcap) break;
+        if (!mat || c->h_ctr->count <= sink.pcap) break;
         // more pairs than the capacity: run the probe again at the exact size
-        cap = c->h_ctr->count + warps * kChunkPairs;
+        cap = c->h_ctr->count;
         if (attempt == 1) return set_err(c, HJ_E_CUDA, "pair capacity still too small after resizing");
     }
     fill_result(c, res, t->width, HJ_ALGO_SHJ, 0, 0);

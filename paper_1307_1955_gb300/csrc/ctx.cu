@@ -76,7 +76,10 @@ static cudaEvent_t take_event(hj_ctx *c) {
 
 void prof_begin(hj_ctx *c, const char *name) {
     c->launches++;
+    c->prof_open = false;
     if (!c->prof) return;
+    if (!c->prof_only.empty() && c->prof_only != name) return;
+    c->prof_open = true;
     hj_ctx::Rec r;
     r.name = name;
     r.a = take_event(c);
@@ -86,7 +89,8 @@ void prof_begin(hj_ctx *c, const char *name) {
 }
 
 void prof_end(hj_ctx *c) {
-    if (!c->prof || c->recs.empty()) return;
+    if (!c->prof_open || c->recs.empty()) return;
+    c->prof_open = false;
     cudaEventRecord(c->recs.back().b, c->stream);
 }
 
@@ -277,6 +281,13 @@ hj_status hj_sync(hj_ctx *c) {
 hj_status hj_prof_enable(hj_ctx *c, int on) {
     if (!c) return HJ_E_INVALID;
     c->prof = on != 0;
+    return HJ_OK;
+}
+
+hj_status hj_prof_only(hj_ctx *c, const char *name) {
+    if (!c) return HJ_E_INVALID;
+    if (name && strlen(name) >= sizeof(hj_prof_entry{}.name)) return set_err(c, HJ_E_INVALID, "kernel name too long");
+    c->prof_only = name ? name : "";
     return HJ_OK;
 }
 

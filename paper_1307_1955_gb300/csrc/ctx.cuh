@@ -54,6 +54,8 @@ struct hj_ctx {
     hj_counters *h_ctr = nullptr;      // pinned host mirror
     // profiling
     bool prof = false;
+    bool prof_open = false;   // the last launch was bracketed (its end event is due)
+    std::string prof_only;    // bracket only this kernel ("" = all)
     struct Rec {
         const char *name;
         cudaEvent_t a, b;

@@ -43,13 +43,19 @@ template <> struct PairOut<8> {
 
 // Output context of a launch: the pair buffer of one join and its counters.  With
 // `dense`, every append claims exactly its pairs from ctr->count (no chunks, no
-// holes); otherwise warps take whole chunks from ctr->cursor.
+// holes).  With `stage` (this warp's shared-memory buffer of `scap` pairs), a warp
+// collects its pairs there and claims exactly as many rows of ctr->count when the
+// buffer fills or the warp is done, then copies them out with coalesced stores:
+// no holes either, one atomic per buffer.  Otherwise warps take whole chunks from
+// ctr->cursor.
 struct OutCtx {
     void *pairs;
     uint64_t pcap;
     hj_counters *ctr;
     unsigned int join = 0;
     bool dense = false;
+    void *stage = nullptr;
+    unsigned scap = 0;
 };
 
 // Warp-uniform state of a warp's current chunk.
@@ -60,6 +66,29 @@ struct OutState {
     unsigned long long pairs = 0;
 };
 
+template <int W> struct PairVec { using T = uint2; };
+template <> struct PairVec<8> { using T = ulonglong2; };
+
+// Staged output: claim rows for the st.used pairs in the warp's buffer and copy
+// them out (pairs past the capacity are dropped; the count stays exact).  All 32
+// lanes must call.
+template <int W> __device__ __forceinline__ void warp_stage_flush(OutState &st, const OutCtx &oc) {
+    using P = typename PairVec<W>::T;
+    const unsigned n = st.used;
+    if (!n) return;
+    __syncwarp();  // the buffer's stores are visible to every lane
+    const unsigned lane = threadIdx.x & 31;
+    unsigned long long b = 0;
+    if (lane == 0) b = atomicAdd(&oc.ctr->count, (unsigned long long)n);
+    b = __shfl_sync(0xffffffffu, b, 0);
+    const P *sp = (const P *)oc.stage;
+    P *out = (P *)oc.pairs;
+    for (unsigned i = lane; i < n; i += 32)
+        if (b + i < oc.pcap) out[b + i] = sp[i];
+    __syncwarp();  // read before the buffer is refilled
+    st.used = 0;
+}
+
 // Append one pair per lane whose `has` is set.  All 32 lanes must call.
 template <int W>
 __device__ __forceinline__ void warp_append(OutState &st, const OutCtx &oc, bool has, typename Tup<W>::U a,
@@ -69,6 +98,16 @@ __device__ __forceinline__ void warp_append(OutState &st, const OutCtx &oc, bool
     const unsigned lane = threadIdx.x & 31;
     const unsigned k = __popc(mask);
     const unsigned rank = __popc(mask & ((1u << lane) - 1u));
+    if (oc.stage) {  // (k <= 32 <= scap: one flush makes room)
+        if (st.used + k > oc.scap) warp_stage_flush<W>(st, oc);
+        using P = typename PairVec<W>::T;
+        if (has) {
+            if constexpr (W == 4) ((P *)oc.stage)[st.used + rank] = make_uint2(a, b_);
+            else ((P *)oc.stage)[st.used + rank] = make_ulonglong2(a, b_);
+        }
+        st.used += k;
+        return;
+    }
     if (oc.dense) {
         unsigned long long b = 0;
         if (lane == 0) b = atomicAdd(&oc.ctr->count, (unsigned long long)k);
@@ -99,7 +138,7 @@ __device__ __forceinline__ void warp_append(OutState &st, const OutCtx &oc, bool
 // Record the warp's partly filled chunk and add its pair count.  All lanes call.
 __device__ __forceinline__ void warp_finish(const OutState &st, const OutCtx &oc, const RecArea &ra) {
     if ((threadIdx.x & 31) != 0) return;
-    if (oc.dense) return;  // dense appends count themselves and leave no holes
+    if (oc.dense || oc.stage) return;  // exact claims count themselves and leave no holes
     if (st.claimed && st.used < kChunkPairs) {
         unsigned long long i = atomicAdd(ra.n, 1ull);
         if (i < ra.cap) {

@@ -22,8 +22,11 @@ hj_status table_build(hj_ctx *c, hj_table *t, const void *R, uint64_t lo, uint64
 // Probe with tuples [lo, hi) of S; counts and checksums accumulate into the
 // context counters, pairs into `pairs` (capacity pcap; unused in count modes).
 // Warps that leave a partly filled output chunk record it in `ra`.
-// ctr: the counters to accumulate into (NULL: the context's); with `dense`
-// every append claims exactly its rows from ctr->count (no chunks, no holes).
+// ctr: the counters to accumulate into (NULL: the context's).  dense: 0 = warps
+// take whole chunks of the cursor (holes recorded in `ra`); 1 = every append
+// claims exactly its rows from ctr->count; 2 = each warp stages its pairs in
+// shared memory and claims exactly that many rows per full buffer (no holes,
+// one atomic per 256 pairs).
 hj_status table_probe(hj_ctx *c, const hj_table *t, const void *S, uint64_t lo, uint64_t hi, uint64_t n_total,
                       void *pairs, uint64_t pcap, int checksum, RecArea ra, PartFilter pf,
                       hj_counters *ctr = nullptr, int dense = 0);

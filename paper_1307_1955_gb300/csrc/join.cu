@@ -260,6 +260,9 @@ template <int W> struct ProbeU {
     static constexpr int value = 2;
 };
 
+// Pairs per warp in the probe's shared-memory staging buffer (exact output mode).
+constexpr unsigned kProbeStage = 256;
+
 template <int W, bool AGG>
 __global__ void __launch_bounds__(256) table_probe_kernel(const void *S, uint64_t lo, uint64_t hi, uint64_t n_total,
                                                           const void *slots, uint64_t cap, const TableSide *side,
@@ -270,7 +273,13 @@ __global__ void __launch_bounds__(256) table_probe_kernel(const void *S, uint64_
     const unsigned nwarps = (gridDim.x * blockDim.x) >> 5;
     const uint64_t va = lo / PV;
     OutState st;
-    OutCtx oc{pairs, pcap, ctr, 0u, dense != 0};
+    OutCtx oc{pairs, pcap, ctr, 0u, dense == 1};
+    extern __shared__ __align__(16) unsigned char tp_stage[];
+    if (dense == 2) {  // this warp's staging buffer
+        oc.stage = tp_stage + (size_t)(threadIdx.x >> 5) * kProbeStage * 2 * W;
+        oc.scap = kProbeStage;
+        st.used = 0;
+    }
     ProbeAcc acc;
     if constexpr (AGG) {
         AggTab<W> tab{(const AggSlot<W> *)slots, cap, side};
@@ -280,6 +289,7 @@ __global__ void __launch_bounds__(256) table_probe_kernel(const void *S, uint64_
         PairTab<W> tab{(const typename PairSlot<W>::S *)slots, cap, side->n_allones, 1u};
         warp_probe<W, U, false>(tab, S, lo, hi, n_total, va + (uint64_t)warp * 32 * U, (uint64_t)nwarps * 32 * U,
                                 pf, chk != 0, st, oc, acc);
+        if (oc.stage) warp_stage_flush<W>(st, oc);
         warp_finish(st, oc, ra);
     }
     flush_acc(ctr, acc, AGG);
@@ -351,7 +361,8 @@ hj_status table_probe(hj_ctx *c, const hj_table *t, const void *S, uint64_t lo, 
     if (!ctr) ctr = c->d_ctr;
     const unsigned grid = (unsigned)(table_probe_warps(c, hi - lo) / 8);
     const TableSide *side = (const TableSide *)t->side;
-#define HJ_TP(WW, AA) HJ_LAUNCH(c, "table_probe", (table_probe_kernel<WW, AA>), grid, 256, 0, S, lo, hi, n_total, t->slots, t->cap, side, pairs, pcap, ra, ctr, checksum, pf, dense)
+    const size_t smem = dense == 2 && !t->agg ? (size_t)8 * kProbeStage * 2 * t->width : 0;
+#define HJ_TP(WW, AA) HJ_LAUNCH(c, "table_probe", (table_probe_kernel<WW, AA>), grid, 256, smem, S, lo, hi, n_total, t->slots, t->cap, side, pairs, pcap, ra, ctr, checksum, pf, dense)
     if (t->width == 4) {
         if (t->agg) HJ_TP(4, true); else HJ_TP(4, false);
     } else {

@@ -104,6 +104,7 @@ def load_library(path: str = LIB_PATH):
         "hj_sync": (I32, [V]),
         "hj_copy": (I32, [V, V, V, U64]),
         "hj_prof_enable": (I32, [V, ctypes.c_int]),
+        "hj_prof_only": (I32, [V, ctypes.c_char_p]),
         "hj_prof_reset": (I32, [V]),
         "hj_prof_read": (I32, [V, P(hj_prof_entry), ctypes.c_int, P(ctypes.c_int)]),
         "hj_launch_count": (U64, [V]),
@@ -446,6 +447,11 @@ def hj_sync(ctx: Context):
 
 def prof_enable(ctx: Context, on: bool = True):
     _check(ctx, load_library().hj_prof_enable(ctx.handle, 1 if on else 0))
+
+
+def prof_only(ctx: Context, name: str | None = None):
+    """Bracket only launches of kernel `name` with events (None: every launch)."""
+    _check(ctx, load_library().hj_prof_only(ctx.handle, name.encode() if name else None))
 
 
 def prof_reset(ctx: Context):
