@@ -69,6 +69,16 @@ WORKLOADS = {
         desc="larger-than-device join from host memory: the 2^24 x 2^28 PHJ workload (uint32 key/rid, ~50% "
              "match) in page-locked host memory, joined through a 1 GiB device budget (chunked top-level split on "
              "the device, host partitions, partition pairs joined on the device), pairs copied to host memory"),
+    "heavy_16m_s10": dict(
+        kind="heavy", nr=1 << 24, ns=1 << 24, s=0.10, algo=2,
+        desc="the paper's low-skew data set at its default size: |R| = |S| = 2^24 (uint32 key, uint32 rid); 10 % of "
+             "R's tuples share one key, the other R keys distinct, S keys uniform over R's distinct keys; pairs "
+             "materialised"),
+    "heavy_16m_s25": dict(
+        kind="heavy", nr=1 << 24, ns=1 << 24, s=0.25, algo=2,
+        desc="the paper's high-skew data set at its default size: |R| = |S| = 2^24 (uint32 key, uint32 rid); 25 % of "
+             "R's tuples share one key, the other R keys distinct, S keys uniform over R's distinct keys; pairs "
+             "materialised"),
     "shj_1m": dict(
         nr=1 << 20, ns=1 << 20, dom=1 << 20, algo=1,
         desc="SHJ, |R|=|S|=2^20 (uint32 key, uint32 rid); R keys a permutation of 1..2^20, S keys drawn "
@@ -276,6 +286,8 @@ def make_inputs(wl, rank, device):
         return W.zipf_pair(wl["nr"], wl["ns"], wl["theta_r"], wl["theta_s"], wl["ranks"], W.DEFAULT_SEED, device,
                            ids=(3, int(wl["theta_s"] * 10), rank))
 
+    if wl.get("kind") == "heavy":
+        return W.heavy_hitter(wl["nr"], wl["ns"], wl["s"], W.DEFAULT_SEED, device, ids=(66, int(wl["s"] * 100), rank))
     return W.unique_and_uniform(wl["nr"], wl["ns"], wl["dom"], W.DEFAULT_SEED, device, ids=(2, rank))
 
 
@@ -316,7 +328,7 @@ def run_reference(args, wl, ws, rank):
     if wl.get("kind") in ("batch", "serve"):
         run_reference_batch(args, wl, ws, per_step)
         return
-    if wl.get("kind") == "zipf":
+    if wl.get("kind") in ("zipf", "heavy"):
         run_reference_prefix(args, wl, ws, per_step)
         return
     # Scale the workload down (|S| / |R| and the key-domain ratio kept) so that one
@@ -532,7 +544,7 @@ def run_hj(args, wl, ws, rank, local):
     if not args.no_e2e:
         Rh = R.cpu().pin_memory()
         Sh = S.cpu().pin_memory()
-        out = (torch.empty((wl["ns"] + (1 << 20), 2), dtype=R.dtype).pin_memory()
+        out = (torch.empty((max(wl["ns"], count) + (1 << 20), 2), dtype=R.dtype).pin_memory()
                if mode == hj.HJ_MATERIALIZE else None)
         res = hj.hj_join_host(ctx, Rh, Sh, out, **kw)
         m = res.count

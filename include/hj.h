@@ -120,8 +120,10 @@ const char *hj_last_error(const hj_ctx *ctx);
 
 /* SHJ build phase (Alg. 1, steps b1-b4): a device hash table on R.  For the
  * MATERIALIZE mode the table holds every R tuple (duplicates kept as separate
- * entries); for the count modes it holds one entry per distinct key with the
- * tuple count and the sum of A(rid).  `opts->mode` fixes which; the table is only
+ * entries; if a key repeats so often that an insert walks past 1024 slots, the
+ * table is rebuilt in the paper's key-list form -- one entry per distinct key
+ * with the list of its rids -- within the same call); for the count modes it
+ * holds one entry per distinct key with the tuple count and the sum of A(rid).  `opts->mode` fixes which; the table is only
  * valid for probes in a mode of the same family.  R is read during the call's
  * stream work only; the table does not point into R. */
 hj_status hj_build(hj_ctx *ctx, const hj_rel *R, const hj_opts *opts, hj_table **out);
@@ -239,7 +241,10 @@ hj_status hj_result_free(hj_ctx *ctx, hj_result *res);
  * NULL when pairs_cap is 0).  *count receives the number of pairs; checksum
  * (NULL allowed) receives c0, c1 as in HJ_COUNT_CHECKSUM; the pairs are written
  * densely in no particular order.  Returns HJ_E_OVERFLOW, with *count set, if
- * the join has more than pairs_cap pairs (the first pairs_cap are written).
+ * the join has more than pairs_cap pairs (the first pairs_cap are written).  Its
+ * table keeps one slot per build tuple, so a build key repeated so often that an
+ * insert walks past 65536 slots makes the call return HJ_E_UNSUPPORTED (nothing
+ * useful in *count or the pairs): hj_join handles such relations.
  *
  * Its scratch -- counters and the hash table -- is one file-scope device array of
  * HJ_STATIC_SCRATCH_BYTES bytes in the library, which every GPU that loads the

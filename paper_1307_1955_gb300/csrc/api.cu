@@ -21,7 +21,9 @@ struct TableHold {
 };
 
 // Partitions whose table did not fit in shared memory: SHJ with a global table,
-// task by task (host loop over the listed tasks).
+// task by task (host loop over the listed tasks).  Such a partition may hold a
+// heavily repeated key, so pairs come from a key-list table (one entry per
+// distinct key, its rids in one list); count modes use the aggregate table.
 hj_status oversize_fallback(hj_ctx *c, int W, bool agg, bool chk, const PartTask *tasks, const uint32_t *list_dev,
                             uint64_t nov, const std::vector<JoinSlot> &slots_host) {
     std::vector<uint32_t> list(nov);
@@ -34,6 +36,11 @@ hj_status oversize_fallback(hj_ctx *c, int W, bool agg, bool chk, const PartTask
         const PartFilter pf{tk.p, (int)tk.b1, (int)tk.b2, 1};
         const JoinSlot &js = slots_host[tk.join];
         TableHold tg{c};
+        if (!agg) {
+            HJ_TRY(keylist_build(c, W, tk.R, tk.nr, pf, &tg.t));
+            HJ_TRY(keylist_probe(c, tg.t, tk.S, tk.ns, pf, js.pairs, js.pcap, js.ctr, chk));
+            continue;
+        }
         HJ_TRY(table_create(c, W, agg, tk.nr, &tg.t));
         HJ_TRY(table_build(c, tg.t, tk.R, 0, tk.nr, tk.nr, pf));
         const RecArea none{nullptr, nullptr, 0};
@@ -160,9 +167,11 @@ uint64_t first_capacity(const hj_opts &o, uint64_t nS, uint64_t warps) {
 // ----------------------------------------------------------------------- SHJ
 // With `after_build` the counters hold the status of a build queued just before
 // (no host synchronisation in between): the first attempt keeps them, and a full
-// table is reported after the probe.
+// table is reported after the probe.  A build that met a run of repeated keys
+// (kStatusLongRun) sets *long_run and leaves the result alone: the caller builds
+// a key-list table and probes again.
 hj_status probe_into(hj_ctx *c, const hj_table *t, const hj_rel *S, const hj_opts &o, hj_result *res,
-                     bool after_build = false) {
+                     bool after_build = false, bool *long_run = nullptr) {
     const bool mat = o.mode == HJ_MATERIALIZE, chk = wants_checksum(o);
     PairSink sink(c, t->width);
     // exact output leaves no holes: the caller's hint, else one pair per probe tuple
@@ -173,10 +182,19 @@ hj_status probe_into(hj_ctx *c, const hj_table *t, const hj_rel *S, const hj_opt
         RecArea ra{nullptr, nullptr, 0};
         if (mat) HJ_TRY(sink.reset(cap));
         if (!(after_build && attempt == 0)) HJ_TRY(zero_counters(c));
-        HJ_TRY(table_probe(c, t, S->tuples, 0, S->n, S->n, sink.pairs.p, sink.pcap, chk, ra, PartFilter{0, 0, 0, 0},
-                           nullptr, 2));
+        if (t->keylist)
+            HJ_TRY(keylist_probe(c, t, S->tuples, S->n, PartFilter{0, 0, 0, 0}, sink.pairs.p, sink.pcap, c->d_ctr,
+                                 chk));
+        else
+            HJ_TRY(table_probe(c, t, S->tuples, 0, S->n, S->n, sink.pairs.p, sink.pcap, chk, ra,
+                               PartFilter{0, 0, 0, 0}, nullptr, 2));
         HJ_TRY(read_counters(c));
         if (c->h_ctr->status & kStatusTableFull) return set_err(c, HJ_E_CUDA, "hash table unexpectedly full");
+        if (c->h_ctr->status & kStatusLongRun) {
+            if (!long_run) return set_err(c, HJ_E_CUDA, "pair table with a run of repeated keys");
+            *long_run = true;
+            return HJ_OK;
+        }
         HJ_TRY(check_output_status(c));
         if (!mat || c->h_ctr->count <= sink.pcap) break;
         // more pairs than the capacity: run the probe again at the exact size
@@ -194,6 +212,14 @@ hj_status join_shj(hj_ctx *c, const hj_rel *R, const hj_rel *S, const hj_opts &o
     HJ_TRY(zero_counters(c));
     HJ_TRY(table_create(c, R->width, is_agg(o.mode), R->n, &tg.t));
     HJ_TRY(table_build(c, tg.t, R->tuples, 0, R->n, R->n, PartFilter{0, 0, 0, 0}));
+    bool long_run = false;
+    HJ_TRY(probe_into(c, tg.t, S, o, res, true, &long_run));
+    if (!long_run) return HJ_OK;
+    // heavily repeated build keys: one entry per distinct key with its rid list
+    table_destroy(c, tg.t);
+    tg.t = nullptr;
+    HJ_TRY(zero_counters(c));
+    HJ_TRY(keylist_build(c, R->width, R->tuples, R->n, PartFilter{0, 0, 0, 0}, &tg.t));
     return probe_into(c, tg.t, S, o, res, true);
 }
 
@@ -465,6 +491,14 @@ hj_status hj_build(hj_ctx *c, const hj_rel *R, const hj_opts *opts, hj_table **o
     HJ_TRY(table_build(c, tg.t, R->tuples, 0, R->n, R->n, PartFilter{0, 0, 0, 0}));
     HJ_TRY(read_counters(c));
     if (c->h_ctr->status & kStatusTableFull) return set_err(c, HJ_E_CUDA, "hash table unexpectedly full");
+    if (c->h_ctr->status & kStatusLongRun) {  // heavily repeated keys: a key-list table
+        table_destroy(c, tg.t);
+        tg.t = nullptr;
+        HJ_TRY(zero_counters(c));
+        HJ_TRY(keylist_build(c, R->width, R->tuples, R->n, PartFilter{0, 0, 0, 0}, &tg.t));
+        HJ_TRY(read_counters(c));
+        if (c->h_ctr->status & kStatusTableFull) return set_err(c, HJ_E_CUDA, "hash table unexpectedly full");
+    }
     *out = tg.t;
     tg.t = nullptr;
     return HJ_OK;

@@ -215,11 +215,18 @@ struct TableSide {
     unsigned long long full;        // set when an insert found no free slot
 };
 
+// Longest walk of a pair-table insert.  Unique keys at load factor <= 1/2 never
+// come near it; a key with many copies does (every copy walks past the earlier
+// ones), and the join then takes a key-list table instead.
+constexpr uint64_t kMaxPairWalk = 1024;
+
 // Insert one build tuple into a pair table of `cap` slots.  Returns false if
-// the table had no free slot (cannot happen while cap > number of tuples).
+// the table had no free slot (cannot happen while cap > number of tuples) or
+// the walk passed max_walk slots.
 template <int W>
 __device__ __forceinline__ bool pair_insert(typename PairSlot<W>::S *slots, uint64_t cap, TableSide *side,
-                                            typename Tup<W>::U k, typename Tup<W>::U r, uint64_t h) {
+                                            typename Tup<W>::U k, typename Tup<W>::U r, uint64_t h,
+                                            uint64_t max_walk = kMaxPairWalk) {
     using PS = PairSlot<W>;
     if (k == Tup<W>::kAllOnes && r == Tup<W>::kAllOnes) {
         atomicAdd(&side->n_allones, 1ull);
@@ -227,7 +234,8 @@ __device__ __forceinline__ bool pair_insert(typename PairSlot<W>::S *slots, uint
     }
     typename PS::S v = PS::pack(k, r);
     uint64_t b = bucket_of<W>(h, cap);
-    for (uint64_t it = 0; it < cap; ++it) {
+    const uint64_t lim = cap < max_walk ? cap : max_walk;
+    for (uint64_t it = 0; it < lim; ++it) {
         if (PS::try_claim(&slots[b], v)) return true;
         if (++b == cap) b = 0;
     }
@@ -378,6 +386,7 @@ enum : int {
     kStatusBadInput = 4,
     kStatusRecords = 8,    // a chunk-record area was too small
     kStatusCompact = 16,   // device compaction found holes and tail pairs of different sizes
+    kStatusLongRun = 32,   // a pair-table insert walked past kMaxPairWalk slots (heavily repeated keys)
 };
 
 }  // namespace hj

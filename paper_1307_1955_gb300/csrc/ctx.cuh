@@ -87,10 +87,13 @@ struct hj_ctx {
 
 struct hj_table {
     int width = 4;
-    int agg = 0;          // 1: aggregate table (count modes), 0: pair table
+    int agg = 0;          // 1: aggregate table (count modes), 0: pairs (pair or key-list table)
     void *slots = nullptr;
     uint64_t cap = 0;
     void *side = nullptr; // hj::TableSide on the device
+    int keylist = 0;      // 1: aggregate-table slots plus rid lists (heavily repeated build keys)
+    void *rids = nullptr; // key-list table: every key's rids, contiguous
+    uint64_t nr = 0;      // key-list table: build tuples (size of rids)
 };
 
 namespace hj {

@@ -15,6 +15,14 @@ struct RecArea;  // emit.cuh
 // Global-memory table (SHJ, Alg. 1): allocate + initialise, build, probe.
 hj_status table_create(hj_ctx *c, int width, int agg, uint64_t n_build, hj_table **out);
 void table_destroy(hj_ctx *c, hj_table *t);
+// Key-list table (keylist.cu): aggregate-table slots over the kept tuples of
+// R[0, n) plus the rid lists (t->rids, every key's rids contiguous at the offset
+// its slot holds).  For build relations with heavily repeated keys.
+hj_status keylist_build(hj_ctx *c, int width, const void *R, uint64_t n, PartFilter pf, hj_table **out);
+// Pairs of the kept tuples of S[0, ns) against a key-list table, claimed exactly
+// from ctr->count (dense output); checksums with `chk`.
+hj_status keylist_probe(hj_ctx *c, const hj_table *t, const void *S, uint64_t ns, PartFilter pf, void *pairs,
+                        uint64_t pcap, hj_counters *ctr, int chk);
 // Insert tuples [lo, hi) of the array `R` (n_total tuples long) into the table.
 // With pf.on only tuples of partition pf.p are inserted (padding is skipped).
 hj_status table_build(hj_ctx *c, hj_table *t, const void *R, uint64_t lo, uint64_t hi, uint64_t n_total,

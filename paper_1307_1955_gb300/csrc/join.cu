@@ -250,7 +250,8 @@ __global__ void __launch_bounds__(256) table_build_kernel(const void *R, uint64_
             if (!pf.keep(h)) continue;
             bool ok = AGG ? agg_insert<W>((AggSlot<W> *)slots, cap, side, k[e], mix_a(r[e]), h)
                           : pair_insert<W>((typename PairSlot<W>::S *)slots, cap, side, k[e], r[e], h);
-            if (!ok) atomicOr(&ctr->status, (unsigned long long)kStatusTableFull);
+            if (!ok) atomicOr(&ctr->status, (unsigned long long)(AGG || cap <= kMaxPairWalk ? kStatusTableFull
+                                                                                         : kStatusLongRun));
         }
     }
 }
@@ -327,6 +328,7 @@ void table_destroy(hj_ctx *c, hj_table *t) {
     if (!t) return;
     dfree(c, t->slots);
     dfree(c, t->side);
+    dfree(c, t->rids);
     delete t;
 }
 
@@ -829,6 +831,9 @@ __device__ __forceinline__ uint32_t probe_items(const SoaTab<W> &tab, const type
     return walk;
 }
 
+// Longest walk (in buckets) of an insert into a partition's shared-memory table.
+constexpr uint32_t kMaxSmemWalk = 64;
+
 // Entries per warp of the queue of pending run walks (probe keys and rids whose
 // run goes on past a full home bucket).
 constexpr uint32_t kWalkQ = 64;
@@ -1190,7 +1195,10 @@ __global__ void __launch_bounds__(NT, 2048 / NT / 2) partition_join_kernel(
                     } else {
                         T *kv = (T *)smem;
                         uint32_t bkt = part_bucket<W>(k[e], tab.nb);
-                        for (uint32_t it = 0; it < tab.nb && !ok; ++it) {
+                        // a walk past kMaxSmemWalk buckets means a heavily repeated
+                        // key: the partition goes to the key-list fallback
+                        const uint32_t lim = tab.nb < kMaxSmemWalk ? tab.nb : kMaxSmemWalk;
+                        for (uint32_t it = 0; it < lim && !ok; ++it) {
                             for (uint32_t q = 0; q < G; ++q) {
                                 T *slot = &kv[bkt * G + q];
                                 if (cas_key<W>(slot, empty, k[e]) == empty) {

@@ -1,0 +1,417 @@
+// keylist.cu -- the hash table of Sec. 3.1 with key lists and rid lists, for
+// build relations whose keys repeat heavily.
+//
+// Open addressing over (key, rid) slots stores each duplicate in a slot of its
+// own: a key with a million copies becomes a run of a million slots that every
+// probe landing in it has to walk.  The paper's table instead gives each
+// distinct key one entry whose rid list holds all of its build tuples' rids.
+// Here that is the aggregate table (one slot per distinct key with its count)
+// plus one array of rids:
+//   1. build the aggregate table over R (counts);
+//   2. an exclusive scan of the counts gives each key the offset of its rid list;
+//   3. a second pass over R places every rid in its key's list (a per-key fill
+//      position claimed by atomicAdd; the order inside a list is free).
+// A probe finds its key's one slot and emits the key's rid list with its own rid:
+// a single pair at once; a list of up to kCoopPairs by the whole warp, reading
+// the list with coalesced loads; a longer list (a heavy hitter) is recorded and
+// expanded afterwards by a grid-wide kernel in segments of kSegPairs pairs, so
+// that the millions of pairs of one probe tuple are written by every SM.
+// R tuples whose key is all ones (the aggregate table's empty marker) are
+// counted on the table's side and keep their rids at the end of the array.
+#include <algorithm>
+
+#include "common.cuh"
+#include "ctx.cuh"
+#include "emit.cuh"
+#include "engine.cuh"
+
+namespace hj {
+
+namespace {
+
+constexpr unsigned kScanThreads = 1024;
+constexpr uint64_t kScanBlock = 2 * kScanThreads;  // entries per scan block
+constexpr uint64_t kCoopPairs = 4096;              // longest list one warp emits
+constexpr uint64_t kSegPairs = 1ull << 16;         // pairs per expansion segment
+
+template <int W>
+__device__ __forceinline__ void kl_load(const void *base, uint64_t v, uint64_t n_total, typename Tup<W>::U *k,
+                                        typename Tup<W>::U *r) {
+    if constexpr (W == 8) {
+        const ulonglong2 x = ld_stream((const ulonglong2 *)base + v);
+        k[0] = x.x;
+        r[0] = x.y;
+    } else if (2 * v + 1 < n_total) {
+        const uint4 x = ld_stream((const uint4 *)base + v);
+        k[0] = x.x; r[0] = x.y; k[1] = x.z; r[1] = x.w;
+    } else {
+        const uint2 x = ((const uint2 *)base)[2 * v];
+        k[0] = x.x; r[0] = x.y; k[1] = 0; r[1] = 0;
+    }
+}
+
+// Slot of key k (not all ones) in the aggregate table, or cap if absent.
+template <int W>
+__device__ __forceinline__ uint64_t kl_find(const AggSlot<W> *slots, uint64_t cap, typename Tup<W>::U k, uint64_t h) {
+    uint64_t b = bucket_of<W>(h, cap);
+    for (uint64_t it = 0; it < cap; ++it) {
+        const typename Tup<W>::U sk = slots[b].key;
+        if (sk == k) return b;
+        if (sk == Tup<W>::kAllOnes) return cap;
+        if (++b == cap) b = 0;
+    }
+    return cap;
+}
+
+// ------------------------------------------------------------------ scans
+// Exclusive scans of per-entry counts, in three launches (block sums, a scan of
+// the block sums by one block, per-block scans); Src::get(i) is entry i's count,
+// Dst::put(i, off) stores its offset, and bsum[nb] receives the total.
+
+struct AggCnt4 {
+    AggSlot<4> *s;
+    __device__ uint64_t get(uint64_t i) const { return s[i].cnt; }
+    // offset in the low half of the 64-bit field, the list's fill position (0) in the high half
+    __device__ void put(uint64_t i, uint64_t off) const { s[i].suma = (uint32_t)off; }
+};
+struct AggCnt8 {
+    AggSlot<8> *s;
+    __device__ uint64_t get(uint64_t i) const { return s[i].cnt; }
+    __device__ void put(uint64_t i, uint64_t off) const {
+        s[i].suma = off;
+        s[i].pad = 0;
+    }
+};
+struct Big {
+    unsigned long long off, cnt, s;
+};
+struct SegCnt {
+    const Big *b;
+    unsigned long long *pref;
+    __device__ uint64_t get(uint64_t i) const { return (b[i].cnt + kSegPairs - 1) / kSegPairs; }
+    __device__ void put(uint64_t i, uint64_t off) const { pref[i] = off; }
+};
+
+// Exclusive block-wide scan of one value per thread (kScanThreads threads).
+__device__ __forceinline__ uint64_t block_excl_scan(uint64_t v, uint64_t *total) {
+    __shared__ unsigned long long ws[32];
+    const unsigned lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    uint64_t x = v;
+#pragma unroll
+    for (int d = 1; d < 32; d <<= 1) {
+        const uint64_t y = __shfl_up_sync(0xffffffffu, x, d);
+        if (lane >= (unsigned)d) x += y;
+    }
+    if (lane == 31) ws[warp] = x;
+    __syncthreads();
+    if (warp == 0) {
+        uint64_t w = lane < (blockDim.x >> 5) ? ws[lane] : 0;
+#pragma unroll
+        for (int d = 1; d < 32; d <<= 1) {
+            const uint64_t y = __shfl_up_sync(0xffffffffu, w, d);
+            if (lane >= (unsigned)d) w += y;
+        }
+        ws[lane] = w;
+    }
+    __syncthreads();
+    const uint64_t before = (warp ? ws[warp - 1] : 0) + x - v;
+    *total = ws[31];
+    __syncthreads();  // ws is reused by the next call
+    return before;
+}
+
+template <class Src>
+__global__ void __launch_bounds__(kScanThreads) kl_block_sums(Src src, uint64_t n, unsigned long long *bsum) {
+    const uint64_t i0 = blockIdx.x * kScanBlock + 2 * threadIdx.x;
+    const uint64_t v = (i0 < n ? src.get(i0) : 0) + (i0 + 1 < n ? src.get(i0 + 1) : 0);
+    uint64_t tot;
+    block_excl_scan(v, &tot);
+    if (threadIdx.x == 0) bsum[blockIdx.x] = tot;
+}
+
+__global__ void __launch_bounds__(kScanThreads) kl_scan_sums(unsigned long long *bsum, uint64_t nb) {
+    uint64_t carry = 0;
+    for (uint64_t b0 = 0; b0 < nb; b0 += kScanThreads) {
+        const uint64_t i = b0 + threadIdx.x;
+        const uint64_t v = i < nb ? bsum[i] : 0;
+        uint64_t tot;
+        const uint64_t x = block_excl_scan(v, &tot);
+        if (i < nb) bsum[i] = carry + x;
+        carry += tot;
+    }
+    if (threadIdx.x == 0) bsum[nb] = carry;
+}
+
+template <class Src, class Dst>
+__global__ void __launch_bounds__(kScanThreads) kl_apply(Src src, Dst dst, uint64_t n, const unsigned long long *bsum) {
+    const uint64_t i0 = blockIdx.x * kScanBlock + 2 * threadIdx.x;
+    const uint64_t a = i0 < n ? src.get(i0) : 0, b = i0 + 1 < n ? src.get(i0 + 1) : 0;
+    uint64_t tot;
+    const uint64_t x = bsum[blockIdx.x] + block_excl_scan(a + b, &tot);
+    if (i0 < n) dst.put(i0, x);
+    if (i0 + 1 < n) dst.put(i0 + 1, x + a);
+}
+
+template <class Src, class Dst>
+hj_status scan_entries(hj_ctx *c, Src src, Dst dst, uint64_t n, uint64_t *total_host) {
+    const uint64_t nb = (n + kScanBlock - 1) / kScanBlock;
+    DevBuf bsum(c);
+    HJ_TRY(bsum.alloc((nb + 1) * 8));
+    if (nb) {
+        HJ_LAUNCH(c, "keylist_scan", kl_block_sums<Src>, (unsigned)nb, kScanThreads, 0, src, n,
+                  bsum.as<unsigned long long>());
+        HJ_LAUNCH(c, "keylist_scan", kl_scan_sums, 1, kScanThreads, 0, bsum.as<unsigned long long>(), nb);
+        HJ_LAUNCH(c, "keylist_scan", (kl_apply<Src, Dst>), (unsigned)nb, kScanThreads, 0, src, dst, n,
+                  bsum.as<unsigned long long>());
+    } else {
+        HJ_CUDA(c, cudaMemsetAsync(bsum.p, 0, 8, c->stream));
+    }
+    if (total_host) {
+        HJ_CUDA(c, cudaMemcpyAsync(total_host, bsum.as<unsigned long long>() + nb, 8, cudaMemcpyDeviceToHost,
+                                   c->stream));
+        HJ_CUDA(c, cudaStreamSynchronize(c->stream));
+    }
+    return HJ_OK;
+}
+
+// --------------------------------------------------------------- build
+// Every kept R tuple's rid into its key's list.
+template <int W>
+__global__ void __launch_bounds__(256) kl_scatter(const void *R, uint64_t n, AggSlot<W> *slots, uint64_t cap,
+                                                  TableSide *side, typename Tup<W>::U *rids, hj_counters *ctr,
+                                                  PartFilter pf) {
+    using U = typename Tup<W>::U;
+    constexpr int PV = Tup<W>::kPerVec;
+    const uint64_t nv = (n + PV - 1) / PV;
+    for (uint64_t v = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; v < nv; v += (uint64_t)gridDim.x * blockDim.x) {
+        U k[2], r[2];
+        kl_load<W>(R, v, n, k, r);
+#pragma unroll
+        for (int e = 0; e < PV; ++e) {
+            if (v * PV + e >= n) continue;
+            const uint64_t h = key_hash<W>(k[e]);
+            if (!pf.keep(h)) continue;
+            if (k[e] == Tup<W>::kAllOnes) {
+                rids[n - 1 - atomicAdd(&side->n_allones, 1ull)] = r[e];
+                continue;
+            }
+            const uint64_t b = kl_find<W>(slots, cap, k[e], h);
+            if (b == cap) {  // cannot happen: step 1 inserted every kept key
+                atomicOr(&ctr->status, (unsigned long long)kStatusTableFull);
+                continue;
+            }
+            uint64_t at;
+            if constexpr (W == 4) {
+                unsigned *half = (unsigned *)&slots[b].suma;  // [0] offset, [1] fill position
+                at = half[0] + atomicAdd(&half[1], 1u);
+            } else {
+                at = slots[b].suma + atomicAdd(&slots[b].pad, 1ull);
+            }
+            rids[at] = r[e];
+        }
+    }
+}
+
+// --------------------------------------------------------------- probe
+template <int W>
+__global__ void __launch_bounds__(256) kl_probe(const void *S, uint64_t ns, const AggSlot<W> *slots, uint64_t cap,
+                                                const TableSide *side, const typename Tup<W>::U *rids, uint64_t nr,
+                                                void *pairs, uint64_t pcap, hj_counters *ctr, int chk, PartFilter pf,
+                                                Big *big, unsigned long long *nbig) {
+    using U = typename Tup<W>::U;
+    constexpr int PV = Tup<W>::kPerVec;
+    const unsigned lane = threadIdx.x & 31;
+    const uint64_t warp = (blockIdx.x * (uint64_t)blockDim.x + threadIdx.x) >> 5;
+    const uint64_t nwarps = ((uint64_t)gridDim.x * blockDim.x) >> 5;
+    const uint64_t nv = (ns + PV - 1) / PV;
+    OutState st;
+    const OutCtx oc{pairs, pcap, ctr, 0u, true};
+    unsigned long long c0 = 0, c1 = 0;
+    const uint64_t allones = side->agg_cnt;
+    for (uint64_t v0 = warp * 32; v0 < nv; v0 += nwarps * 32) {
+        const uint64_t v = v0 + lane;
+        U k[2] = {0, 0}, r[2] = {0, 0};
+        if (v < nv) kl_load<W>(S, v, ns, k, r);
+#pragma unroll
+        for (int e = 0; e < PV; ++e) {
+            uint64_t cnt = 0, off = 0;
+            if (v < nv && v * PV + e < ns) {
+                const uint64_t h = key_hash<W>(k[e]);
+                if (pf.keep(h)) {
+                    if (k[e] == Tup<W>::kAllOnes) {
+                        cnt = allones;
+                        off = nr - allones;
+                    } else {
+                        const uint64_t b = kl_find<W>(slots, cap, k[e], h);
+                        if (b < cap) {
+                            cnt = slots[b].cnt;
+                            off = W == 4 ? (uint32_t)slots[b].suma : slots[b].suma;
+                        }
+                    }
+                }
+            }
+            const U s = r[e];
+            // one match
+            const bool one = cnt == 1;
+            const U a = one ? rids[off] : U(0);
+            if (chk && one) {
+                const uint64_t A = mix_a(a), B = mix_b(s);
+                c0 += A * B;
+                c1 += A + B;
+            }
+            warp_append<W>(st, oc, one, a, s);
+            // a heavy hitter: expanded by the grid afterwards
+            if (cnt > kCoopPairs) {
+                const unsigned long long i = atomicAdd(nbig, 1ull);
+                big[i] = Big{off, cnt, (unsigned long long)s};  // at most one entry per probe tuple
+            }
+            // a short list: the whole warp, 32 pairs per step
+            unsigned coop = __ballot_sync(0xffffffffu, cnt > 1 && cnt <= kCoopPairs);
+            while (coop) {
+                const int L = __ffs(coop) - 1;
+                coop &= coop - 1;
+                const uint64_t o = __shfl_sync(0xffffffffu, off, L), n = __shfl_sync(0xffffffffu, cnt, L);
+                const U ss = __shfl_sync(0xffffffffu, s, L);
+                for (uint64_t j0 = 0; j0 < n; j0 += 32) {
+                    const bool has = j0 + lane < n;
+                    const U ra = has ? rids[o + j0 + lane] : U(0);
+                    if (chk && has) {
+                        const uint64_t A = mix_a(ra), B = mix_b(ss);
+                        c0 += A * B;
+                        c1 += A + B;
+                    }
+                    warp_append<W>(st, oc, has, ra, ss);
+                }
+            }
+        }
+    }
+    c0 = warp_sum(c0);
+    c1 = warp_sum(c1);
+    if (lane == 0) {
+        if (c0) atomicAdd(&ctr->c0, c0);
+        if (c1) atomicAdd(&ctr->c1, c1);
+    }
+}
+
+// Segment g of the heavy hitters' pairs: its entry (the last with pref <= g), rows
+// claimed from ctr->count by the CTA, pairs written by all its threads.
+template <int W>
+__global__ void __launch_bounds__(256) kl_expand(const Big *big, const unsigned long long *pref, uint64_t nbig,
+                                                 uint64_t nseg, const typename Tup<W>::U *rids, void *pairs,
+                                                 uint64_t pcap, hj_counters *ctr, int chk) {
+    using U = typename Tup<W>::U;
+    using P = typename PairVec<W>::T;
+    __shared__ unsigned long long s_base;
+    unsigned long long c0 = 0, c1 = 0;
+    for (uint64_t g = blockIdx.x; g < nseg; g += gridDim.x) {
+        uint64_t lo = 0, hi = nbig;  // pref[lo] <= g < pref[hi], with pref[nbig] read as nseg
+        while (hi - lo > 1) {
+            const uint64_t mid = (lo + hi) >> 1;
+            if (pref[mid] <= g) lo = mid;
+            else hi = mid;
+        }
+        const Big b = big[lo];
+        const uint64_t j0 = (g - pref[lo]) * kSegPairs;
+        const uint64_t len = b.cnt - j0 < kSegPairs ? b.cnt - j0 : kSegPairs;
+        if (threadIdx.x == 0) s_base = atomicAdd(&ctr->count, (unsigned long long)len);
+        __syncthreads();
+        const unsigned long long base = s_base;
+        const U s = (U)b.s;
+        const uint64_t B = chk ? mix_b(s) : 0;
+        for (uint64_t i = threadIdx.x; i < len; i += blockDim.x) {
+            const U a = rids[b.off + j0 + i];
+            if (base + i < pcap) {
+                if constexpr (W == 4) ((P *)pairs)[base + i] = make_uint2(a, s);
+                else ((P *)pairs)[base + i] = make_ulonglong2(a, s);
+            }
+            if (chk) {
+                const uint64_t A = mix_a(a);
+                c0 += A * B;
+                c1 += A + B;
+            }
+        }
+        __syncthreads();  // s_base is rewritten for the next segment
+    }
+    c0 = warp_sum(c0);
+    c1 = warp_sum(c1);
+    if ((threadIdx.x & 31) == 0) {
+        if (c0) atomicAdd(&ctr->c0, c0);
+        if (c1) atomicAdd(&ctr->c1, c1);
+    }
+}
+
+}  // namespace
+
+hj_status keylist_build(hj_ctx *c, int width, const void *R, uint64_t n, PartFilter pf, hj_table **out) {
+    *out = nullptr;
+    DevBuf rids(c);
+    hj_table *t = nullptr;
+    HJ_TRY(table_create(c, width, 1, n, &t));
+    struct Guard {
+        hj_ctx *c;
+        hj_table *t;
+        ~Guard() {
+            if (t) table_destroy(c, t);
+        }
+    } g{c, t};
+    HJ_TRY(table_build(c, t, R, 0, n, n, pf));
+    if (width == 4) HJ_TRY(scan_entries(c, AggCnt4{(AggSlot<4> *)t->slots}, AggCnt4{(AggSlot<4> *)t->slots}, t->cap, nullptr));
+    else HJ_TRY(scan_entries(c, AggCnt8{(AggSlot<8> *)t->slots}, AggCnt8{(AggSlot<8> *)t->slots}, t->cap, nullptr));
+    HJ_TRY(rids.alloc((n ? n : 1) * (uint64_t)width));
+    const uint64_t nv = (n + 1) / (width == 4 ? 2 : 1);
+    const unsigned grid = (unsigned)std::min<uint64_t>((nv + 255) / 256 + 1, (uint64_t)num_sms(c) * 8);
+    if (width == 4)
+        HJ_LAUNCH(c, "keylist_scatter", kl_scatter<4>, grid, 256, 0, R, n, (AggSlot<4> *)t->slots, t->cap,
+                  (TableSide *)t->side, (uint32_t *)rids.p, c->d_ctr, pf);
+    else
+        HJ_LAUNCH(c, "keylist_scatter", kl_scatter<8>, grid, 256, 0, R, n, (AggSlot<8> *)t->slots, t->cap,
+                  (TableSide *)t->side, (uint64_t *)rids.p, c->d_ctr, pf);
+    t->agg = 0;  // a table for pairs, whatever its slots
+    t->keylist = 1;
+    t->rids = rids.release();
+    t->nr = n;
+    *out = t;
+    g.t = nullptr;
+    return HJ_OK;
+}
+
+hj_status keylist_probe(hj_ctx *c, const hj_table *t, const void *S, uint64_t ns, PartFilter pf, void *pairs,
+                        uint64_t pcap, hj_counters *ctr, int chk) {
+    if (!ns) return HJ_OK;
+    const int W = t->width;
+    const void *rids = t->rids;
+    const uint64_t nr = t->nr;
+    DevBuf big(c), nbig(c), pref(c);
+    HJ_TRY(big.alloc(ns * sizeof(Big)));
+    HJ_TRY(nbig.alloc(8));
+    HJ_CUDA(c, cudaMemsetAsync(nbig.p, 0, 8, c->stream));
+    const uint64_t nv = (ns + 1) / (W == 4 ? 2 : 1);
+    const unsigned grid = (unsigned)std::min<uint64_t>((nv + 255) / 256 + 1, (uint64_t)num_sms(c) * 8);
+    if (W == 4)
+        HJ_LAUNCH(c, "keylist_probe", kl_probe<4>, grid, 256, 0, S, ns, (const AggSlot<4> *)t->slots, t->cap,
+                  (const TableSide *)t->side, (const uint32_t *)rids, nr, pairs, pcap, ctr, chk, pf, big.as<Big>(),
+                  nbig.as<unsigned long long>());
+    else
+        HJ_LAUNCH(c, "keylist_probe", kl_probe<8>, grid, 256, 0, S, ns, (const AggSlot<8> *)t->slots, t->cap,
+                  (const TableSide *)t->side, (const uint64_t *)rids, nr, pairs, pcap, ctr, chk, pf, big.as<Big>(),
+                  nbig.as<unsigned long long>());
+    uint64_t nb = 0;
+    HJ_CUDA(c, cudaMemcpyAsync(&nb, nbig.p, 8, cudaMemcpyDeviceToHost, c->stream));
+    HJ_CUDA(c, cudaStreamSynchronize(c->stream));
+    if (!nb) return HJ_OK;
+    // heavy hitters: segments of kSegPairs pairs over the whole grid
+    HJ_TRY(pref.alloc((nb + 1) * 8));
+    uint64_t nseg = 0;
+    HJ_TRY(scan_entries(c, SegCnt{big.as<Big>(), pref.as<unsigned long long>()},
+                        SegCnt{big.as<Big>(), pref.as<unsigned long long>()}, nb, &nseg));
+    const unsigned eg = (unsigned)std::min<uint64_t>(nseg, (uint64_t)num_sms(c) * 8);
+    if (W == 4)
+        HJ_LAUNCH(c, "keylist_expand", kl_expand<4>, eg, 256, 0, big.as<Big>(), pref.as<unsigned long long>(), nb,
+                  nseg, (const uint32_t *)rids, pairs, pcap, ctr, chk);
+    else
+        HJ_LAUNCH(c, "keylist_expand", kl_expand<8>, eg, 256, 0, big.as<Big>(), pref.as<unsigned long long>(), nb,
+                  nseg, (const uint64_t *)rids, pairs, pcap, ctr, chk);
+    return HJ_OK;  // the buffers are freed in stream order after the expansion
+}
+
+}  // namespace hj

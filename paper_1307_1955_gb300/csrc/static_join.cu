@@ -28,13 +28,18 @@ struct StaticHeader {
 };
 static_assert(sizeof(StaticHeader) <= kHeaderBytes, "header does not fit");
 
+constexpr uint64_t kStaticMaxWalk = 1ull << 16;  // longest insert walk of the static table
+
 template <int W>
 __global__ void static_build_kernel(const void *R, uint64_t n, void *slots, uint64_t cap, StaticHeader *hdr) {
     using U = typename Tup<W>::U;
     for (uint64_t t = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; t < n; t += (uint64_t)gridDim.x * blockDim.x) {
         const U k = ((const U *)R)[2 * t], r = ((const U *)R)[2 * t + 1];
-        if (!pair_insert<W>((typename PairSlot<W>::S *)slots, cap, &hdr->side, k, r, key_hash<W>(k)))
-            atomicOr(&hdr->ctr.status, (unsigned long long)kStatusTableFull);
+        // (no key-list form here: a longer walk bound than the library's joins, so
+        // that keys repeated some thousand times still work)
+        if (!pair_insert<W>((typename PairSlot<W>::S *)slots, cap, &hdr->side, k, r, key_hash<W>(k), kStaticMaxWalk))
+            atomicOr(&hdr->ctr.status,
+                     (unsigned long long)(cap <= kStaticMaxWalk ? kStatusTableFull : kStatusLongRun));
     }
 }
 
@@ -191,6 +196,7 @@ extern "C" hj_status hj_join_static(const hj_rel *R, const hj_rel *S, void *cuda
         return HJ_E_CUDA;
     }
     if (h.status & kStatusTableFull) return HJ_E_CUDA;
+    if (h.status & kStatusLongRun) return HJ_E_UNSUPPORTED;  // a key repeated too often for this table
     *count = h.count;
     if (checksum) {
         checksum[0] = h.c0;

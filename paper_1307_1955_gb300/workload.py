@@ -140,6 +140,33 @@ def unique_and_uniform(n_r: int, n_s: int, s_domain: int, seed: int, device, wid
     return make_relation(rk, rr, width), make_relation(sk, sr, width)
 
 
+def heavy_hitter(n_r: int, n_s: int, s: float, seed: int, device, width: int = 4, ids: tuple = (),
+                 heavy_key: int = 1):
+    """The paper's skewed data sets (Sec. 5.1: a fraction s of the tuples share one
+    duplicated key value), read as: round(s |R|) R tuples carry one key, the heavy
+    hitter (`heavy_key`, an unsigned value; 1 by default), and the other R tuples
+    the distinct keys 2 .. |R| - round(s |R|) + 1, in a seeded order.  S keys are
+    uniform over R's distinct keys, so a few S tuples meet the heavy hitter and
+    every other S tuple exactly one R tuple.  rids are row indices."""
+    nh = int(round(s * n_r))
+    if not 0 < nh <= n_r:
+        raise ValueError("s * |R| must round to between 1 and |R| tuples")
+    pr = stream_id(seed, *ids, 1)
+    ps = stream_id(seed, *ids, 2)
+    p = permutation(n_r, pr, device)
+    hk = torch.full_like(p, _s64(heavy_key))
+    rk = torch.where(p < nh, hk, p - nh + 2)
+    nd = n_r - nh + 1  # distinct R keys: the heavy hitter (drawn as 1) and 2 .. n_r - nh + 1
+    if n_s:
+        sk = uniform_below(nd, ps, n_s, device) + 1
+        sk = torch.where(sk == 1, torch.full_like(sk, _s64(heavy_key)), sk)
+    else:
+        sk = torch.zeros(0, dtype=torch.int64, device=device)
+    rr = torch.arange(n_r, dtype=torch.int64, device=device)
+    sr = torch.arange(n_s, dtype=torch.int64, device=device)
+    return make_relation(rk, rr, width), make_relation(sk, sr, width)
+
+
 def zipf_cdf(n_ranks: int, theta: float) -> torch.Tensor:
     """CPU float64 CDF of P(rank = k) proportional to k^-theta, k = 1..n_ranks (last entry 1.0)."""
     k = torch.arange(1, n_ranks + 1, dtype=torch.float64)

@@ -62,6 +62,27 @@ def test_unique_and_uniform_structure():
     assert torch.equal(R, R2) and torch.equal(S, S2)
 
 
+@pytest.mark.parametrize("width,hk", [(4, 1), (4, 0xFFFFFFFF), (8, (1 << 64) - 1)])
+def test_heavy_hitter_structure(width, hk):
+    # round(s |R|) R tuples share the heavy key, the rest are distinct, S keys are
+    # uniform over R's distinct keys (the heavy key among them)
+    n_r, n_s, s = 4000, 30000, 0.25
+    R, S = W.heavy_hitter(n_r, n_s, s, 9, "cpu", width=width, heavy_key=hk)
+    r, q = W.to_numpy_u(R), W.to_numpy_u(S)
+    nh = int(round(s * n_r))
+    heavy = r[:, 0] == np.array(hk, dtype=r.dtype)
+    assert heavy.sum() == nh
+    others = np.sort(r[~heavy, 0])
+    assert np.array_equal(others, np.arange(2, n_r - nh + 2, dtype=r.dtype))
+    assert np.array_equal(r[:, 1], np.arange(n_r, dtype=r.dtype))
+    assert np.isin(q[:, 0], r[:, 0]).all()
+    # the heavy key gets its share 1 / (n_r - nh + 1) of S
+    frac = np.mean(q[:, 0] == np.array(hk, dtype=q.dtype))
+    assert abs(frac - 1.0 / (n_r - nh + 1)) < 0.002
+    R2, S2 = W.heavy_hitter(n_r, n_s, s, 9, "cpu", width=width, heavy_key=hk)
+    assert torch.equal(R, R2) and torch.equal(S, S2)
+
+
 def test_u64_relation_bit_patterns():
     keys = torch.tensor([0, -1, 1 << 40], dtype=torch.int64)
     rel = W.make_relation(keys, torch.arange(3), 8)
