@@ -7,7 +7,7 @@
 // distinct key one entry whose rid list holds all of its build tuples' rids.
 // Here that is the aggregate table (one slot per distinct key with its count)
 // plus one array of rids:
-//   1. build the aggregate table over R (counts);
+//   1. insert every kept key of R into the aggregate table with its count;
 //   2. an exclusive scan of the counts gives each key the offset of its rid list;
 //   3. a second pass over R places every rid in its key's list (a per-key fill
 //      position claimed by atomicAdd; the order inside a list is free).
@@ -175,39 +175,100 @@ hj_status scan_entries(hj_ctx *c, Src src, Dst dst, uint64_t n, uint64_t *total_
 }
 
 // --------------------------------------------------------------- build
-// Every kept R tuple's rid into its key's list.
+// Lanes of a warp holding the same kept key act as one: the lowest takes the
+// group's count in one atomic (a heavy hitter has many copies in every warp, and
+// one atomic per copy on one address would serialise the build).
+__device__ __forceinline__ unsigned lanes_lt() { return (1u << (threadIdx.x & 31)) - 1u; }
+
+// Step 1: every kept key in the table (CAS on the key), its count added.
+template <int W>
+__global__ void __launch_bounds__(256) kl_count(const void *R, uint64_t n, AggSlot<W> *slots, uint64_t cap,
+                                                TableSide *side, hj_counters *ctr, PartFilter pf) {
+    using U = typename Tup<W>::U;
+    constexpr int PV = Tup<W>::kPerVec;
+    const unsigned lane = threadIdx.x & 31;
+    const uint64_t warp = (blockIdx.x * (uint64_t)blockDim.x + threadIdx.x) >> 5;
+    const uint64_t nwarps = ((uint64_t)gridDim.x * blockDim.x) >> 5;
+    const uint64_t nv = (n + PV - 1) / PV;
+    for (uint64_t v0 = warp * 32; v0 < nv; v0 += nwarps * 32) {  // warp-uniform: every lane takes part
+        const uint64_t v = v0 + lane;
+        U k[2] = {0, 0}, r[2] = {0, 0};
+        if (v < nv) kl_load<W>(R, v, n, k, r);
+#pragma unroll
+        for (int e = 0; e < PV; ++e) {
+            const uint64_t h = key_hash<W>(k[e]);
+            const bool ok = v < nv && v * PV + e < n && pf.keep(h);
+            const unsigned g = __match_any_sync(0xffffffffu, k[e]) & __ballot_sync(0xffffffffu, ok);
+            if (!ok || (g & lanes_lt())) continue;  // the group's lowest lane counts for it
+            const unsigned m = __popc(g);
+            if (k[e] == Tup<W>::kAllOnes) {
+                atomicAdd(&side->agg_cnt, (unsigned long long)m);
+                continue;
+            }
+            uint64_t b = bucket_of<W>(h, cap);
+            bool done = false;
+            for (uint64_t it = 0; it < cap && !done; ++it) {
+                const U old = cas_key<W>((U *)&slots[b].key, Tup<W>::kAllOnes, k[e]);
+                if (old == Tup<W>::kAllOnes || old == k[e]) {
+                    add_cnt(&slots[b].cnt, (decltype(slots[b].cnt))m);
+                    done = true;
+                } else if (++b == cap) {
+                    b = 0;
+                }
+            }
+            if (!done) atomicOr(&ctr->status, (unsigned long long)kStatusTableFull);
+        }
+    }
+}
+
+// Step 3: every kept R tuple's rid into its key's list.
 template <int W>
 __global__ void __launch_bounds__(256) kl_scatter(const void *R, uint64_t n, AggSlot<W> *slots, uint64_t cap,
                                                   TableSide *side, typename Tup<W>::U *rids, hj_counters *ctr,
                                                   PartFilter pf) {
     using U = typename Tup<W>::U;
     constexpr int PV = Tup<W>::kPerVec;
+    const unsigned lane = threadIdx.x & 31;
+    const uint64_t warp = (blockIdx.x * (uint64_t)blockDim.x + threadIdx.x) >> 5;
+    const uint64_t nwarps = ((uint64_t)gridDim.x * blockDim.x) >> 5;
     const uint64_t nv = (n + PV - 1) / PV;
-    for (uint64_t v = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; v < nv; v += (uint64_t)gridDim.x * blockDim.x) {
-        U k[2], r[2];
-        kl_load<W>(R, v, n, k, r);
+    for (uint64_t v0 = warp * 32; v0 < nv; v0 += nwarps * 32) {
+        const uint64_t v = v0 + lane;
+        U k[2] = {0, 0}, r[2] = {0, 0};
+        if (v < nv) kl_load<W>(R, v, n, k, r);
 #pragma unroll
         for (int e = 0; e < PV; ++e) {
-            if (v * PV + e >= n) continue;
             const uint64_t h = key_hash<W>(k[e]);
-            if (!pf.keep(h)) continue;
-            if (k[e] == Tup<W>::kAllOnes) {
-                rids[n - 1 - atomicAdd(&side->n_allones, 1ull)] = r[e];
-                continue;
+            const bool ok = v < nv && v * PV + e < n && pf.keep(h);
+            const unsigned g = __match_any_sync(0xffffffffu, k[e]) & __ballot_sync(0xffffffffu, ok);
+            const int leader = g ? __ffs(g) - 1 : 0;
+            // the leader claims the group's places: [at, at + popc(g)) of the key's
+            // list, or of the all-ones keys' list counted down from the array's end
+            uint64_t at = 0;
+            bool fail = false;
+            if (ok && lane == (unsigned)leader) {
+                const uint64_t m = __popc(g);
+                if (k[e] == Tup<W>::kAllOnes) {
+                    at = atomicAdd(&side->n_allones, (unsigned long long)m);
+                } else {
+                    const uint64_t b = kl_find<W>(slots, cap, k[e], h);
+                    if (b == cap) {  // cannot happen: step 1 inserted every kept key
+                        fail = true;
+                    } else if constexpr (W == 4) {
+                        unsigned *half = (unsigned *)&slots[b].suma;  // [0] offset, [1] fill position
+                        at = half[0] + atomicAdd(&half[1], (unsigned)m);
+                    } else {
+                        at = slots[b].suma + atomicAdd(&slots[b].pad, (unsigned long long)m);
+                    }
+                }
+                if (fail) atomicOr(&ctr->status, (unsigned long long)kStatusTableFull);
             }
-            const uint64_t b = kl_find<W>(slots, cap, k[e], h);
-            if (b == cap) {  // cannot happen: step 1 inserted every kept key
-                atomicOr(&ctr->status, (unsigned long long)kStatusTableFull);
-                continue;
-            }
-            uint64_t at;
-            if constexpr (W == 4) {
-                unsigned *half = (unsigned *)&slots[b].suma;  // [0] offset, [1] fill position
-                at = half[0] + atomicAdd(&half[1], 1u);
-            } else {
-                at = slots[b].suma + atomicAdd(&slots[b].pad, 1ull);
-            }
-            rids[at] = r[e];
+            at = __shfl_sync(0xffffffffu, at, leader);
+            fail = __shfl_sync(0xffffffffu, fail, leader);
+            if (!ok || fail) continue;
+            const uint64_t rank = __popc(g & lanes_lt());
+            if (k[e] == Tup<W>::kAllOnes) rids[n - 1 - (at + rank)] = r[e];
+            else rids[at + rank] = r[e];
         }
     }
 }
@@ -354,7 +415,16 @@ hj_status keylist_build(hj_ctx *c, int width, const void *R, uint64_t n, PartFil
             if (t) table_destroy(c, t);
         }
     } g{c, t};
-    HJ_TRY(table_build(c, t, R, 0, n, n, pf));
+    {
+        const uint64_t nv = (n + 1) / (width == 4 ? 2 : 1);
+        const unsigned grid = (unsigned)std::min<uint64_t>((nv + 255) / 256 + 1, (uint64_t)num_sms(c) * 8);
+        if (width == 4)
+            HJ_LAUNCH(c, "keylist_count", kl_count<4>, grid, 256, 0, R, n, (AggSlot<4> *)t->slots, t->cap,
+                      (TableSide *)t->side, c->d_ctr, pf);
+        else
+            HJ_LAUNCH(c, "keylist_count", kl_count<8>, grid, 256, 0, R, n, (AggSlot<8> *)t->slots, t->cap,
+                      (TableSide *)t->side, c->d_ctr, pf);
+    }
     if (width == 4) HJ_TRY(scan_entries(c, AggCnt4{(AggSlot<4> *)t->slots}, AggCnt4{(AggSlot<4> *)t->slots}, t->cap, nullptr));
     else HJ_TRY(scan_entries(c, AggCnt8{(AggSlot<8> *)t->slots}, AggCnt8{(AggSlot<8> *)t->slots}, t->cap, nullptr));
     HJ_TRY(rids.alloc((n ? n : 1) * (uint64_t)width));
