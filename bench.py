@@ -46,7 +46,7 @@ WORKLOADS = {
              "R keys a permutation of 1..|R|, S keys uniform over [1, ceil(|R|/0.75)] (75% match); pairs "
              "materialised; one hj_join_batch call (CUDA graph per wave) per step vs one hj_join per join"),
     "serve_20000": dict(
-        kind="serve", nreq=20000, nr=0, ns=0, algo=0, budget=120 << 30, load=0.7,
+        kind="serve", nreq=20000, nr=0, ns=0, algo=0, budget=120 << 30, load=0.7, sweep=(0.5, 0.9),
         desc="serving: 20000 join requests, Poisson arrivals, |R| log-uniform in [2^12, 2^24], |S| log-uniform "
              "in [|R|, 16|R|] (uint32 key, uint32 rid), R keys a permutation of 1..|R|, S keys uniform over "
              "[1, 2|R|] (50% match), pairs materialised; HBM admission budget 120 GiB"),
@@ -829,6 +829,13 @@ def run_serve(args, wl, ws, rank, local):
         rate = wl["load"] * sat / (total / n)
         arrivals = [sp.arrival_s / rate for sp in specs]
         span_l, lat_l, bad_l = stream(srv, arrivals)
+        # the same stream at lighter and heavier offered loads
+        sweep = []
+        for ld in wl.get("sweep", ()):
+            r_ = ld * sat / (total / n)
+            span_x, lat_x, bad_x = stream(srv, [sp.arrival_s / r_ for sp in specs])
+            sweep.append({"load": ld, "offered_req_per_s": r_, "tuples_per_s": total / span_x, "span_s": span_x,
+                          "p50_ms": 1000 * pct(lat_x, 0.5), "p99_ms": 1000 * pct(lat_x, 0.99), "mismatches": bad_x})
         st = srv.stats()
     # one hj_join per request, one stream, same requests (bounded to ~20 s)
     t0 = time.perf_counter()
@@ -863,6 +870,7 @@ def run_serve(args, wl, ws, rank, local):
             "at_load": {"load": wl["load"], "offered_req_per_s": rate, "tuples_per_s": total / span_l,
                         "span_s": span_l, "p50_ms": 1000 * pct(lat_l, 0.5), "p99_ms": 1000 * pct(lat_l, 0.99),
                         "mismatches": bad_l},
+            "load_sweep": sweep,
             "plain": {"value": plain, "unit": UNIT, "api": "hj_join once per request, one stream"},
             "served_vs_plain": sat / plain,
             "server": st,
