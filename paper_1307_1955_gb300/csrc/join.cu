@@ -376,59 +376,20 @@ hj_status table_probe(hj_ctx *c, const hj_table *t, const void *S, uint64_t lo, 
 
 // ================================================== per-partition join (PHJ)
 //
-// Persistent CTAs take partition pairs (R_p, S_p) from ctr->work.  For each, the
-// CTA builds a table over R_p in shared memory (capacity about twice |R_p|,
-// multiply-shift buckets so any capacity works), then its warps stream S_p.
-// Partitions come from the padded partitioner: every partition starts and ends on
-// a 32-byte sector, so whole 16-byte vectors can be loaded without bounds checks
-// on tuples, and padding tuples are dropped by the partition test (PartFilter).
-// A partition whose table cannot fit (|R_p| too large for a pair table, or more
-// distinct keys than slots for an aggregate table) goes to the host's
-// global-table fallback list.
+// Persistent CTAs take partition tasks (R_p with a slice of S_p) from ctr->work.
+// For each, the CTA builds a table over R_p in shared memory (about three slots
+// per build row, multiply-shift buckets so any capacity works), then its warps
+// stream the S slice.  Partitions come from the padded partitioner: every
+// partition starts and ends on a 32-byte sector, so whole 16-byte vectors can be
+// loaded without bounds checks on tuples, and padding tuples (keys of another
+// partition) match nothing.  A partition whose table cannot fit (|R_p| too large
+// for a pair table, more distinct keys than slots for an aggregate table, or an
+// insert walking past kMaxSmemWalk buckets: a heavily repeated key) goes to the
+// host's fallback list, joined there with a global key-list table (pairs) or
+// aggregate table (counts).
 
 template <int W> struct HashT { using type = uint32_t; };
 template <> struct HashT<8> { using type = uint64_t; };
-
-// Bucket of a shared-memory table; equal to bucket_of<W> for cap < 2^32.
-template <int W> __device__ __forceinline__ uint32_t sbucket(typename HashT<W>::type h, uint32_t cap);
-template <> __device__ __forceinline__ uint32_t sbucket<4>(uint32_t h, uint32_t cap) { return __umulhi(h, cap); }
-template <> __device__ __forceinline__ uint32_t sbucket<8>(uint64_t h, uint32_t cap) {
-    return (uint32_t)__umul64hi(h, (uint64_t)cap);
-}
-
-// A shared-memory table bucket: 32 aligned bytes, read with two 16-byte loads --
-// four slots of 4-byte tuples or two slots of 8-byte tuples.
-template <int W> struct SmemBucket {
-    static constexpr uint32_t kSlots = 32 / (2 * W);
-    ulonglong2 a, b;
-    __device__ __forceinline__ void load(uint32_t base, uint32_t bkt) {
-        const uint32_t addr = base + bkt * 32u;
-        asm volatile("ld.shared.v2.u64 {%0, %1}, [%2];" : "=l"(a.x), "=l"(a.y) : "r"(addr));
-        asm volatile("ld.shared.v2.u64 {%0, %1}, [%2];" : "=l"(b.x), "=l"(b.y) : "r"(addr + 16u));
-    }
-};
-
-template <int W> struct SmemPair;
-template <> struct SmemPair<4> {
-    static __device__ __forceinline__ unsigned long long ld(uint32_t base, uint32_t i) {
-        unsigned long long v;
-        asm volatile("ld.shared.u64 %0, [%1];" : "=l"(v) : "r"(base + i * 8u));
-        return v;
-    }
-    static __device__ __forceinline__ bool empty(unsigned long long s) { return s == ~0ull; }
-    static __device__ __forceinline__ uint32_t key(unsigned long long s) { return (uint32_t)s; }
-    static __device__ __forceinline__ uint32_t rid(unsigned long long s) { return (uint32_t)(s >> 32); }
-};
-template <> struct SmemPair<8> {
-    static __device__ __forceinline__ ulonglong2 ld(uint32_t base, uint32_t i) {
-        ulonglong2 v;
-        asm volatile("ld.shared.v2.u64 {%0, %1}, [%2];" : "=l"(v.x), "=l"(v.y) : "r"(base + i * 16u));
-        return v;
-    }
-    static __device__ __forceinline__ bool empty(ulonglong2 s) { return (s.x & s.y) == ~0ull; }
-    static __device__ __forceinline__ uint64_t key(ulonglong2 s) { return s.x; }
-    static __device__ __forceinline__ uint64_t rid(ulonglong2 s) { return s.y; }
-};
 
 // Bucket of a key inside a partition's shared-memory table: Fibonacci
 // multiply-shift of the key.  Keys of one partition already share their
