@@ -39,7 +39,7 @@ namespace {
 constexpr double kIptHist = 22.0;         // per input tuple (bandwidth-bound)
 constexpr double kIptScatterTma = 132.0;  // per input tuple, fan-out <= 2^11 (TMA-staged kernel)
 constexpr double kIptScatterWide = 293.0; // per input tuple, fan-out 2^12
-constexpr double kIptJoinProbe = 103.0;   // per S tuple, shared-memory table
+constexpr double kIptJoinProbe = 82.0;    // per S tuple, shared-memory table
 constexpr double kIptJoinBuild = 60.0;    // per R tuple, shared-memory table
 constexpr double kIptShjBuild = 40.0;     // per R tuple, global table
 constexpr double kIptShjProbe = 60.0;     // per S tuple, global table
@@ -47,7 +47,7 @@ constexpr double kIssueFraction = 0.55;   // sustained share of the issue slots
 constexpr double kCopyFraction = 0.83;    // share of nominal HBM bandwidth a copy reaches
 constexpr double kRandomFraction = 0.2;   // share for 32-byte random sectors (table probes)
 constexpr double kLaunchS = 4e-6;         // per kernel launch
-constexpr double kShjFixedS = 70e-6;      // per SHJ call: allocations, two host synchronisations
+constexpr double kShjFixedS = 55e-6;      // per SHJ call: table fill, allocations, one host synchronisation
 constexpr double kPhjFixedS = 170e-6;     // per PHJ call: allocations, two host synchronisations
 
 }  // namespace
@@ -92,7 +92,7 @@ double predict_seconds(const CostModel &m, int width, bool agg, bool mat, uint64
         const double rnd = b * kRandomFraction;
         s[2] = std::max(t * nR / b + cap * slot / b + (in_l2 ? 0.0 : 64.0 * nR / rnd), nR * kIptShjBuild / ir);
         s[3] = std::max((t * nS + o * M) / b + (in_l2 ? 0.0 : 32.0 * nS / rnd), nS * kIptShjProbe / ir);
-        s[3] += 8 * kLaunchS + kShjFixedS;
+        s[3] += 5 * kLaunchS + kShjFixedS;
     } else {
         const int b1 = passes == 2 ? bits - bits / 2 : bits, b2 = passes == 2 ? bits / 2 : 0;
         for (int p = 0; p < passes; ++p) {
