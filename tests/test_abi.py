@@ -45,6 +45,15 @@ def test_null_context_is_rejected_without_a_gpu(lib):
     assert lib.hj_last_error(None) == b"null context"
 
 
+def test_profiling_calls_reject_a_null_context_without_a_gpu(lib):
+    for name, args in (("hj_prof_enable", (None, 1)), ("hj_prof_only", (None, b"partition_join")),
+                       ("hj_prof_only", (None, None)), ("hj_prof_reset", (None,)),
+                       ("hj_prof_read", (None, None, 0, None))):
+        f = getattr(lib, name)
+        f.restype = ctypes.c_int32
+        assert f(*args) == 1, name  # HJ_E_INVALID
+
+
 def test_server_calls_reject_null_handles_without_a_gpu(lib):
     for name, args in (("hj_server_create", (None, None, None)), ("hj_server_submit", (None, None, None, 0, None)),
                        ("hj_server_poll", (None, 1, None, None)), ("hj_server_destroy", (None,)),
