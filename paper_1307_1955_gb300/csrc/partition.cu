@@ -908,6 +908,186 @@ static hj_status launch_region(hj_ctx *c, unsigned grid, const void *in, uint64_
     return HJ_OK;
 }
 
+// ------------------------------------------------------------- ring scatter
+// 4-byte tuples at 2^11 digits (the join's usual fan-out): the insert and flush
+// work of the region scatter split between warps that run at the same time, with
+// no barrier after the set-up.  Digit d owns a ring of kRingK slots (slot j at
+// ring[j * P + d], empty slots hold a key of another digit) and two cursors:
+// wr[d], positions claimed, and fl[d], positions flushed.
+//   * An insert warp streams its own blocks of the chunk.  A tuple claims position
+//     w = wr[d] by shared CAS while w - fl[d] < kRingK and stores itself in slot
+//     w mod kRingK; with the ring full it is written from the run's far end, as in
+//     the region scatter.
+//   * A flush warp owns a set of digits.  Once four claimed positions at fl[d]
+//     all hold tuples, it writes them as one 32-byte sector at the run's next
+//     sector, empties the slots, then advances fl[d] (release; inserters read fl
+//     with acquire, so a slot is refilled only after it was emptied).
+//   * When every insert warp is done (release / acquire on a counter) the flush
+//     warps write what is left of each ring, then padding, into the run's gap.
+// Every wait is bounded: a flush warp that passes kRingMaxPasses sets the timeout
+// bit of the status word and returns.
+constexpr int kRingThreads = 1024;
+constexpr int kRingFlushWarps = 8;
+constexpr uint32_t kRingK = 12;                    // three sectors per digit
+constexpr uint32_t kRingMaxClaim = 64;             // CAS attempts before the far-end path
+constexpr uint64_t kRingMaxPasses = 1ull << 22;    // flush passes before the timeout bit
+constexpr int kRingVec = 4;                        // 16-byte vectors per lane in flight
+
+template <int LOG2P> struct RingShape {
+    static constexpr uint32_t P = 1u << LOG2P;
+    static constexpr size_t kSmem = (size_t)kRingK * P * 8 + (size_t)P * 16 + 16;
+};
+
+__device__ __forceinline__ uint32_t ld_acquire_cta(const uint32_t *p) {
+    uint32_t v;
+    asm volatile("ld.acquire.cta.shared.u32 %0, [%1];" : "=r"(v) : "r"((uint32_t)__cvta_generic_to_shared(p)) : "memory");
+    return v;
+}
+__device__ __forceinline__ void st_release_cta(uint32_t *p, uint32_t v) {
+    asm volatile("st.release.cta.shared.u32 [%0], %1;" ::"r"((uint32_t)__cvta_generic_to_shared(p)), "r"(v) : "memory");
+}
+
+template <int LOG2P>
+__global__ void __launch_bounds__(kRingThreads, 1) scatter_ring_kernel(
+    const void *in, uint64_t n_total, const uint64_t *seg_off, uint64_t nseg, const unsigned long long *cb,
+    uint64_t chunk, int shift, const unsigned long long *Hs, void *out, uint64_t sent_k0, uint64_t sent_k1,
+    const void *const *seg_ptrs, unsigned long long *status) {
+    constexpr uint32_t P = 1u << LOG2P, K = kRingK, SV = 4;
+    constexpr unsigned NI = kRingThreads / 32 - kRingFlushWarps, NFL = kRingFlushWarps * 32;
+    extern __shared__ __align__(16) unsigned char smem[];
+    unsigned long long *ring = (unsigned long long *)smem;  // K * P
+    uint32_t *wr = (uint32_t *)(ring + (size_t)K * P);     // P: positions claimed
+    uint32_t *fl = wr + P;                                  // P: positions flushed
+    uint32_t *start = fl + P;                               // P: first row of the run
+    uint32_t *tail = start + P;                             // P: rows at and above hold far-end tuples
+    uint32_t *s_done = tail + P;                            // insert warps finished
+
+    const uint64_t g = blockIdx.x;
+    if (g >= cb[nseg]) return;
+    const ChunkPos cp = chunk_pos(seg_off, nseg, cb, chunk, g);
+    const uint64_t row = cb[cp.s] * P;
+    const uint64_t obase = (seg_off[0] + Hs[row]) / SV * SV;
+    unsigned long long *outp = (unsigned long long *)out + obase;
+    const void *src = seg_ptrs ? seg_ptrs[cp.s] : in;
+    const uint64_t ioff = seg_ptrs ? seg_off[cp.s] : 0;
+    const uint4 *vsrc = (const uint4 *)src + (cp.lo - ioff) / 2;  // chunks start on whole vectors
+    const uint32_t nrows = (uint32_t)(cp.hi - cp.lo);
+    // empty marker of digit d's slots, and its padding tuple: a key of another digit
+    const uint32_t dk0 = (uint32_t)(key_hash<4>((uint32_t)sent_k0) >> shift) & (P - 1u);
+    auto empty_of = [&](uint32_t d) -> uint32_t { return d != dk0 ? (uint32_t)sent_k0 : (uint32_t)sent_k1; };
+    for (uint32_t d = threadIdx.x; d < P; d += kRingThreads) {
+        const uint64_t i = row + (uint64_t)d * cp.nch + cp.cidx;  // the run of (this chunk, d)
+        start[d] = (uint32_t)(seg_off[0] + Hs[i] - obase);
+        tail[d] = (uint32_t)(seg_off[0] + Hs[i + 1] - obase);
+        wr[d] = 0;
+        fl[d] = 0;
+    }
+    for (uint32_t i = threadIdx.x; i < K * P; i += kRingThreads) ring[i] = empty_of(i & (P - 1u));
+    if (threadIdx.x == 0) *s_done = 0;
+    __syncthreads();
+    const unsigned warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+
+    if (warp < NI) {
+        // ------------------------------------------------------- insert warps
+        auto put = [&](uint32_t k, uint32_t rid) {
+            const unsigned long long sl = (unsigned long long)k | ((unsigned long long)rid << 32);
+            const uint32_t d = (uint32_t)(key_hash<4>(k) >> shift) & (P - 1u);
+            for (uint32_t it = 0; it < kRingMaxClaim; ++it) {
+                const uint32_t w = *(volatile uint32_t *)&wr[d];
+                const uint32_t f = ld_acquire_cta(&fl[d]);
+                if (w - f >= K) break;
+                if (atomicCAS(&wr[d], w, w + 1u) == w) {
+                    ring[(size_t)(w % K) * P + d] = sl;  // one 8-byte store: key and rid together
+                    return;
+                }
+            }
+            outp[atomicSub(&tail[d], 1u) - 1u] = sl;
+        };
+        const uint32_t nvec = (nrows + 1u) / 2u;
+        for (uint32_t b = warp * (32u * kRingVec); b < nvec; b += NI * 32u * kRingVec) {
+            uint4 x[kRingVec];
+#pragma unroll
+            for (int j = 0; j < kRingVec; ++j) {
+                const uint32_t v = b + (uint32_t)j * 32u + lane;
+                if (v < nvec) {
+                    if (2u * v + 1u < nrows) {
+                        x[j] = ld_stream(vsrc + v);
+                    } else {  // the chunk's last row alone: an 8-byte load
+                        const uint2 y = ((const uint2 *)vsrc)[2u * v];
+                        x[j] = make_uint4(y.x, y.y, 0u, 0u);
+                    }
+                }
+            }
+#pragma unroll
+            for (int j = 0; j < kRingVec; ++j) {
+                const uint32_t v = b + (uint32_t)j * 32u + lane;
+                if (v < nvec) {
+                    put(x[j].x, x[j].y);
+                    if (2u * v + 1u < nrows) put(x[j].z, x[j].w);
+                }
+            }
+        }
+        __threadfence_block();  // this warp's slot stores before its done count
+        __syncwarp();
+        if (lane == 0) atomicAdd(s_done, 1u);
+        return;
+    }
+
+    // ----------------------------------------------------------- flush warps
+    const uint32_t fid = (warp - NI) * 32u + lane;
+    uint64_t pass = 0;
+    for (; pass < kRingMaxPasses; ++pass) {
+        const bool fin = ld_acquire_cta(s_done) == NI;
+        bool any = false;
+        for (uint32_t d = fid; d < P; d += NFL) {
+            const uint32_t f = fl[d];
+            const uint32_t w = *(volatile uint32_t *)&wr[d];
+            if (w - f < SV) continue;
+            const uint32_t s0 = f % K, ek = empty_of(d);
+            unsigned long long t[SV];
+            bool full = true;
+#pragma unroll
+            for (uint32_t q = 0; q < SV; ++q) {
+                t[q] = *(volatile unsigned long long *)&ring[(size_t)(s0 + q) * P + d];
+                full &= (uint32_t)t[q] != ek;
+            }
+            if (!full) continue;  // a claimed slot is not written yet
+            st_sector(outp + start[d] + f, t);
+#pragma unroll
+            for (uint32_t q = 0; q < SV; ++q) ring[(size_t)(s0 + q) * P + d] = ek;
+            st_release_cta(&fl[d], f + SV);
+            any = true;
+        }
+        if (fin && !any) break;
+        if (!any) __nanosleep(256);
+    }
+    if (pass == kRingMaxPasses) {
+        atomicOr(status, 2ull);  // the timeout bit
+        return;
+    }
+    // every insert warp is done and seen: the ring's remainder, then padding
+    for (uint32_t d = fid; d < P; d += NFL) {
+        const uint32_t f = fl[d], w = wr[d], hd = start[d] + f, tl = tail[d];
+        const unsigned long long pad = empty_of(d);
+        for (uint32_t r = hd; r < tl; ++r) {
+            const uint32_t q = r - hd;
+            outp[r] = q < w - f ? ring[(size_t)((f + q) % K) * P + d] : pad;
+        }
+    }
+}
+
+template <int LOG2P>
+static hj_status launch_ring(hj_ctx *c, unsigned grid, const void *in, uint64_t n_total, const uint64_t *seg_off,
+                             uint64_t nseg, const unsigned long long *cb, uint64_t chunk, int shift,
+                             const unsigned long long *Hs, void *out, uint64_t k0, uint64_t k1,
+                             const void *const *seg_ptrs) {
+    auto kern = scatter_ring_kernel<LOG2P>;
+    HJ_TRY(allow_max_smem(c, (const void *)kern));
+    HJ_LAUNCH(c, "partition_scatter", kern, grid, kRingThreads, RingShape<LOG2P>::kSmem, in, n_total, seg_off, nseg,
+              cb, chunk, shift, Hs, out, k0, k1, seg_ptrs, &c->d_ctr->status);
+    return HJ_OK;
+}
+
 template <int W>
 static hj_status launch_region_bits(hj_ctx *c, int bits, unsigned grid, const void *in, uint64_t n_total,
                                     const uint64_t *seg_off, uint64_t nseg, const unsigned long long *cb,
@@ -916,6 +1096,8 @@ static hj_status launch_region_bits(hj_ctx *c, int bits, unsigned grid, const vo
 #define HJ_RG(B)                                                                                                 \
     case B:                                                                                                      \
         return launch_region<W, B>(c, grid, in, n_total, seg_off, nseg, cb, chunk, shift, Hs, out, k0, k1, seg_ptrs)
+    if (W == 4 && bits == 11)
+        return launch_ring<11>(c, grid, in, n_total, seg_off, nseg, cb, chunk, shift, Hs, out, k0, k1, seg_ptrs);
     switch (bits) {
         HJ_RG(1); HJ_RG(2); HJ_RG(3); HJ_RG(4); HJ_RG(5); HJ_RG(6);
         HJ_RG(7); HJ_RG(8); HJ_RG(9); HJ_RG(10); HJ_RG(11);
