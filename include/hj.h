@@ -341,6 +341,27 @@ hj_status hj_sync(hj_ctx *ctx);
  * Used to read library-owned results (pairs, offsets) into caller memory. */
 hj_status hj_copy(hj_ctx *ctx, void *dst, const void *src, uint64_t bytes);
 
+/* Pipelined CPU/GPU co-processing cost model (PL, Sec. 3.2 and Sec. 4, Eq. 1-5) as
+ * host arithmetic; no device is touched.  A series of n (1..16) steps: step i has
+ * x[i] items, of which the share r_i runs on the CPU at cpu_s[i] seconds per item
+ * and the rest on the GPU at gpu_s[i] seconds per item (computation and memory
+ * stalls, Eq. 2-3); intermediate items between steps of different ratios,
+ * |r_i - r_(i-1)| x_i, cost xfer_s seconds each on the receiving processor; the
+ * pipeline delays are Eq. 4 (r_i > r_(i-1)) and Eq. 5 (r_i < r_(i-1)), clamped at
+ * 0, with the running sums taken without the delay being computed.  The elapsed
+ * time is T = max(T_CPU, T_GPU) (Eq. 1).
+ * hj_coproc_time: T for the given ratios (each in [0, 1]); t_cpu and t_gpu (NULL
+ * allowed) receive T_CPU and T_GPU.
+ * hj_coproc_ratios: the ratios minimising T over r_i in {0, delta, 2 delta, ...,
+ * 1} for every step (the paper's exhaustive search; it uses delta = 0.02), and
+ * that T; ties go to smaller CPU shares.  HJ_E_INVALID for bad arguments (negative
+ * sizes or costs, delta outside (0, 1]); HJ_E_UNSUPPORTED when the grid^n search
+ * would exceed 10^9 ratio vectors. */
+hj_status hj_coproc_time(int n, const double *x, const double *cpu_s, const double *gpu_s, double xfer_s,
+                         const double *ratios, double *t_out, double *t_cpu, double *t_gpu);
+hj_status hj_coproc_ratios(int n, const double *x, const double *cpu_s, const double *gpu_s, double xfer_s,
+                           double delta, double *ratios_out, double *t_out);
+
 /* Per-kernel timing on the context's stream.  While enabled, every kernel launch
  * is bracketed by CUDA events; hj_prof_read synchronises, then reports, for up to
  * `cap` distinct kernel names, the name (NUL-terminated, at most 47 chars), the

@@ -105,6 +105,11 @@ def load_library(path: str = LIB_PATH):
         "hj_copy": (I32, [V, V, V, U64]),
         "hj_prof_enable": (I32, [V, ctypes.c_int]),
         "hj_prof_only": (I32, [V, ctypes.c_char_p]),
+        "hj_coproc_time": (I32, [ctypes.c_int, P(ctypes.c_double), P(ctypes.c_double), P(ctypes.c_double),
+                                 ctypes.c_double, P(ctypes.c_double), P(ctypes.c_double), P(ctypes.c_double),
+                                 P(ctypes.c_double)]),
+        "hj_coproc_ratios": (I32, [ctypes.c_int, P(ctypes.c_double), P(ctypes.c_double), P(ctypes.c_double),
+                                   ctypes.c_double, ctypes.c_double, P(ctypes.c_double), P(ctypes.c_double)]),
         "hj_prof_reset": (I32, [V]),
         "hj_prof_read": (I32, [V, P(hj_prof_entry), ctypes.c_int, P(ctypes.c_int)]),
         "hj_launch_count": (U64, [V]),
@@ -447,6 +452,32 @@ def hj_sync(ctx: Context):
 
 def prof_enable(ctx: Context, on: bool = True):
     _check(ctx, load_library().hj_prof_enable(ctx.handle, 1 if on else 0))
+
+
+def _dbl(xs):
+    return (ctypes.c_double * len(xs))(*[float(v) for v in xs])
+
+
+def hj_coproc_time(x, cpu_s, gpu_s, ratios, xfer_s: float = 0.0) -> tuple[float, float, float]:
+    """The co-processing cost model for per-step CPU ratios (host only): (T, T_CPU, T_GPU)."""
+    n = len(x)
+    t, tc, tg = ctypes.c_double(), ctypes.c_double(), ctypes.c_double()
+    st = load_library().hj_coproc_time(n, _dbl(x), _dbl(cpu_s), _dbl(gpu_s), xfer_s, _dbl(ratios), ctypes.byref(t),
+                                       ctypes.byref(tc), ctypes.byref(tg))
+    if st != HJ_OK:
+        raise HJError(st, "hj_coproc_time failed")
+    return t.value, tc.value, tg.value
+
+
+def hj_coproc_ratios(x, cpu_s, gpu_s, xfer_s: float = 0.0, delta: float = 0.02) -> tuple[list, float]:
+    """The per-step CPU ratios minimising the cost model's time, and that time (host only)."""
+    n = len(x)
+    r = (ctypes.c_double * n)()
+    t = ctypes.c_double()
+    st = load_library().hj_coproc_ratios(n, _dbl(x), _dbl(cpu_s), _dbl(gpu_s), xfer_s, delta, r, ctypes.byref(t))
+    if st != HJ_OK:
+        raise HJError(st, "hj_coproc_ratios failed")
+    return list(r), t.value
 
 
 def prof_only(ctx: Context, name: str | None = None):
