@@ -389,6 +389,14 @@ uint64_t hj_launch_count(const hj_ctx *ctx);
  * context currently holds (0 after every buffer has been released). */
 hj_status hj_debug_fail_alloc(hj_ctx *ctx, int64_t n);
 uint64_t hj_debug_bytes_in_use(const hj_ctx *ctx);
+/* Test hook for the bounded device waits (the paper has no counterpart): the
+ * partition scatter at 2^11 digits for 4-byte tuples runs flush warps that wait
+ * on the CTA's insert warps; after n passes (default 2^22; n = 0 restores it) they
+ * give up, set a sticky fault bit and return, and the call that reads the
+ * counters next returns HJ_E_TIMEOUT (its results are then undefined).  The fault
+ * is reported once; later calls on the context run normally.  Only the limit
+ * changes: no GPU fault is involved.  HJ_E_INVALID for a NULL context. */
+hj_status hj_debug_wait_limit(hj_ctx *ctx, uint64_t n);
 
 #ifdef __cplusplus
 }

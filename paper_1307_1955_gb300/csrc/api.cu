@@ -342,6 +342,14 @@ hj_status join_host_pipelined(hj_ctx *c, const hj_rel *Rh, const hj_rel *Sh, con
         HJ_CUDA(c, cudaEventSynchronize(ps.computed));
         ps.taken = true;
         const hj_counters &h = *ps.h;
+        if (h.fault) {  // a partition pass reported a fault: clear the sticky word, report it once
+            HJ_CUDA(c, cudaMemsetAsync(&c->d_ctr->fault, 0, sizeof(unsigned long long), c->stream));
+            if (h.fault & kStatusTimeout)
+                return set_err(c, HJ_E_TIMEOUT, "chunk %llu: a bounded device wait expired",
+                               (unsigned long long)ps.chunk);
+            return set_err(c, HJ_E_INVALID, "chunk %llu: a partition pass rejected its input",
+                           (unsigned long long)ps.chunk);
+        }
         if (h.status & (kStatusTimeout | kStatusBadInput | kStatusRecords | kStatusCompact | kStatusTableFull))
             return set_err(c, HJ_E_CUDA, "chunk %llu: kernel status %llu", (unsigned long long)ps.chunk,
                            (unsigned long long)h.status);
@@ -532,7 +540,7 @@ hj_status hj_partition(hj_ctx *c, const hj_rel *in, int b1, int b2, hj_rel *out_
     DevBuf tup(c), off(c);
     uint64_t rows = 0;
     HJ_TRY(partition_rel(c, in, b1, b2, 0, tup, off, &rows));
-    HJ_CUDA(c, cudaStreamSynchronize(c->stream));
+    HJ_TRY(read_counters(c));  // synchronises; reports a pass's expired wait or rejected input
     out_tuples->tuples = tup.release();
     out_tuples->n = in->n;
     out_tuples->width = in->width;

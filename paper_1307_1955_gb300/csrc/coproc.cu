@@ -119,12 +119,15 @@ extern "C" hj_status hj_coproc_ratios(int n, const double *x, const double *cpu_
                                       double xfer_s, double delta, double *ratios_out, double *t_out) {
     if (bad_series(n, x, cpu_s, gpu_s, xfer_s) || !ratios_out || !t_out) return HJ_E_INVALID;
     if (!(delta > 0.0 && delta <= 1.0)) return HJ_E_INVALID;
+    // the search visits up to (points per ratio)^n ratio vectors: refuse sizes it
+    // cannot finish before building the grid (a tiny delta would otherwise ask for
+    // a grid larger than memory, or overflow the int count)
+    const double steps = std::floor(1.0 / delta + 1e-9);
+    if (std::pow(steps + 2.0, n) > 1e9) return HJ_E_UNSUPPORTED;
+    const int m = (int)steps;
     std::vector<double> grid{0.0};
-    const int m = (int)std::floor(1.0 / delta + 1e-9);
     for (int k = 1; k <= m; ++k) grid.push_back(std::min(1.0, k * delta));
     if (grid.back() < 1.0) grid.push_back(1.0);
-    // the search visits grid^n ratio vectors (with pruning): refuse sizes it cannot finish
-    if (std::pow((double)grid.size(), n) > 1e9) return HJ_E_UNSUPPORTED;
     const Series s{n, x, cpu_s, gpu_s, xfer_s};
     Search sr{s, grid, std::vector<double>(n, 0.0), std::vector<double>(n, 0.0)};
     sr.go(0, Acc{});

@@ -1,9 +1,11 @@
 // ctx.cu -- context lifetime, memory pool with HBM budget, errors, profiling.
+#include <cstddef>
 #include <cstring>
 #include <mutex>
 #include <set>
 #include <utility>
 
+#include "common.cuh"
 #include "ctx.cuh"
 
 namespace hj {
@@ -116,13 +118,20 @@ static void prof_collect(hj_ctx *c) {
 hj_status read_counters(hj_ctx *c) {
     HJ_CUDA(c, cudaMemcpyAsync(c->h_ctr, c->d_ctr, sizeof(hj_counters), cudaMemcpyDeviceToHost, c->stream));
     HJ_CUDA(c, cudaStreamSynchronize(c->stream));
-    if (c->h_ctr->status & 2ull) return set_err(c, HJ_E_TIMEOUT, "a bounded device wait expired");
-    if (c->h_ctr->status & 4ull) return set_err(c, HJ_E_INVALID, "a kernel rejected its input");
+    const unsigned long long fault = c->h_ctr->fault;
+    if (fault) {  // reported once: the next call starts clean
+        HJ_CUDA(c, cudaMemsetAsync(&c->d_ctr->fault, 0, sizeof(unsigned long long), c->stream));
+        c->h_ctr->fault = 0;
+    }
+    const unsigned long long st = c->h_ctr->status | fault;
+    if (st & kStatusTimeout) return set_err(c, HJ_E_TIMEOUT, "a bounded device wait expired");
+    if (st & kStatusBadInput) return set_err(c, HJ_E_INVALID, "a kernel rejected its input");
     return HJ_OK;
 }
 
 hj_status zero_counters(hj_ctx *c) {
-    HJ_CUDA(c, cudaMemsetAsync(c->d_ctr, 0, sizeof(hj_counters), c->stream));
+    // every field but the sticky fault word
+    HJ_CUDA(c, cudaMemsetAsync(c->d_ctr, 0, offsetof(hj_counters, fault), c->stream));
     return HJ_OK;
 }
 
@@ -220,6 +229,7 @@ hj_status ctx_create(hj_ctx **out, int device, void *cuda_stream, uint64_t budge
         e = cudaMemPoolSetAttribute(c->pool, cudaMemPoolAttrReleaseThreshold, &keep);
     }
     if (e == cudaSuccess) e = cudaMalloc(&c->d_ctr, sizeof(hj_counters));
+    if (e == cudaSuccess) e = cudaMemset(c->d_ctr, 0, sizeof(hj_counters));
     if (e == cudaSuccess) e = cudaMallocHost(&c->h_ctr, sizeof(hj_counters));
     if (e != cudaSuccess) {
         cudaGetLastError();
@@ -328,5 +338,13 @@ hj_status hj_debug_fail_alloc(hj_ctx *c, int64_t n) {
 }
 
 uint64_t hj_debug_bytes_in_use(const hj_ctx *c) { return c ? c->in_use : 0; }
+
+/* Test hook: limit of the ring scatter's bounded wait (flush passes before its
+ * flush warps give up and report HJ_E_TIMEOUT); 0 restores the default. */
+hj_status hj_debug_wait_limit(hj_ctx *c, uint64_t n) {
+    if (!c) return HJ_E_INVALID;
+    c->wait_limit = n;
+    return HJ_OK;
+}
 
 }  // extern "C"

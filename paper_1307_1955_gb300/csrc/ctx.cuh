@@ -23,7 +23,11 @@ struct hj_counters {
     unsigned long long status;     // kStatus* bits
     unsigned long long cursor;     // output slots handed out in whole chunks (pairs + holes)
     unsigned long long work;       // next partition for the persistent join kernel
-    unsigned long long pad;
+    // Sticky fault bits of partition passes (kStatus* bits; a bounded wait that
+    // expired).  zero_counters leaves this word alone, so that a fault of a pass
+    // queued before a join's counters are cleared still reaches the host;
+    // read_counters reports and clears it.
+    unsigned long long fault;
 };
 
 namespace hj {
@@ -83,6 +87,7 @@ struct hj_ctx {
     uint64_t host_cap[2] = {0, 0};
     // test hooks (host-side fault injection)
     int64_t fail_alloc_after = -1;  // fail the N-th allocation from now (0 = next)
+    uint64_t wait_limit = 0;        // bounded device waits: passes / polls before giving up (0 = default)
 };
 
 struct hj_table {

@@ -483,6 +483,7 @@ __global__ void __launch_bounds__(NT) scatter_kernel(const void *in, uint64_t n_
 constexpr int kTmaThreads = 1024;
 constexpr uint32_t kWaitLimit = 1u << 26;  // mbarrier polls before giving up
 
+
 template <int W> struct TmaShape {
     static constexpr int IT = W == 4 ? 8 : 4;    // tuples per thread per tile
     static constexpr int T = kTmaThreads * IT;
@@ -516,7 +517,7 @@ template <int W>
 __global__ void __launch_bounds__(kTmaThreads, 1) scatter_tma_kernel(
     const void *in, uint64_t n_total, const uint64_t *seg_off, uint64_t nseg, const unsigned long long *cb,
     uint64_t chunk, int shift, int bits, const unsigned long long *Hs, void *out, int pad, uint64_t sent_k0,
-    uint64_t sent_k1, hj_counters *ctr, const void *const *seg_ptrs) {
+    uint64_t sent_k1, unsigned long long *fault, const void *const *seg_ptrs, uint32_t wait_limit) {
     using U = typename Tup<W>::U;
     using TS = TmaShape<W>;
     using Slot = typename SortSlot<W>::T;
@@ -589,12 +590,12 @@ __global__ void __launch_bounds__(kTmaThreads, 1) scatter_tma_kernel(
     if (threadIdx.x == 0 && cp.lo < cp.hi) issue(cp.lo, min(cp.lo + (uint64_t)T, cp.hi));
     for (uint64_t t0 = cp.lo; t0 < cp.hi; t0 += T) {
         const uint64_t t1 = min(t0 + (uint64_t)T, cp.hi);
-        if (!mbar_wait_bounded(bar, parity, kWaitLimit)) s_abort = 1;
+        if (!mbar_wait_bounded(bar, parity, wait_limit)) s_abort = 1;
         parity ^= 1u;
         __syncthreads();
         if (s_abort) {  // a copy did not complete: report, let it drain, stop
             if (threadIdx.x == 0) {
-                atomicOr(&ctr->status, (unsigned long long)kStatusTimeout);
+                atomicOr(fault, (unsigned long long)kStatusTimeout);
                 mbar_wait_bounded(bar, parity ^ 1u, kWaitLimit);
             }
             return;
@@ -775,7 +776,7 @@ template <int W, int LOG2P>
 __global__ void __launch_bounds__(kRegionThreads, 1) scatter_region_kernel(
     const void *in, uint64_t n_total, const uint64_t *seg_off, uint64_t nseg, const unsigned long long *cb,
     uint64_t chunk, int shift, const unsigned long long *Hs, void *out, uint64_t sent_k0, uint64_t sent_k1,
-    const void *const *seg_ptrs) {
+    const void *const *seg_ptrs, unsigned long long *fault) {
     using U = typename Tup<W>::U;
     using Vec = typename Tup<W>::Vec;
     using RS = RegionShape<W, LOG2P>;
@@ -791,6 +792,13 @@ __global__ void __launch_bounds__(kRegionThreads, 1) scatter_region_kernel(
 
     const uint64_t g = blockIdx.x;
     if (g >= cb[nseg]) return;
+    // runs start on whole sectors only if the pass's first output row does (the
+    // padded counts are whole sectors): otherwise the sector stores below would be
+    // misaligned, so refuse the input
+    if (seg_off[0] % SV) {
+        if (threadIdx.x == 0) atomicOr(fault, (unsigned long long)kStatusBadInput);
+        return;
+    }
     const ChunkPos cp = chunk_pos(seg_off, nseg, cb, chunk, g);
     const uint64_t row = cb[cp.s] * P;
     const uint64_t seg_start = seg_off[0] + Hs[row];
@@ -904,7 +912,7 @@ static hj_status launch_region(hj_ctx *c, unsigned grid, const void *in, uint64_
     const size_t smem = RegionShape<W, LOG2P>::kSmem;
     HJ_TRY(allow_max_smem(c, (const void *)kern));
     HJ_LAUNCH(c, "partition_scatter", kern, grid, kRegionThreads, smem, in, n_total, seg_off, nseg, cb, chunk, shift,
-              Hs, out, k0, k1, seg_ptrs);
+              Hs, out, k0, k1, seg_ptrs, &c->d_ctr->fault);
     return HJ_OK;
 }
 
@@ -924,8 +932,9 @@ static hj_status launch_region(hj_ctx *c, unsigned grid, const void *in, uint64_
 //     with acquire, so a slot is refilled only after it was emptied).
 //   * When every insert warp is done (release / acquire on a counter) the flush
 //     warps write what is left of each ring, then padding, into the run's gap.
-// Every wait is bounded: a flush warp that passes kRingMaxPasses sets the timeout
-// bit of the status word and returns.
+// Every wait is bounded: a flush warp that passes `max_passes` (kRingMaxPasses, or
+// the context's test setting) sets the timeout bit of the sticky fault word and
+// returns; insert warps never wait, so the CTA still ends.
 constexpr int kRingThreads = 1024;
 constexpr int kRingFlushWarps = 8;
 constexpr uint32_t kRingK = 12;                    // three sectors per digit
@@ -951,7 +960,7 @@ template <int LOG2P>
 __global__ void __launch_bounds__(kRingThreads, 1) scatter_ring_kernel(
     const void *in, uint64_t n_total, const uint64_t *seg_off, uint64_t nseg, const unsigned long long *cb,
     uint64_t chunk, int shift, const unsigned long long *Hs, void *out, uint64_t sent_k0, uint64_t sent_k1,
-    const void *const *seg_ptrs, unsigned long long *status) {
+    const void *const *seg_ptrs, unsigned long long *fault, uint64_t max_passes) {
     constexpr uint32_t P = 1u << LOG2P, K = kRingK, SV = 4;
     constexpr unsigned NI = kRingThreads / 32 - kRingFlushWarps, NFL = kRingFlushWarps * 32;
     extern __shared__ __align__(16) unsigned char smem[];
@@ -964,6 +973,10 @@ __global__ void __launch_bounds__(kRingThreads, 1) scatter_ring_kernel(
 
     const uint64_t g = blockIdx.x;
     if (g >= cb[nseg]) return;
+    if (seg_off[0] % SV) {  // runs would not start on whole sectors (see the region scatter)
+        if (threadIdx.x == 0) atomicOr(fault, (unsigned long long)kStatusBadInput);
+        return;
+    }
     const ChunkPos cp = chunk_pos(seg_off, nseg, cb, chunk, g);
     const uint64_t row = cb[cp.s] * P;
     const uint64_t obase = (seg_off[0] + Hs[row]) / SV * SV;
@@ -1036,7 +1049,7 @@ __global__ void __launch_bounds__(kRingThreads, 1) scatter_ring_kernel(
     // ----------------------------------------------------------- flush warps
     const uint32_t fid = (warp - NI) * 32u + lane;
     uint64_t pass = 0;
-    for (; pass < kRingMaxPasses; ++pass) {
+    for (; pass < max_passes; ++pass) {
         const bool fin = ld_acquire_cta(s_done) == NI;
         bool any = false;
         for (uint32_t d = fid; d < P; d += NFL) {
@@ -1061,8 +1074,8 @@ __global__ void __launch_bounds__(kRingThreads, 1) scatter_ring_kernel(
         if (fin && !any) break;
         if (!any) __nanosleep(256);
     }
-    if (pass == kRingMaxPasses) {
-        atomicOr(status, 2ull);  // the timeout bit
+    if (pass == max_passes) {
+        atomicOr(fault, (unsigned long long)kStatusTimeout);
         return;
     }
     // every insert warp is done and seen: the ring's remainder, then padding
@@ -1083,8 +1096,9 @@ static hj_status launch_ring(hj_ctx *c, unsigned grid, const void *in, uint64_t 
                              const void *const *seg_ptrs) {
     auto kern = scatter_ring_kernel<LOG2P>;
     HJ_TRY(allow_max_smem(c, (const void *)kern));
+    const uint64_t passes = c->wait_limit ? std::min<uint64_t>(c->wait_limit, kRingMaxPasses) : kRingMaxPasses;
     HJ_LAUNCH(c, "partition_scatter", kern, grid, kRingThreads, RingShape<LOG2P>::kSmem, in, n_total, seg_off, nseg,
-              cb, chunk, shift, Hs, out, k0, k1, seg_ptrs, &c->d_ctr->status);
+              cb, chunk, shift, Hs, out, k0, k1, seg_ptrs, &c->d_ctr->fault, passes);
     return HJ_OK;
 }
 
@@ -1214,11 +1228,13 @@ hj_status partition_pass(hj_ctx *c, int width, const void *in, uint64_t n_total,
         if (width == 4) {
             HJ_TRY(allow_max_smem(c, (const void *)scatter_tma_kernel<4>));
             HJ_LAUNCH(c, "partition_scatter", scatter_tma_kernel<4>, (unsigned)max_chunks, kTmaThreads, tma_smem, in,
-                      n_total, seg_off, nseg, cb, chunk, shift, bits, Hs, out, pad, k0, k1, c->d_ctr, seg_ptrs);
+                      n_total, seg_off, nseg, cb, chunk, shift, bits, Hs, out, pad, k0, k1, &c->d_ctr->fault, seg_ptrs,
+                      kWaitLimit);
         } else {
             HJ_TRY(allow_max_smem(c, (const void *)scatter_tma_kernel<8>));
             HJ_LAUNCH(c, "partition_scatter", scatter_tma_kernel<8>, (unsigned)max_chunks, kTmaThreads, tma_smem, in,
-                      n_total, seg_off, nseg, cb, chunk, shift, bits, Hs, out, pad, k0, k1, c->d_ctr, seg_ptrs);
+                      n_total, seg_off, nseg, cb, chunk, shift, bits, Hs, out, pad, k0, k1, &c->d_ctr->fault, seg_ptrs,
+                      kWaitLimit);
         }
     } else if (width == 4) {
         if (cfg.nt == 512) HJ_SC(4, 512, 8); else HJ_SC(4, 1024, 2);

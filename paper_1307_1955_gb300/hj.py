@@ -115,6 +115,7 @@ def load_library(path: str = LIB_PATH):
         "hj_launch_count": (U64, [V]),
         "hj_debug_fail_alloc": (I32, [V, ctypes.c_int64]),
         "hj_debug_bytes_in_use": (U64, [V]),
+        "hj_debug_wait_limit": (I32, [V, U64]),
         "hj_plan": (I32, [V, P(hj_rel), P(hj_rel), P(hj_opts), P(hj_plan_info)]),
         "hj_tune": (I32, [V, P(hj_rel), P(hj_rel), P(hj_opts), ctypes.c_int, P(hj_plan_info)]),
         "hj_tune_clear": (I32, [V]),
@@ -403,17 +404,41 @@ def hj_results_free(ctx: Context, outs: ctypes.Array, n: int | None = None):
         _check(ctx, lib.hj_result_free(ctx.handle, ctypes.byref(outs[j])))
 
 
+def check_pairs_buffer(pairs: torch.Tensor | None, R: torch.Tensor) -> int:
+    """Rows of a caller-owned pair buffer: None, or a contiguous (m, 2) CUDA tensor
+    of R's dtype on R's device (anything else could let the join write past its
+    end).  Raises ValueError otherwise."""
+    if pairs is None:
+        return 0
+    if not isinstance(pairs, torch.Tensor):
+        raise ValueError("pairs must be a torch tensor or None")
+    if pairs.dim() != 2 or pairs.shape[1] != 2:
+        raise ValueError("pairs must be an (m, 2) tensor")
+    if pairs.dtype != R.dtype:
+        raise ValueError(f"pairs must have the relations' dtype {R.dtype}, not {pairs.dtype}")
+    if not pairs.is_contiguous():
+        raise ValueError("pairs must be contiguous")
+    if not pairs.is_cuda or pairs.device != R.device:
+        raise ValueError(f"pairs must be a CUDA tensor on {R.device}")
+    return int(pairs.shape[0])
+
+
 def hj_join_static(R: torch.Tensor, S: torch.Tensor, pairs: torch.Tensor | None, stream=None):
     """The allocation-free SHJ: pairs land in the caller's (m, 2) CUDA tensor of R's
-    dtype.  Returns (count, (c0, c1)); raises HJError on a non-OK status (count is
-    then in .count for HJ_E_OVERFLOW)."""
+    dtype.  The work is ordered on `stream`, by default torch's current stream of R's
+    device (so it follows the kernels that made R and S).  Returns (count, (c0, c1));
+    raises HJError on a non-OK status (count is then in .count for HJ_E_OVERFLOW)."""
+    if not R.is_cuda or S.device != R.device:
+        raise ValueError("R and S must be CUDA tensors on one device")
     r, s = rel_of(R), rel_of(S)
+    cap = check_pairs_buffer(pairs, R)
     cnt = ctypes.c_uint64()
     chk = (ctypes.c_uint64 * 2)()
-    ptr = pairs.data_ptr() if pairs is not None and pairs.numel() else None
-    cap = pairs.shape[0] if pairs is not None else 0
-    st = load_library().hj_join_static(ctypes.byref(r), ctypes.byref(s), stream_handle(stream) if stream else None,
-                                       ptr, cap, ctypes.byref(cnt), chk)
+    ptr = pairs.data_ptr() if cap else None
+    if stream is None:
+        stream = torch.cuda.current_stream(R.device)
+    st = load_library().hj_join_static(ctypes.byref(r), ctypes.byref(s), stream_handle(stream), ptr, cap,
+                                       ctypes.byref(cnt), chk)
     if st != HJ_OK:
         e = HJError(st, "hj_join_static failed")
         e.count = int(cnt.value)

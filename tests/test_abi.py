@@ -79,3 +79,25 @@ def test_product_path_does_not_import_the_oracle():
             if f.endswith((".py", ".cu", ".cuh", ".h", ".cpp")):
                 txt = open(os.path.join(dirpath, f)).read()
                 assert "import oracle" not in txt and "from oracle" not in txt and "hj_oracle" not in txt, f
+
+
+def test_static_join_pair_buffer_is_checked_before_any_call():
+    # A caller-owned pair buffer of the wrong shape, dtype, layout or device would
+    # let the probe write past its end: the binding rejects it on the host.
+    import torch
+
+    from paper_1307_1955_gb300 import hj
+
+    R = torch.zeros((4, 2), dtype=torch.int64)
+    assert hj.check_pairs_buffer(None, R) == 0
+    bad = [torch.zeros(8, dtype=torch.int64),                      # 1-D
+           torch.zeros((4, 3), dtype=torch.int64),                 # three columns
+           torch.zeros((4, 2), dtype=torch.int32),                 # narrower than R
+           torch.zeros((2, 4), dtype=torch.int64).t(),             # not contiguous
+           torch.zeros((4, 2), dtype=torch.int64),                 # host memory
+           [[0, 0]]]                                               # not a tensor
+    for p in bad:
+        with pytest.raises(ValueError):
+            hj.check_pairs_buffer(p, R)
+    with pytest.raises(ValueError):                                # host relations
+        hj.hj_join_static(R, R, None)

@@ -96,3 +96,12 @@ def test_invalid_arguments(hjm):
     with pytest.raises(hjm.HJError) as e:  # 51^8 ratio vectors
         hjm.hj_coproc_ratios([1.0] * 8, [1.0] * 8, [1.0] * 8)
     assert e.value.status == hjm.HJ_E_UNSUPPORTED
+
+
+def test_tiny_delta_is_refused_before_the_grid_is_built(hjm):
+    # 1 / delta = 1e12 grid points per ratio: refused at once, without building the
+    # grid (or converting 1e12 to an int)
+    for d in (1e-12, 1e-9):
+        with pytest.raises(hjm.HJError) as e:
+            hjm.hj_coproc_ratios([1.0], [1.0], [1.0], delta=d)
+        assert e.value.status == hjm.HJ_E_UNSUPPORTED

@@ -85,8 +85,12 @@ def test_shj_unique_keys_full_size(hjm, ctx):
     assert res.algo == hjm.HJ_ALGO_SHJ
 
 
-@pytest.mark.parametrize("bits,passes", [(1, 1), (5, 1), (8, 1), (12, 1), (2, 2), (9, 2), (14, 2)])
+@pytest.mark.parametrize("bits,passes", [(1, 1), (5, 1), (8, 1), (11, 1), (12, 1), (2, 2), (9, 2), (14, 2), (21, 2),
+                                         (22, 2)])
 def test_phj_half_match_scaled(hjm, ctx, bits, passes):
+    # (11 bits in one pass is the plan the tuner picks at full size, and (21, 2) /
+    # (22, 2) put 11-bit passes first / in both passes: the ring scatter at its
+    # chunk and segment paths.)
     # PHJ on the |R| = 2^24, |S| = 2^28 workload scaled by 2^-8 (ragged sizes):
     # R unique, S keys uniform over twice R's key range (about half match).
     nr, ns = (1 << 16) + 37, (1 << 20) + 11
@@ -164,8 +168,9 @@ def test_phj_full_size_properties(hjm, ctx):
 # --------------------------------------------------------------------- edge cases
 
 
-@pytest.mark.parametrize("algo,bits", [(1, 0), (2, 3), (2, 10)])
-@pytest.mark.parametrize("nr,ns", [(0, 0), (0, 100), (100, 0), (1, 1), (3, 7), (1025, 4097)])
+@pytest.mark.parametrize("algo,bits", [(1, 0), (2, 3), (2, 10), (2, 11)])
+@pytest.mark.parametrize("nr,ns", [(0, 0), (0, 100), (100, 0), (1, 1), (3, 7), (1025, 4097), (8191, 8193),
+                                   (40_001, 123_457)])
 def test_empty_and_ragged(hjm, ctx, algo, bits, nr, ns):
     R, S = W.unique_and_uniform(nr, ns, max(nr, 1), SEED, DEV, ids=(5, nr, ns))
     _check_all_modes(hjm, ctx, R, S, algo=algo, radix_bits=bits)

@@ -4,16 +4,19 @@ It serves callers that may not allocate device memory (for example a host proces
 whose device memory is owned by another allocator, or a loop that forbids
 allocation after start-up): its scratch is one fixed device array inside the
 library and the caller brings the pair buffer.  Here it is called through the C ABI
-twice in a row, on different inputs, and each result must equal what the ordinary
-entry point (hj_join with the SHJ algorithm) returns: same pair multiset, count and
-checksums -- join results are integers, so the comparison is exact.  The second
-call also checks that nothing left in the shared scratch by the first call leaks
-into it.  This file is collected last so that a run stopping at the first failure
-has already run every other test."""
+twice in a row, on different inputs, and each result must equal both what the
+ordinary entry point (hj_join with the SHJ algorithm) returns and what the CPU
+oracle computes: same pair multiset, count and checksums -- join results are
+integers, so the comparison is exact.  The oracle shares no code with either CUDA
+path, so a fault in the table code the two entry points share cannot cancel out.
+The second call also checks that nothing left in the shared scratch by the first
+call leaks into it.  This file is collected last so that a run stopping at the
+first failure has already run every other test."""
 import numpy as np
 import pytest
 import torch
 
+import oracle
 from paper_1307_1955_gb300 import workload as W
 
 pytestmark = pytest.mark.gpu
@@ -46,10 +49,17 @@ def _reference(hjm, R, S):
     return out
 
 
-def _static(hjm, R, S, cap):
+def _oracle(R, S):
+    r, s = W.to_numpy_u(R), W.to_numpy_u(S)
+    rr, ss = oracle.hash_join(r, s)
+    cnt, c0, c1 = oracle.join_aggregate(r, s)
+    return oracle.sorted_pairs(rr, ss), cnt, (c0, c1)
+
+
+def _static(hjm, R, S, cap, stream=None):
     dt = R.dtype
     pairs = torch.empty((cap, 2), dtype=dt, device=DEV)
-    count, chk = hjm.hj_join_static(R, S, pairs)
+    count, chk = hjm.hj_join_static(R, S, pairs, stream=stream)
     got = pairs[:count].cpu().numpy().view(np.uint32 if dt == torch.int32 else np.uint64)
     return _sorted(got), count, chk
 
@@ -62,10 +72,26 @@ def test_static_join_matches_hj_join_on_two_calls_in_a_row(hjm):
     R2, S2 = W.zipf_pair(20_000, 90_000, 0.75, 0.5, 1 << 12, W.DEFAULT_SEED, DEV, ids=(21,))
     for R, S in ((R1, S1), (R2, S2)):
         want = _reference(hjm, R, S)
+        ora = _oracle(R, S)
         got = _static(hjm, R, S, want[1] + 64)
-        assert got[1] == want[1]
-        assert got[2] == want[2]
+        assert got[1] == want[1] == ora[1]
+        assert got[2] == want[2] == ora[2]
         assert np.array_equal(got[0], want[0])
+        assert np.array_equal(got[0], ora[0])
+
+
+def test_static_join_follows_the_stream_that_made_its_inputs(hjm):
+    # inputs made on a side torch stream and the join issued on that stream as the
+    # current one: the default stream argument orders the join after the generation
+    side = torch.cuda.Stream()
+    with torch.cuda.stream(side):
+        R, S = W.unique_and_uniform(200_000, 800_000, 200_000, W.DEFAULT_SEED, DEV, ids=(23,))
+        got = _static(hjm, R, S, 800_064)
+    side.synchronize()
+    ora = _oracle(R, S)
+    assert got[1] == 800_000 == ora[1]          # every S key is an R key, R keys unique
+    assert got[2] == ora[2]
+    assert np.array_equal(got[0], ora[0])
 
 
 def test_static_join_reports_overflow_and_size_limit(hjm):
