@@ -920,31 +920,39 @@ static hj_status launch_region(hj_ctx *c, unsigned grid, const void *in, uint64_
 // 4-byte tuples at 2^11 digits (the join's usual fan-out): the insert and flush
 // work of the region scatter split between warps that run at the same time, with
 // no barrier after the set-up.  Digit d owns a ring of kRingK slots (slot j at
-// ring[j * P + d], empty slots hold a key of another digit) and two cursors:
-// wr[d], positions claimed, and fl[d], positions flushed.
-//   * An insert warp streams its own blocks of the chunk.  A tuple claims position
-//     w = wr[d] by shared CAS while w - fl[d] < kRingK and stores itself in slot
-//     w mod kRingK; with the ring full it is written from the run's far end, as in
-//     the region scatter.
-//   * A flush warp owns a set of digits.  Once four claimed positions at fl[d]
-//     all hold tuples, it writes them as one 32-byte sector at the run's next
-//     sector, empties the slots, then advances fl[d] (release; inserters read fl
-//     with acquire, so a slot is refilled only after it was emptied).
+// ring[j * P + d], empty slots hold a key of another digit) and one packed word,
+// claimed | flushed << 16: positions claimed and positions flushed, both counted
+// modulo kRingMod (a multiple of kRingK and of the sector, so a position's slot
+// is the same in every lap of the count).
+//   * An insert warp streams its own blocks of the chunk.  A tuple reads its
+//     digit's word once (acquire) and, while claimed - flushed < kRingK, claims
+//     position w with one CAS of the word and stores itself in slot w mod kRingK
+//     (key and rid in one 8-byte store); with the ring full it is written from
+//     the run's far end, as in the region scatter.
+//   * A flush lane owns a set of digits (consecutive digits across a warp's lanes,
+//     so its slot accesses do not conflict).  Once the four claimed positions at
+//     the flushed count all hold tuples, it writes them as one 32-byte sector at
+//     the run's next row, empties the slots, then adds the sector to the flushed
+//     half with a release add (inserts read the word with acquire, so a slot is
+//     refilled only after it was emptied).  Only that lane writes the flushed half.
 //   * When every insert warp is done (release / acquire on a counter) the flush
-//     warps write what is left of each ring, then padding, into the run's gap.
+//     lanes write what is left of each ring, then padding, into the run's gap.
+// One packed word instead of two cursors saves an insert one shared load: the
+// kernel is bound by the shared-memory data pipe, not by DRAM (measured).
 // Every wait is bounded: a flush warp that passes `max_passes` (kRingMaxPasses, or
 // the context's test setting) sets the timeout bit of the sticky fault word and
 // returns; insert warps never wait, so the CTA still ends.
 constexpr int kRingThreads = 1024;
-constexpr int kRingFlushWarps = 8;
+constexpr int kRingFlushWarps = 4;                 // 4 of 32 warps flush (2 fall behind, 8 slow the inserts)
 constexpr uint32_t kRingK = 12;                    // three sectors per digit
+constexpr uint32_t kRingMod = 65532;               // 12 * 5461: positions modulo this, in 16 bits
 constexpr uint32_t kRingMaxClaim = 64;             // CAS attempts before the far-end path
 constexpr uint64_t kRingMaxPasses = 1ull << 22;    // flush passes before the timeout bit
 constexpr int kRingVec = 4;                        // 16-byte vectors per lane in flight
 
 template <int LOG2P> struct RingShape {
     static constexpr uint32_t P = 1u << LOG2P;
-    static constexpr size_t kSmem = (size_t)kRingK * P * 8 + (size_t)P * 16 + 16;
+    static constexpr size_t kSmem = (size_t)kRingK * P * 8 + (size_t)P * 12 + 16;
 };
 
 __device__ __forceinline__ uint32_t ld_acquire_cta(const uint32_t *p) {
@@ -952,8 +960,9 @@ __device__ __forceinline__ uint32_t ld_acquire_cta(const uint32_t *p) {
     asm volatile("ld.acquire.cta.shared.u32 %0, [%1];" : "=r"(v) : "r"((uint32_t)__cvta_generic_to_shared(p)) : "memory");
     return v;
 }
-__device__ __forceinline__ void st_release_cta(uint32_t *p, uint32_t v) {
-    asm volatile("st.release.cta.shared.u32 [%0], %1;" ::"r"((uint32_t)__cvta_generic_to_shared(p)), "r"(v) : "memory");
+__device__ __forceinline__ void red_release_add_cta(uint32_t *p, uint32_t v) {
+    asm volatile("red.release.cta.shared::cta.add.u32 [%0], %1;" ::"r"((uint32_t)__cvta_generic_to_shared(p)), "r"(v)
+                 : "memory");
 }
 
 template <int LOG2P>
@@ -961,14 +970,13 @@ __global__ void __launch_bounds__(kRingThreads, 1) scatter_ring_kernel(
     const void *in, uint64_t n_total, const uint64_t *seg_off, uint64_t nseg, const unsigned long long *cb,
     uint64_t chunk, int shift, const unsigned long long *Hs, void *out, uint64_t sent_k0, uint64_t sent_k1,
     const void *const *seg_ptrs, unsigned long long *fault, uint64_t max_passes) {
-    constexpr uint32_t P = 1u << LOG2P, K = kRingK, SV = 4;
+    constexpr uint32_t P = 1u << LOG2P, K = kRingK, SV = 4, M = kRingMod;
     constexpr unsigned NI = kRingThreads / 32 - kRingFlushWarps, NFL = kRingFlushWarps * 32;
     extern __shared__ __align__(16) unsigned char smem[];
-    unsigned long long *ring = (unsigned long long *)smem;  // K * P
-    uint32_t *wr = (uint32_t *)(ring + (size_t)K * P);     // P: positions claimed
-    uint32_t *fl = wr + P;                                  // P: positions flushed
-    uint32_t *start = fl + P;                               // P: first row of the run
-    uint32_t *tail = start + P;                             // P: rows at and above hold far-end tuples
+    unsigned long long *ring = (unsigned long long *)smem;  // K * P, slot j of digit d at ring[j * P + d]
+    uint32_t *word = (uint32_t *)(ring + (size_t)K * P);   // P: claimed | flushed << 16 (mod M)
+    uint32_t *nxt = word + P;                               // P: next output row of the run
+    uint32_t *tail = nxt + P;                               // P: rows at and above hold far-end tuples
     uint32_t *s_done = tail + P;                            // insert warps finished
 
     const uint64_t g = blockIdx.x;
@@ -985,15 +993,13 @@ __global__ void __launch_bounds__(kRingThreads, 1) scatter_ring_kernel(
     const uint64_t ioff = seg_ptrs ? seg_off[cp.s] : 0;
     const uint4 *vsrc = (const uint4 *)src + (cp.lo - ioff) / 2;  // chunks start on whole vectors
     const uint32_t nrows = (uint32_t)(cp.hi - cp.lo);
-    // empty marker of digit d's slots, and its padding tuple: a key of another digit
     const uint32_t dk0 = (uint32_t)(key_hash<4>((uint32_t)sent_k0) >> shift) & (P - 1u);
     auto empty_of = [&](uint32_t d) -> uint32_t { return d != dk0 ? (uint32_t)sent_k0 : (uint32_t)sent_k1; };
     for (uint32_t d = threadIdx.x; d < P; d += kRingThreads) {
         const uint64_t i = row + (uint64_t)d * cp.nch + cp.cidx;  // the run of (this chunk, d)
-        start[d] = (uint32_t)(seg_off[0] + Hs[i] - obase);
+        nxt[d] = (uint32_t)(seg_off[0] + Hs[i] - obase);
         tail[d] = (uint32_t)(seg_off[0] + Hs[i + 1] - obase);
-        wr[d] = 0;
-        fl[d] = 0;
+        word[d] = 0;
     }
     for (uint32_t i = threadIdx.x; i < K * P; i += kRingThreads) ring[i] = empty_of(i & (P - 1u));
     if (threadIdx.x == 0) *s_done = 0;
@@ -1001,16 +1007,17 @@ __global__ void __launch_bounds__(kRingThreads, 1) scatter_ring_kernel(
     const unsigned warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
 
     if (warp < NI) {
-        // ------------------------------------------------------- insert warps
         auto put = [&](uint32_t k, uint32_t rid) {
             const unsigned long long sl = (unsigned long long)k | ((unsigned long long)rid << 32);
             const uint32_t d = (uint32_t)(key_hash<4>(k) >> shift) & (P - 1u);
             for (uint32_t it = 0; it < kRingMaxClaim; ++it) {
-                const uint32_t w = *(volatile uint32_t *)&wr[d];
-                const uint32_t f = ld_acquire_cta(&fl[d]);
-                if (w - f >= K) break;
-                if (atomicCAS(&wr[d], w, w + 1u) == w) {
-                    ring[(size_t)(w % K) * P + d] = sl;  // one 8-byte store: key and rid together
+                const uint32_t v = ld_acquire_cta(&word[d]);
+                const uint32_t w = v & 0xFFFFu, f = v >> 16;
+                const uint32_t used = w >= f ? w - f : w + M - f;
+                if (used >= K) break;
+                const uint32_t w1 = w + 1u == M ? 0u : w + 1u;
+                if (atomicCAS(&word[d], v, (v & 0xFFFF0000u) | w1) == v) {
+                    ring[(size_t)(w % K) * P + d] = sl;
                     return;
                 }
             }
@@ -1025,7 +1032,7 @@ __global__ void __launch_bounds__(kRingThreads, 1) scatter_ring_kernel(
                 if (v < nvec) {
                     if (2u * v + 1u < nrows) {
                         x[j] = ld_stream(vsrc + v);
-                    } else {  // the chunk's last row alone: an 8-byte load
+                    } else {
                         const uint2 y = ((const uint2 *)vsrc)[2u * v];
                         x[j] = make_uint4(y.x, y.y, 0u, 0u);
                     }
@@ -1040,7 +1047,7 @@ __global__ void __launch_bounds__(kRingThreads, 1) scatter_ring_kernel(
                 }
             }
         }
-        __threadfence_block();  // this warp's slot stores before its done count
+        __threadfence_block();
         __syncwarp();
         if (lane == 0) atomicAdd(s_done, 1u);
         return;
@@ -1053,9 +1060,10 @@ __global__ void __launch_bounds__(kRingThreads, 1) scatter_ring_kernel(
         const bool fin = ld_acquire_cta(s_done) == NI;
         bool any = false;
         for (uint32_t d = fid; d < P; d += NFL) {
-            const uint32_t f = fl[d];
-            const uint32_t w = *(volatile uint32_t *)&wr[d];
-            if (w - f < SV) continue;
+            const uint32_t v = *(volatile uint32_t *)&word[d];
+            const uint32_t w = v & 0xFFFFu, f = v >> 16;
+            const uint32_t used = w >= f ? w - f : w + M - f;
+            if (used < SV) continue;
             const uint32_t s0 = f % K, ek = empty_of(d);
             unsigned long long t[SV];
             bool full = true;
@@ -1065,10 +1073,13 @@ __global__ void __launch_bounds__(kRingThreads, 1) scatter_ring_kernel(
                 full &= (uint32_t)t[q] != ek;
             }
             if (!full) continue;  // a claimed slot is not written yet
-            st_sector(outp + start[d] + f, t);
+            const uint32_t o = nxt[d];
+            st_sector(outp + o, t);
 #pragma unroll
             for (uint32_t q = 0; q < SV; ++q) ring[(size_t)(s0 + q) * P + d] = ek;
-            st_release_cta(&fl[d], f + SV);
+            nxt[d] = o + SV;
+            // the slots are empty before the flushed count says so (release)
+            red_release_add_cta(&word[d], (f + SV == M ? SV - M : SV) << 16);
             any = true;
         }
         if (fin && !any) break;
@@ -1080,11 +1091,13 @@ __global__ void __launch_bounds__(kRingThreads, 1) scatter_ring_kernel(
     }
     // every insert warp is done and seen: the ring's remainder, then padding
     for (uint32_t d = fid; d < P; d += NFL) {
-        const uint32_t f = fl[d], w = wr[d], hd = start[d] + f, tl = tail[d];
+        const uint32_t v = word[d], w = v & 0xFFFFu, f = v >> 16;
+        const uint32_t used = w >= f ? w - f : w + M - f;
+        const uint32_t hd = nxt[d], tl = tail[d];
         const unsigned long long pad = empty_of(d);
         for (uint32_t r = hd; r < tl; ++r) {
             const uint32_t q = r - hd;
-            outp[r] = q < w - f ? ring[(size_t)((f + q) % K) * P + d] : pad;
+            outp[r] = q < used ? ring[(size_t)((f + q) % K) * P + d] : pad;
         }
     }
 }
