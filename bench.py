@@ -8,7 +8,10 @@ whole join through the C ABI (hj_join): partition R and S, join every partition
 pair, materialise the (rid_R, rid_S) pairs.  Inputs (2.28 GB) exceed the 129 MB
 L2, so no flush is needed between steps.
 
-Prints ONE JSON line (rank 0).  `--impl reference` times the CPU oracle instead.
+Prints ONE JSON line (rank 0).  At N=1 the default workload's line also carries
+("also") summaries of the batched (4096 joins), served (20000 requests) and skewed
+64-bit configurations, each run afterwards in a process of its own (--no-extras
+skips them).  `--impl reference` times the CPU oracle instead.
 Under torchrun every rank joins its own seeded relations (independent problems,
 weak scaling, no data-path collective); value = all ranks' tuples / max time.
 """
@@ -79,6 +82,12 @@ WORKLOADS = {
         desc="the paper's high-skew data set at its default size: |R| = |S| = 2^24 (uint32 key, uint32 rid); 25 % of "
              "R's tuples share one key, the other R keys distinct, S keys uniform over R's distinct keys; pairs "
              "materialised"),
+    "phj_sharded": dict(
+        kind="sharded", nr=1 << 24, ns=1 << 28, dom=1 << 25, algo=2,
+        desc="one PHJ of |R|=2^24, |S|=2^28 (uint32 key, uint32 rid; the default workload's relations) sharded "
+             "over the ranks: each rank holds 1/N of R's and S's rows, splits them by the sharding hash (hj_split), "
+             "one all-to-all of R and one of S, a local hj_join, one all-reduce of count and checksums; strong "
+             "scaling (the whole job is one join); pairs materialised, left on the rank that found them"),
     "shj_1m": dict(
         nr=1 << 20, ns=1 << 20, dom=1 << 20, algo=1,
         desc="SHJ, |R|=|S|=2^20 (uint32 key, uint32 rid); R keys a permutation of 1..2^20, S keys drawn "
@@ -104,6 +113,11 @@ def parse():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-clocks", action="store_true")
+    ap.add_argument("--no-extras", action="store_true",
+                    help="default workload at N=1: skip the batched, served and skewed runs added to the line")
+    ap.add_argument("--plain-seconds", type=float, default=20.0,
+                    help="serving: bound on the one-hj_join-per-request comparison run")
+    ap.add_argument("--no-sweep", action="store_true", help="serving: skip the offered-load sweep")
     return ap.parse_args()
 
 
@@ -565,6 +579,14 @@ def run_hj(args, wl, ws, rank, local):
     if rank == 0 and not args.no_cpu_baseline:
         cpu = cpu_sample(wl, R, S, target_s=15.0)
 
+    also = None
+    if ws == 1 and not args.no_extras and args.workload == "phj_16m_256m":
+        # the other configurations, each in its own process once this one's memory is free
+        ctx.close()
+        del R, S
+        torch.cuda.empty_cache()
+        also = run_extras()
+
     if rank == 0:
         line = {
             "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
@@ -579,6 +601,8 @@ def run_hj(args, wl, ws, rank, local):
             "roofline": roofline, "join_roofline": join_roof, "kernels": kernels,
             "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches, "clocks": clocks,
         }
+        if also is not None:
+            line["also"] = also
         print(json.dumps(line), flush=True)
     ctx.close()
     if ws > 1:
@@ -724,6 +748,98 @@ def run_batch(args, wl, ws, rank, local):
         dist.destroy_process_group()
 
 
+def run_sharded(args, wl, ws, rank, local):
+    """One join whose rows are spread over the ranks (paper_1307_1955_gb300.dist):
+    split, all-to-all, local join, all-reduce per step; value = the whole join's
+    tuples over the slowest rank's time (strong scaling)."""
+    import torch
+    import torch.distributed as dist
+
+    import __graft_entry__
+
+    if ws > 1:
+        dist.init_process_group("nccl" if torch.cuda.is_available() else "gloo")
+    torch.cuda.set_device(local)
+    if rank == 0:
+        __graft_entry__.build()
+    if ws > 1:
+        dist.barrier()
+    from paper_1307_1955_gb300 import dist as D
+    from paper_1307_1955_gb300 import hj
+    from paper_1307_1955_gb300 import workload as W
+
+    dev = torch.device("cuda", local)
+    # the default workload's relations; this rank keeps its share of the rows
+    R, S = W.unique_and_uniform(wl["nr"], wl["ns"], wl["dom"], W.DEFAULT_SEED, dev, ids=(2, 0))
+    r0, r1 = wl["nr"] * rank // ws, wl["nr"] * (rank + 1) // ws
+    s0, s1 = wl["ns"] * rank // ws, wl["ns"] * (rank + 1) // ws
+    R, S = R[r0:r1].clone(), S[s0:s1].clone()
+    torch.cuda.synchronize()
+    torch.cuda.empty_cache()
+    stream = torch.cuda.current_stream(dev)
+    ctx = hj.Context(local, stream=stream)
+
+    def step():
+        res = D.shard_join(ctx, R, S, mode=hj.HJ_MATERIALIZE, checksum=False)
+        res.local.free()
+        return res
+
+    for _ in range(args.warmup):
+        res = step()
+    sampler = ClockSampler(local)
+    if not args.no_clocks:
+        sampler.start()
+        time.sleep(0.3)
+    if ws > 1:
+        dist.barrier()
+    torch.cuda.synchronize()
+    l0 = hj.launch_count(ctx)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(args.steps):
+        res = step()
+    e1.record(stream)
+    torch.cuda.synchronize()
+    if ws > 1:
+        dist.barrier()
+    launches = hj.launch_count(ctx) - l0
+    clocks = sampler.stop() if not args.no_clocks else None
+    ms = ranks_max(e0.elapsed_time(e1), ws, dev)
+    n = wl["nr"] + wl["ns"]
+    value = n * args.steps / (ms / 1000.0)
+    # one profiled step for the per-kernel times of this rank
+    hj.prof_reset(ctx)
+    hj.prof_enable(ctx, True)
+    step()
+    prof = hj.prof_read(ctx)
+    hj.prof_enable(ctx, False)
+    peak, peak_kind = measured_peak()
+    dom_name, (dom_launches, dom_ms) = max(prof.items(), key=lambda kv: kv[1][1])
+    tb = 8
+    join_bytes = 3 * tb * n + tb * res.count
+    step_s = ms / 1000.0 / args.steps
+    if rank == 0:
+        line = {
+            "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True, "scaling": "strong",
+            "vs_baseline": None, "dtype": "u32", "data": "synthetic",
+            "config": {"workload": wl["desc"], "pairs_per_step": res.count, "parallelism": f"sharded x{ws}",
+                       "rows_per_rank": [r1 - r0, s1 - s0], "received_rows_rank0": list(res.received),
+                       "l2": "inputs far larger than the 129 MB L2; no flush"},
+            "join_roofline": {"bytes_per_step": join_bytes, "achieved_gbs": join_bytes / step_s / 1e9,
+                              "frac": join_bytes / step_s / 1e9 / peak / ws, "peak_per_gpu": peak},
+            "roofline": None,
+            "kernels_rank0": {k: {"launches": v[0], "ms": v[1]} for k, v in
+                              sorted(prof.items(), key=lambda kv: -kv[1][1])},
+            "dominant_kernel_rank0": dom_name,
+            "cpu_baseline": None, "e2e": None, "gpu_launches": launches, "clocks": clocks,
+        }
+        print(json.dumps(line), flush=True)
+    ctx.close()
+    if ws > 1:
+        dist.destroy_process_group()
+
+
 def serve_pool(wl, rank, dev, pool_bytes: float):
     """Request sizes and arrival order of the whole stream, and the device inputs of
     its first K requests (K as large as pool_bytes allows); request i is served
@@ -831,7 +947,7 @@ def run_serve(args, wl, ws, rank, local):
         span_l, lat_l, bad_l = stream(srv, arrivals)
         # the same stream at lighter and heavier offered loads
         sweep = []
-        for ld in wl.get("sweep", ()):
+        for ld in (() if args.no_sweep else wl.get("sweep", ())):
             r_ = ld * sat / (total / n)
             span_x, lat_x, bad_x = stream(srv, [sp.arrival_s / r_ for sp in specs])
             sweep.append({"load": ld, "offered_req_per_s": r_, "tuples_per_s": total / span_x, "span_s": span_x,
@@ -844,7 +960,7 @@ def run_serve(args, wl, ws, rank, local):
         R, S = reqs[order[i]]
         hj.hj_join(ctx, R, S).free()
         done_t += tuples[i]
-        if time.perf_counter() - t0 > 20.0:
+        if time.perf_counter() - t0 > args.plain_seconds:
             break
     torch.cuda.synchronize()
     plain = done_t / (time.perf_counter() - t0)
@@ -995,6 +1111,55 @@ def run_outcore(args, wl, ws, rank, local):
     ctx.close()
 
 
+# Other configurations, measured after the default workload's line is computed (N=1 only), each in a
+# process of its own so that the previous run's device memory is gone: the batched joins, the served
+# request stream and the skewed 64-bit joins.  Their summaries ride on the default line ("also").
+EXTRAS = (
+    ("batched", ["--workload", "batch_4096", "--steps", "3", "--warmup", "1", "--plain-steps", "1"]),
+    ("served", ["--workload", "serve_20000", "--warmup", "1", "--plain-seconds", "8", "--no-sweep"]),
+    ("skewed_u64_theta_0.5", ["--workload", "zipf_4m_64m_t05", "--steps", "10", "--warmup", "3", "--no-e2e"]),
+    ("skewed_u64_theta_1.0", ["--workload", "zipf_4m_64m_t10", "--steps", "10", "--warmup", "3", "--no-e2e"]),
+)
+
+
+def run_extras() -> dict:
+    """Run every EXTRAS configuration through this script and keep a summary of its
+    JSON line (throughput, its comparison, latency and roofline figures)."""
+    out = {}
+    for name, extra in EXTRAS:
+        cmd = [sys.executable, os.path.abspath(__file__), *extra, "--no-cpu-baseline", "--no-clocks", "--no-extras"]
+        t0 = time.perf_counter()
+        try:
+            r = subprocess.run(cmd, capture_output=True, text=True, timeout=600)
+            lines = [x for x in r.stdout.splitlines() if x.startswith("{")]
+            if r.returncode != 0 or not lines:
+                out[name] = {"error": f"exit {r.returncode}: {(r.stderr or r.stdout)[-300:]}"}
+                continue
+            d = json.loads(lines[-1])
+        except Exception as e:  # a failed extra leaves the default line intact
+            out[name] = {"error": repr(e)[:300]}
+            continue
+        rec = {"value": d["value"], "unit": d["unit"], "ms_per_step": d["ms_per_step"], "steps": d["steps"],
+               "workload": d["config"]["workload"], "wall_s": round(time.perf_counter() - t0, 1),
+               "cmd": "python bench.py " + " ".join(extra)}
+        if "roofline" in d and d["roofline"]:
+            rec["roofline_frac"] = d["roofline"].get("frac")
+            rec["roofline_kernel"] = d["roofline"].get("kernel")
+        if "join_roofline" in d:
+            rec["join_roofline_frac"] = d["join_roofline"].get("frac")
+        if "batched_vs_plain" in d:
+            rec.update(plain_value=d["plain"]["value"], batched_vs_plain=d["batched_vs_plain"],
+                       joins=d["config"]["joins"], pairs_per_step=d["config"]["pairs_per_step"])
+        if "served_vs_plain" in d:
+            rec.update(plain_value=d["plain"]["value"], served_vs_plain=d["served_vs_plain"],
+                       requests=d["config"]["requests"], saturated=d["saturated"], at_load=d["at_load"])
+        if d.get("config", {}).get("mode"):
+            rec["mode"] = d["config"]["mode"]
+            rec["pairs_per_step"] = d["config"].get("pairs_per_step")
+        out[name] = rec
+    return out
+
+
 def main():
     args = parse()
     ws, rank, local = dist_env()
@@ -1009,6 +1174,8 @@ def main():
         run_outcore(args, wl, ws, rank, local)
     elif wl.get("kind") == "batch":
         run_batch(args, wl, ws, rank, local)
+    elif wl.get("kind") == "sharded":
+        run_sharded(args, wl, ws, rank, local)
     else:
         run_hj(args, wl, ws, rank, local)
 

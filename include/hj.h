@@ -383,6 +383,23 @@ hj_status hj_prof_reset(hj_ctx *ctx);
 hj_status hj_prof_read(hj_ctx *ctx, hj_prof_entry *entries, int cap, int *n_out);
 uint64_t hj_launch_count(const hj_ctx *ctx);
 
+/* ---------------------------------------------------------------- sharding
+ * The local step of one join sharded over several GPUs (the partitioning of
+ * Alg. 2 applied across GPUs, Sec. 3.1): every GPU splits its slices of R and S
+ * into `nparts` groups, group g of every GPU goes to GPU g (one all-to-all by the
+ * caller's collective library), and each GPU joins what it received -- equal keys
+ * meet on one GPU, so the local joins together are the whole join.
+ * hj_split writes the n tuples of `in` to `out` (device, caller-owned, room for
+ * in->n tuples of in's width, 16-byte aligned, not overlapping `in`) grouped by
+ * group = (high 32 bits of the SplitMix64 finaliser of the key) * nparts >> 32, a
+ * hash that no local join uses (their digits and buckets come from MurmurHash2
+ * and from a Fibonacci multiply), so a GPU's keys still spread over all of its
+ * digits and buckets.  Group g is rows [offsets[g], offsets[g+1]) of `out`;
+ * `offsets` is a HOST array of nparts + 1 entries, filled before the call returns
+ * (it synchronises the context's stream).  Order inside a group is unspecified.
+ * nparts in [1, 4096]; HJ_E_INVALID otherwise or for bad pointers. */
+hj_status hj_split(hj_ctx *ctx, const hj_rel *in, int nparts, void *out, uint64_t *offsets);
+
 /* Host-side fault injection for tests (no GPU fault is involved):
  * hj_debug_fail_alloc makes the n-th device allocation from now fail with
  * HJ_E_NOMEM (n < 0 disarms); hj_debug_bytes_in_use reports the device bytes the

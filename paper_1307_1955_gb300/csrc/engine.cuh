@@ -107,6 +107,8 @@ hj_status partition_pass(hj_ctx *c, int width, const void *in, uint64_t n_total,
                          uint64_t nseg, int shift, int bits, void *out, uint64_t *part_off, int pad,
                          const void *const *seg_ptrs = nullptr);
 uint64_t partition_out_rows(hj_ctx *c, int width, uint64_t n_total, uint64_t nseg, int bits, int pad);
+// Exclusive scan of n uint32 counts into n + 1 uint64 offsets (out[n] = total).
+hj_status scan_counts(hj_ctx *c, const uint32_t *in, uint64_t n, unsigned long long *out);
 
 // --------------------------------------------------------------- output.cu
 // The pair buffer of a materialising join: warps append whole chunks, then

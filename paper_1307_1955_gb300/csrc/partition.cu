@@ -76,7 +76,7 @@ __global__ void __launch_bounds__(kScanThreads) scan_apply_kernel(const uint32_t
     }
 }
 
-static hj_status scan_counts(hj_ctx *c, const uint32_t *in, uint64_t n, unsigned long long *out) {
+hj_status scan_counts(hj_ctx *c, const uint32_t *in, uint64_t n, unsigned long long *out) {
     uint64_t nb = (n + kScanBlock - 1) / kScanBlock;
     if (nb == 0) nb = 1;
     DevBuf partial(c);

@@ -116,6 +116,7 @@ def load_library(path: str = LIB_PATH):
         "hj_debug_fail_alloc": (I32, [V, ctypes.c_int64]),
         "hj_debug_bytes_in_use": (U64, [V]),
         "hj_debug_wait_limit": (I32, [V, U64]),
+        "hj_split": (I32, [V, P(hj_rel), ctypes.c_int, V, P(U64)]),
         "hj_plan": (I32, [V, P(hj_rel), P(hj_rel), P(hj_opts), P(hj_plan_info)]),
         "hj_tune": (I32, [V, P(hj_rel), P(hj_rel), P(hj_opts), ctypes.c_int, P(hj_plan_info)]),
         "hj_tune_clear": (I32, [V]),
@@ -444,6 +445,22 @@ def hj_join_static(R: torch.Tensor, S: torch.Tensor, pairs: torch.Tensor | None,
         e.count = int(cnt.value)
         raise e
     return int(cnt.value), (int(chk[0]), int(chk[1]))
+
+
+def hj_split(ctx: Context, rel: torch.Tensor, nparts: int, out: torch.Tensor | None = None):
+    """Group the tuples of `rel` by the sharding hash into `nparts` groups (see
+    include/hj.h).  Returns (grouped (n, 2) tensor on rel's device, offsets: list of
+    nparts + 1 ints); `out` (same shape and dtype as rel, on its device) is used
+    when given."""
+    r = rel_of(rel)
+    if out is None:
+        out = torch.empty_like(rel)
+    elif out.shape != rel.shape or out.dtype != rel.dtype or not out.is_contiguous() or out.device != rel.device:
+        raise ValueError("out must be a contiguous tensor of rel's shape, dtype and device")
+    offs = (ctypes.c_uint64 * (nparts + 1))()
+    _check(ctx, load_library().hj_split(ctx.handle, ctypes.byref(r), nparts, out.data_ptr() if out.numel() else None,
+                                        offs))
+    return out, [int(x) for x in offs]
 
 
 def hj_result_free(ctx: Context, res: Result):
