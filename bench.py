@@ -88,6 +88,12 @@ WORKLOADS = {
              "over the ranks: each rank holds 1/N of R's and S's rows, splits them by the sharding hash (hj_split), "
              "one all-to-all of R and one of S, a local hj_join, one all-reduce of count and checksums; strong "
              "scaling (the whole job is one join); pairs materialised, left on the rank that found them"),
+    "coproc_16m": dict(
+        kind="coproc", nr=1 << 24, ns=1 << 24, dom=1 << 24, algo=2, shares=24,
+        desc="CPU/GPU co-processing of the paper's default join, |R| = |S| = 2^24 (uint32 key, uint32 rid; R keys a "
+             "permutation of 1..2^24, S keys uniform over them): the PHJ's join step divided between the GPU and "
+             "the host cores (hj_join_coproc) at the cost model's share, and the model (Eq. 1-5) checked against "
+             "measured times at seeded random shares; pairs materialised"),
     "shj_1m": dict(
         nr=1 << 20, ns=1 << 20, dom=1 << 20, algo=1,
         desc="SHJ, |R|=|S|=2^20 (uint32 key, uint32 rid); R keys a permutation of 1..2^20, S keys drawn "
@@ -840,6 +846,100 @@ def run_sharded(args, wl, ws, rank, local):
         dist.destroy_process_group()
 
 
+def run_coproc(args, wl, ws, rank, local):
+    """hj_join_coproc on the paper's default join: per-item costs calibrated at CPU
+    shares 0 and 1, then the cost model's predicted time (hj_coproc_time, steps
+    partition + join, the partition step on the GPU) against the measured time at
+    seeded random shares; the value is the throughput at the model's own share."""
+    import torch
+
+    import __graft_entry__
+
+    torch.cuda.set_device(local)
+    if rank == 0:
+        __graft_entry__.build()
+    from paper_1307_1955_gb300 import hj
+    from paper_1307_1955_gb300 import workload as W
+
+    dev = torch.device("cuda", local)
+    R, S = W.unique_and_uniform(wl["nr"], wl["ns"], wl["dom"], W.DEFAULT_SEED, dev, ids=(67, rank))
+    torch.cuda.synchronize()
+    ctx = hj.Context(local)
+    N = wl["nr"] + wl["ns"]
+
+    def run(share):
+        res, t = hj.hj_join_coproc(ctx, R, S, share)
+        cnt = res.count
+        res.free()
+        return t, cnt
+
+    for _ in range(max(1, args.warmup)):
+        run(0.0)
+    run(1.0)
+    # calibration: GPU per-item costs at share 0, CPU and copy costs at share 1 (medians of 3)
+    t0 = [run(0.0)[0] for _ in range(3)]
+    t1 = [run(1.0)[0] for _ in range(3)]
+    med = lambda xs: statistics.median(xs)
+    g1 = med([t["partition_gpu"] for t in t0]) / N
+    g2 = med([t["join_gpu"] for t in t0]) / N
+    c2 = med([t["join_cpu"] for t in t1]) / N
+    xf = med([t["copy_to_host"] for t in t1]) / N
+    cpu_s, gpu_s, x = [1.0, c2], [g1, g2], [float(N), float(N)]
+    ratios_best, t_best = hj.hj_coproc_ratios(x, cpu_s, gpu_s, xfer_s=xf, delta=0.02)
+    # the model against measured times at seeded random shares (and a few small ones)
+    import random
+    rnd = random.Random(1307)
+    shares = sorted([0.005, 0.01, 0.02, 0.05] + [rnd.random() for _ in range(wl["shares"])])
+    # Eq. 4 lets the CPU start step 2 once the GPU has produced its share of step 1
+    # (r x T1); here the partition pass hands over every partition at its end, so the
+    # CPU waits all of T1: the second prediction uses that wait
+    pts, errs, errs_adj = [], [], []
+    for r in shares:
+        meas = med([run(r)[0]["total"] for _ in range(2)])
+        pred, _, pred_gpu = hj.hj_coproc_time(x, cpu_s, gpu_s, [0.0, r], xfer_s=xf)
+        pred_adj = max(pred_gpu, g1 * N + r * N * (xf + c2))
+        err, err_adj = (pred - meas) / meas, (pred_adj - meas) / meas
+        errs.append(abs(err))
+        errs_adj.append(abs(err_adj))
+        pts.append({"share": r, "measured_s": meas, "predicted_s": pred, "rel_err": err,
+                    "predicted_whole_wait_s": pred_adj, "rel_err_whole_wait": err_adj})
+    # timed: the model's share
+    share = ratios_best[1]
+    sampler = ClockSampler(local)
+    if not args.no_clocks:
+        sampler.start()
+        time.sleep(0.3)
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    for _ in range(args.steps):
+        tt, cnt = run(share)
+    e1.record()
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1)
+    clocks = sampler.stop() if not args.no_clocks else None
+    value = N * args.steps / (ms / 1000.0)
+    if rank == 0:
+        line = {
+            "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "u32", "data": "synthetic",
+            "config": {"workload": wl["desc"], "cpu_share": share, "pairs_per_step": cnt,
+                       "host_cores": host_cores(), "parallelism": f"replicas x{ws}",
+                       "l2": "inputs 268 MB per step exceed the 129 MB L2; no flush"},
+            "model": {"per_item_s": {"partition_gpu": g1, "join_gpu": g2, "join_cpu": c2, "copy_to_host": xf},
+                      "best_shares": ratios_best, "best_predicted_s": t_best,
+                      "mean_abs_rel_err": sum(errs) / len(errs), "max_abs_rel_err": max(errs),
+                      "mean_abs_rel_err_whole_wait": sum(errs_adj) / len(errs_adj),
+                      "max_abs_rel_err_whole_wait": max(errs_adj),
+                      "points": pts,
+                      "measured_best": min(pts, key=lambda q: q["measured_s"])},
+            "roofline": None, "cpu_baseline": None, "e2e": None, "gpu_launches": None, "clocks": clocks,
+        }
+        print(json.dumps(line), flush=True)
+    ctx.close()
+
+
 def serve_pool(wl, rank, dev, pool_bytes: float):
     """Request sizes and arrival order of the whole stream, and the device inputs of
     its first K requests (K as large as pool_bytes allows); request i is served
@@ -1176,6 +1276,8 @@ def main():
         run_batch(args, wl, ws, rank, local)
     elif wl.get("kind") == "sharded":
         run_sharded(args, wl, ws, rank, local)
+    elif wl.get("kind") == "coproc":
+        run_coproc(args, wl, ws, rank, local)
     else:
         run_hj(args, wl, ws, rank, local)
 

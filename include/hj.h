@@ -383,6 +383,24 @@ hj_status hj_prof_reset(hj_ctx *ctx);
 hj_status hj_prof_read(hj_ctx *ctx, hj_prof_entry *entries, int cap, int *n_out);
 uint64_t hj_launch_count(const hj_ctx *ctx);
 
+/* ------------------------------------------------------ CPU/GPU co-processing
+ * The PHJ with its join step divided between the GPU and the host CPU: the
+ * paper's data dividing (DD, Sec. 3.2) applied to the join step, whose share the
+ * cost model (Sec. 4, Eq. 1-5; hj_coproc_time / hj_coproc_ratios) prices.  The GPU
+ * partitions R and S (Alg. 2); the partition pairs holding the first `cpu_share`
+ * of S's rows are copied to page-locked host memory (kept on the context) and
+ * joined by `cpu_threads` host threads (0: one per host core) while the GPU joins
+ * the other pairs.  The result is what hj_join returns -- count, checksums, and in
+ * HJ_MATERIALIZE the pairs in one library-owned device buffer (the CPU's after the
+ * GPU's) -- for the PHJ plan hj_join would pick (or opts' radix bits and passes).
+ * cpu_share in [0, 1]: 0 is the GPU join alone, 1 every partition on the CPU.
+ * times (optional, 5 doubles, seconds measured in this call): GPU partitioning,
+ * GPU join, copy of the CPU's share to the host, CPU join, the whole call.
+ * Synchronises the context's stream.  HJ_E_INVALID for an SHJ algo, a share
+ * outside [0, 1] or cpu_threads < 0. */
+hj_status hj_join_coproc(hj_ctx *ctx, const hj_rel *R, const hj_rel *S, const hj_opts *opts, double cpu_share,
+                         int cpu_threads, hj_result *out, double *times);
+
 /* ---------------------------------------------------------------- sharding
  * The local step of one join sharded over several GPUs (the partitioning of
  * Alg. 2 applied across GPUs, Sec. 3.1): every GPU splits its slices of R and S

@@ -16,7 +16,7 @@ ROOT = os.path.dirname(HERE)
 CSRC = os.path.join(HERE, "csrc")
 OUT = os.path.join(HERE, "_build")
 LIB = os.path.join(OUT, "libhj.so")
-SOURCES = ["ctx.cu", "join.cu", "partition.cu", "output.cu", "api.cu", "static_join.cu", "batch.cu", "server.cu", "tune.cu", "outcore.cu", "keylist.cu", "coproc.cu", "dist.cu"]
+SOURCES = ["ctx.cu", "join.cu", "partition.cu", "output.cu", "api.cu", "static_join.cu", "batch.cu", "server.cu", "tune.cu", "outcore.cu", "keylist.cu", "coproc.cu", "dist.cu", "coexec.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 

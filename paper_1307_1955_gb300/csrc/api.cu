@@ -1,8 +1,10 @@
 // api.cu -- the C ABI of include/hj.h: argument checks, plan choice, and the
 // SHJ / PHJ drivers that sequence the kernels of join.cu and partition.cu.
 #include <algorithm>
-#include <memory>
+#include <chrono>
 #include <cmath>
+#include <memory>
+#include <thread>
 #include <vector>
 
 #include "common.cuh"
@@ -482,9 +484,204 @@ hj_status join_host_pipelined(hj_ctx *c, const hj_rel *Rh, const hj_rel *Sh, con
     return HJ_OK;
 }
 
+// ------------------------------------------------------- CPU/GPU co-processing
+// The PHJ with its join step divided between the GPU and the host CPU (the
+// paper's data dividing, Sec. 3.2, on the join step; coexec.cu has the CPU side).
+// The GPU partitions both relations; the partition pairs [0, p_cpu) -- the first
+// cpu_share of S's rows -- are copied to page-locked host memory by a host thread
+// (its own stream, after the partition passes) and joined there by cpu_threads
+// threads, while the GPU joins the pairs [p_cpu, NP) (the CPU's tasks are emptied
+// first).  The CPU's pairs are then appended to the GPU's in the result buffer.
+
+__global__ void drop_tasks_kernel(PartTask *tasks, uint64_t ntasks, uint32_t p_cpu) {
+    for (uint64_t i = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; i < ntasks; i += (uint64_t)gridDim.x * blockDim.x)
+        if (tasks[i].p < p_cpu) {
+            tasks[i].nr = 0;
+            tasks[i].ns = 0;
+        }
+}
+
+hj_status join_coproc(hj_ctx *c, const hj_rel *R, const hj_rel *S, const hj_opts &o, int bits, int passes,
+                      double cpu_share, int threads, hj_result *res, double *times) {
+    using clk = std::chrono::steady_clock;
+    const auto t_start = clk::now();
+    const bool mat = o.mode == HJ_MATERIALIZE, chk = wants_checksum(o);
+    const int W = R->width;
+    const uint64_t tb = tuple_bytes(W);
+    const int b1 = passes == 2 ? bits - bits / 2 : bits, b2 = passes == 2 ? bits / 2 : 0;
+    if (b1 < 1 || b1 > 12 || b2 < 0 || b2 > 12)
+        return set_err(c, HJ_E_INVALID, "radix bits %d in %d passes: each pass takes 1..12 bits", bits, passes);
+    const uint64_t NP = 1ull << bits;
+    cudaEvent_t ev[4] = {};
+    struct EvGuard {
+        cudaEvent_t *e;
+        ~EvGuard() {
+            for (int i = 0; i < 4; ++i)
+                if (e[i]) cudaEventDestroy(e[i]);
+        }
+    } eg{ev};
+    for (auto &e : ev) HJ_CUDA(c, cudaEventCreate(&e));
+    DevBuf Rp(c), Sp(c), roff(c), soff(c), oversize(c), tasks(c), slot(c);
+    PairSink sink(c, W);
+    uint64_t r_rows = 0, s_rows = 0;
+    HJ_CUDA(c, cudaEventRecord(ev[0], c->stream));
+    HJ_TRY(partition_rel(c, R, b1, b2, 1, Rp, roff, &r_rows));
+    HJ_TRY(partition_rel(c, S, b1, b2, 1, Sp, soff, &s_rows));
+    HJ_CUDA(c, cudaEventRecord(ev[1], c->stream));
+    // partition offsets on the host (this waits for the partition passes)
+    std::vector<uint64_t> ro(NP + 1), so(NP + 1);
+    HJ_CUDA(c, cudaMemcpyAsync(ro.data(), roff.p, (NP + 1) * 8, cudaMemcpyDeviceToHost, c->stream));
+    HJ_CUDA(c, cudaMemcpyAsync(so.data(), soff.p, (NP + 1) * 8, cudaMemcpyDeviceToHost, c->stream));
+    HJ_TRY(read_counters(c));  // synchronises; a partition pass's fault is reported here
+    // the CPU's partitions: the first ones holding cpu_share of S's rows
+    uint32_t p_cpu = 0;
+    if (cpu_share >= 1.0) {
+        p_cpu = (uint32_t)NP;
+    } else if (cpu_share > 0.0) {
+        const double want = cpu_share * (double)(so[NP] - so[0]);
+        while (p_cpu < NP && (double)(so[p_cpu] - so[0]) < want) ++p_cpu;
+    }
+    // host buffers for the CPU's rows, kept on the context
+    const uint64_t rb = (ro[p_cpu] - ro[0]) * tb, sb = (so[p_cpu] - so[0]) * tb;
+    for (int side = 0; side < 2; ++side) {
+        const uint64_t need = side ? sb : rb;
+        if (need && c->host_cap[side] < need) {
+            if (c->host_buf[side]) cudaFreeHost(c->host_buf[side]);
+            c->host_buf[side] = nullptr;
+            c->host_cap[side] = 0;
+            HJ_CUDA(c, cudaMallocHost(&c->host_buf[side], need));
+            c->host_cap[side] = need;
+        }
+    }
+    if (!c->pipe_in) HJ_CUDA(c, cudaStreamCreateWithFlags(&c->pipe_in, cudaStreamNonBlocking));
+    if (!c->cpu_pool) c->cpu_pool = cpu_pool_new();
+    // CPU side: copy the CPU's rows home and join them, beside the GPU's join
+    CpuJoinResult cres;
+    cudaError_t cerr = cudaSuccess;
+    double t_copy = 0.0, t_cpu = 0.0;
+    std::thread cpu_side;
+    if (p_cpu) {
+        cpu_side = std::thread([&, rb, sb, p_cpu]() {
+            const auto t0 = clk::now();
+            cerr = cudaSetDevice(c->device);
+            if (cerr == cudaSuccess && rb)
+                cerr = cudaMemcpyAsync(c->host_buf[0], (const char *)Rp.p + ro[0] * tb, rb, cudaMemcpyDeviceToHost,
+                                       c->pipe_in);
+            if (cerr == cudaSuccess && sb)
+                cerr = cudaMemcpyAsync(c->host_buf[1], (const char *)Sp.p + so[0] * tb, sb, cudaMemcpyDeviceToHost,
+                                       c->pipe_in);
+            if (cerr == cudaSuccess) cerr = cudaStreamSynchronize(c->pipe_in);
+            const auto t1 = clk::now();
+            t_copy = std::chrono::duration<double>(t1 - t0).count();
+            if (cerr != cudaSuccess) return;
+            cpu_join_partitions(c->cpu_pool, W, c->host_buf[0], ro.data(), c->host_buf[1], so.data(), p_cpu, b1, b2,
+                                mat, chk, threads, &cres);
+            t_cpu = std::chrono::duration<double>(clk::now() - t1).count();
+        });
+    }
+    struct Joiner {
+        std::thread &t;
+        ~Joiner() {
+            if (t.joinable()) t.join();
+        }
+    } joiner{cpu_side};
+    // GPU side: the remaining partition pairs, as join_phj does
+    const uint64_t slice = task_slice_rows(W, S->n, NP), ntasks = max_tasks(NP, s_rows, slice);
+    HJ_TRY(oversize.alloc(ntasks * 4));
+    HJ_TRY(tasks.alloc(ntasks * sizeof(PartTask) + 8));
+    HJ_TRY(slot.alloc(sizeof(JoinSlot)));
+    HJ_TRY(make_tasks(c, Rp.p, roff.as<uint64_t>(), Sp.p, soff.as<uint64_t>(), NP, 0, b1, b2, W, slice, ntasks,
+                      tasks.as<PartTask>()));
+    if (p_cpu) {
+        const unsigned grid = (unsigned)std::min<uint64_t>((ntasks + 255) / 256, (uint64_t)num_sms(c) * 8);
+        HJ_LAUNCH(c, "drop_tasks", drop_tasks_kernel, grid ? grid : 1, 256, 0, tasks.as<PartTask>(), ntasks, p_cpu);
+    }
+    const uint64_t warps = partition_join_warps(c);
+    // the GPU's pairs: at most one per S row of its partitions (unique R keys), else resized
+    uint64_t cap = mat ? first_capacity(o, S->n, warps) : 0;
+    HJ_CUDA(c, cudaEventRecord(ev[2], c->stream));
+    for (int attempt = 0; attempt < 2; ++attempt) {
+        if (mat) HJ_TRY(sink.reset(cap));
+        HJ_TRY(run_partition_join(c, R, S, o, Rp.p, roff.as<uint64_t>(), Sp.p, soff.as<uint64_t>(), NP, ntasks, b1, b2,
+                                  &sink, oversize.as<uint32_t>(), tasks.as<PartTask>(), slot.as<JoinSlot>()));
+        if (!mat || (c->h_ctr->cursor <= sink.pcap && c->h_ctr->count <= sink.pcap)) break;
+        cap = c->h_ctr->count + warps * kChunkPairs;
+        if (attempt == 1) return set_err(c, HJ_E_CUDA, "pair capacity still too small after resizing");
+    }
+    HJ_CUDA(c, cudaEventRecord(ev[3], c->stream));
+    const uint64_t g_count = c->h_ctr->count, g_c0 = c->h_ctr->c0, g_c1 = c->h_ctr->c1;
+    if (cpu_side.joinable()) cpu_side.join();
+    if (cerr != cudaSuccess) return cuda_err(c, cerr, "copy of the CPU's partitions");
+    // merge: counts and checksums add; the CPU's pairs follow the GPU's
+    res->count = g_count + cres.count;
+    res->checksum[0] = g_c0 + cres.c0;
+    res->checksum[1] = g_c1 + cres.c1;
+    res->width = W;
+    res->algo = HJ_ALGO_PHJ;
+    res->radix_bits = bits;
+    res->passes = passes;
+    res->pairs = nullptr;
+    res->pairs_cap = 0;
+    if (mat) {
+        if (sink.pcap < res->count) {  // room for both parts
+            DevBuf all(c);
+            HJ_TRY(all.alloc(res->count * tb));
+            if (g_count)
+                HJ_CUDA(c, cudaMemcpyAsync(all.p, sink.pairs.p, g_count * tb, cudaMemcpyDeviceToDevice, c->stream));
+            sink.pairs.reset();
+            sink.pairs.p = all.release();
+            sink.pcap = res->count;
+        }
+        uint64_t at = g_count;
+        for (const auto &v : cres.pairs) {
+            if (v.empty()) continue;
+            HJ_CUDA(c, cudaMemcpyAsync((char *)sink.pairs.p + at * tb, v.data(), v.size(), cudaMemcpyHostToDevice,
+                                       c->stream));
+            at += v.size() / tb;
+        }
+        HJ_CUDA(c, cudaStreamSynchronize(c->stream));
+        res->pairs = sink.pairs.release();
+        res->pairs_cap = sink.pcap;
+    }
+    if (times) {
+        HJ_CUDA(c, cudaEventSynchronize(ev[3]));
+        float ms = 0.f;
+        cudaEventElapsedTime(&ms, ev[0], ev[1]);
+        times[0] = ms / 1e3;
+        cudaEventElapsedTime(&ms, ev[2], ev[3]);
+        times[1] = ms / 1e3;
+        times[2] = t_copy;
+        times[3] = t_cpu;
+        times[4] = std::chrono::duration<double>(clk::now() - t_start).count();
+    }
+    return HJ_OK;
+}
+
 }  // namespace
 
 extern "C" {
+
+hj_status hj_join_coproc(hj_ctx *c, const hj_rel *R, const hj_rel *S, const hj_opts *opts, double cpu_share,
+                         int cpu_threads, hj_result *res, double *times) {
+    HJ_TRY(check_ctx(c));
+    if (!res) return set_err(c, HJ_E_INVALID, "result is NULL");
+    HJ_TRY(check_rel(c, R, "R"));
+    HJ_TRY(check_rel(c, S, "S"));
+    if (R->width != S->width) return set_err(c, HJ_E_INVALID, "R and S widths differ (%d, %d)", R->width, S->width);
+    if (!(cpu_share >= 0.0 && cpu_share <= 1.0)) return set_err(c, HJ_E_INVALID, "cpu_share outside [0, 1]");
+    if (cpu_threads < 0) return set_err(c, HJ_E_INVALID, "cpu_threads %d < 0", cpu_threads);
+    hj_opts o = opts ? *opts : default_opts();
+    if (o.mode < HJ_COUNT || o.mode > HJ_MATERIALIZE) return set_err(c, HJ_E_INVALID, "bad mode %d", o.mode);
+    if (o.algo == HJ_ALGO_SHJ) return set_err(c, HJ_E_INVALID, "co-processing divides the PHJ's join step");
+    if (o.passes < 0 || o.passes > 2) return set_err(c, HJ_E_INVALID, "passes %d not in {1, 2}", o.passes);
+    if (o.radix_bits < 0 || o.radix_bits > 24) return set_err(c, HJ_E_INVALID, "radix bits %d > 24", o.radix_bits);
+    *res = hj_result{};
+    int algo, bits, passes;
+    choose_plan(c, R->width, o.mode, R->n, S->n, HJ_ALGO_PHJ, o.radix_bits, o.passes, &algo, &bits, &passes);
+    int threads = cpu_threads;
+    if (!threads) threads = (int)std::max(1u, std::thread::hardware_concurrency());
+    return join_coproc(c, R, S, o, bits, passes, cpu_share, threads, res, times);
+}
 
 hj_status hj_build(hj_ctx *c, const hj_rel *R, const hj_opts *opts, hj_table **out) {
     HJ_TRY(check_ctx(c));

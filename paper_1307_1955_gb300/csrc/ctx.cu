@@ -275,6 +275,7 @@ hj_status hj_destroy(hj_ctx *c) {
         if (c->cev[i]) cudaEventDestroy(c->cev[i]);
     if (c->pool && c->own_pool) cudaMemPoolDestroy(c->pool);
     if (c->own_stream) cudaStreamDestroy(c->stream);
+    if (c->cpu_pool) hj::cpu_pool_delete(c->cpu_pool);
     delete c;
     return HJ_OK;
 }

@@ -41,6 +41,8 @@ struct CostModel {
 struct TunedPlan {
     int algo, bits, passes;
 };
+struct CpuPool;
+void cpu_pool_delete(CpuPool *p);
 }  // namespace hj
 
 struct hj_ctx {
@@ -85,6 +87,8 @@ struct hj_ctx {
     // page-locked host buffers kept for hj_join_host_large (R side, S side)
     void *host_buf[2] = {nullptr, nullptr};
     uint64_t host_cap[2] = {0, 0};
+    // co-processing: host worker threads (created on first use)
+    hj::CpuPool *cpu_pool = nullptr;
     // test hooks (host-side fault injection)
     int64_t fail_alloc_after = -1;  // fail the N-th allocation from now (0 = next)
     uint64_t wait_limit = 0;        // bounded device waits: passes / polls before giving up (0 = default)

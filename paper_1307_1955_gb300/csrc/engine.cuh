@@ -147,6 +147,26 @@ uint64_t plan_key(int width, bool agg, uint64_t nR, uint64_t nS);
 void choose_plan(hj_ctx *c, int width, int mode, uint64_t nR, uint64_t nS, int algo, int bits, int passes,
                  int *a_out, int *b_out, int *g_out);
 
+// --------------------------------------------------------------- coexec.cu
+// Host threads join partition pairs 0 .. np - 1 of padded partitioned copies in
+// HOST memory (pass bits b1, b2): R rows roff[p] - roff[0] .. roff[p + 1] - roff[0]
+// of `R`, likewise for S.  Counts and checksums add up in `out`; with `mat` each
+// thread's (rid_R, rid_S) pairs (fields of `width` bytes) are in out->pairs[t].
+struct CpuJoinPart {
+    uint64_t count = 0, c0 = 0, c1 = 0;
+};
+struct CpuJoinResult {
+    uint64_t count = 0, c0 = 0, c1 = 0;
+    std::vector<CpuJoinPart> parts;
+    std::vector<std::vector<uint8_t>> pairs;
+};
+struct CpuPool;  // host worker threads, kept on a context
+CpuPool *cpu_pool_new();
+void cpu_pool_delete(CpuPool *p);
+void cpu_join_partitions(CpuPool *pool, int width, const void *R, const uint64_t *roff, const void *S,
+                         const uint64_t *soff, uint32_t np, int b1, int b2, bool mat, bool chk, int threads,
+                         CpuJoinResult *out);
+
 // Tuple bytes of a relation of `width`-byte fields.
 inline uint64_t tuple_bytes(int width) { return 2ull * (uint64_t)width; }
 

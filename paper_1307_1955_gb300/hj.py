@@ -117,6 +117,8 @@ def load_library(path: str = LIB_PATH):
         "hj_debug_bytes_in_use": (U64, [V]),
         "hj_debug_wait_limit": (I32, [V, U64]),
         "hj_split": (I32, [V, P(hj_rel), ctypes.c_int, V, P(U64)]),
+        "hj_join_coproc": (I32, [V, P(hj_rel), P(hj_rel), P(hj_opts), ctypes.c_double, ctypes.c_int, P(hj_result),
+                                 P(ctypes.c_double)]),
         "hj_plan": (I32, [V, P(hj_rel), P(hj_rel), P(hj_opts), P(hj_plan_info)]),
         "hj_tune": (I32, [V, P(hj_rel), P(hj_rel), P(hj_opts), ctypes.c_int, P(hj_plan_info)]),
         "hj_tune_clear": (I32, [V]),
@@ -445,6 +447,21 @@ def hj_join_static(R: torch.Tensor, S: torch.Tensor, pairs: torch.Tensor | None,
         e.count = int(cnt.value)
         raise e
     return int(cnt.value), (int(chk[0]), int(chk[1]))
+
+
+def hj_join_coproc(ctx: Context, R: torch.Tensor, S: torch.Tensor, cpu_share: float, cpu_threads: int = 0,
+                   mode: int = HJ_MATERIALIZE, radix_bits: int = 0, passes: int = 0, out_capacity: int = 0,
+                   checksum: bool = False):
+    """PHJ with the join step divided between the GPU and the host CPU (see
+    include/hj.h).  Returns (Result, times dict in seconds)."""
+    r, s = rel_of(R), rel_of(S)
+    o = _opts(HJ_ALGO_PHJ, mode, radix_bits, passes, out_capacity, checksum)
+    out = hj_result()
+    t = (ctypes.c_double * 5)()
+    _check(ctx, load_library().hj_join_coproc(ctx.handle, ctypes.byref(r), ctypes.byref(s), ctypes.byref(o),
+                                              float(cpu_share), int(cpu_threads), ctypes.byref(out), t))
+    names = ("partition_gpu", "join_gpu", "copy_to_host", "join_cpu", "total")
+    return _result(ctx, out), {k: float(v) for k, v in zip(names, t)}
 
 
 def hj_split(ctx: Context, rel: torch.Tensor, nparts: int, out: torch.Tensor | None = None):
