@@ -124,6 +124,8 @@ def parse():
     ap.add_argument("--plain-seconds", type=float, default=20.0,
                     help="serving: bound on the one-hj_join-per-request comparison run")
     ap.add_argument("--no-sweep", action="store_true", help="serving: skip the offered-load sweep")
+    ap.add_argument("--scatter", default="auto", choices=["auto", "region", "ring"],
+                    help="padded-pass scatter at 2^9..2^11 digits (hj_debug_scatter): auto, or force one kernel")
     return ap.parse_args()
 
 
@@ -456,6 +458,14 @@ def run_reference_batch(args, wl, ws, per_step):
     print(json.dumps(line), flush=True)
 
 
+def force_scatter(hj, ctx, kind: str):
+    """Make the context's padded passes take one scatter kernel (measurement only;
+    results are identical either way)."""
+    if kind != "auto":
+        code = {"region": hj.HJ_SCATTER_REGION, "ring": hj.HJ_SCATTER_RING}[kind]
+        assert hj.load_library().hj_debug_scatter(ctx.handle, code) == hj.HJ_OK
+
+
 def run_hj(args, wl, ws, rank, local):
     import torch
     import torch.distributed as dist
@@ -475,6 +485,7 @@ def run_hj(args, wl, ws, rank, local):
     R, S = make_inputs(wl, rank, dev)
     stream = torch.cuda.current_stream(dev)
     ctx = hj.Context(local, stream=stream)
+    force_scatter(hj, ctx, args.scatter)
     mode = wl.get("mode", hj.HJ_MATERIALIZE)
     w = wl.get("width", 4)
     kw = dict(algo=wl["algo"] if args.algo < 0 else args.algo, radix_bits=args.radix_bits, passes=args.passes,
@@ -600,7 +611,7 @@ def run_hj(args, wl, ws, rank, local):
             "vs_baseline": None, "dtype": "u32" if w == 4 else "u64", "data": "synthetic",
             "config": {"workload": wl["desc"], "algo": {1: "SHJ", 2: "PHJ"}[algo], "radix_bits": bits,
                        "mode": {0: "count", 1: "count+checksum", 2: "pairs materialised"}[mode],
-                       "passes": passes, "plan": "hj_tune" if tuned else "forced",
+                       "passes": passes, "plan": "hj_tune" if tuned else "forced", "scatter": args.scatter,
                        "tuned": tuned, "pairs_per_step": count, "parallelism": f"replicas x{ws}",
                        "l2": f"inputs {tb * n / 1e9:.2f} GB per step exceed the 129 MB L2; no flush"
                        if tb * n > 129e6 else "inputs smaller than L2; warm L2 across steps"},

@@ -425,13 +425,24 @@ hj_status hj_split(hj_ctx *ctx, const hj_rel *in, int nparts, void *out, uint64_
 hj_status hj_debug_fail_alloc(hj_ctx *ctx, int64_t n);
 uint64_t hj_debug_bytes_in_use(const hj_ctx *ctx);
 /* Test hook for the bounded device waits (the paper has no counterpart): the
- * partition scatter at 2^11 digits for 4-byte tuples runs flush warps that wait
+ * ring partition scatter (2^9 .. 2^11 digits) runs flush warps that wait
  * on the CTA's insert warps; after n passes (default 2^22; n = 0 restores it) they
  * give up, set a sticky fault bit and return, and the call that reads the
  * counters next returns HJ_E_TIMEOUT (its results are then undefined).  The fault
  * is reported once; later calls on the context run normally.  Only the limit
  * changes: no GPU fault is involved.  HJ_E_INVALID for a NULL context. */
 hj_status hj_debug_wait_limit(hj_ctx *ctx, uint64_t n);
+/* Test and measurement hook: which kernel scatters a padded partition pass at
+ * 2^9 .. 2^11 digits.  HJ_SCATTER_AUTO (the default) takes the ring scatter where
+ * it measured faster than the region scatter (4-byte tuples at 2^10 and 2^11
+ * digits, 8-byte tuples at 2^9 .. 2^11) and the region scatter elsewhere; HJ_SCATTER_REGION and HJ_SCATTER_RING force one
+ * (other fan-outs always take the region scatter).  Results are identical either
+ * way; only the kernel changes.  HJ_E_INVALID for a NULL context or another
+ * value. */
+#define HJ_SCATTER_AUTO 0
+#define HJ_SCATTER_REGION 1
+#define HJ_SCATTER_RING 2
+hj_status hj_debug_scatter(hj_ctx *ctx, int kind);
 
 #ifdef __cplusplus
 }

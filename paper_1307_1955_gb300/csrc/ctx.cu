@@ -348,4 +348,11 @@ hj_status hj_debug_wait_limit(hj_ctx *c, uint64_t n) {
     return HJ_OK;
 }
 
+/* Measurement hook: force the region or the ring scatter (HJ_SCATTER_*). */
+hj_status hj_debug_scatter(hj_ctx *c, int kind) {
+    if (!c || kind < HJ_SCATTER_AUTO || kind > HJ_SCATTER_RING) return HJ_E_INVALID;
+    c->scatter_kind = kind;
+    return HJ_OK;
+}
+
 }  // extern "C"

@@ -917,24 +917,27 @@ static hj_status launch_region(hj_ctx *c, unsigned grid, const void *in, uint64_
 }
 
 // ------------------------------------------------------------- ring scatter
-// 4-byte tuples at 2^11 digits (the join's usual fan-out): the insert and flush
-// work of the region scatter split between warps that run at the same time, with
-// no barrier after the set-up.  Digit d owns a ring of kRingK slots (slot j at
-// ring[j * P + d], empty slots hold a key of another digit) and one packed word,
-// claimed | flushed << 16: positions claimed and positions flushed, both counted
-// modulo kRingMod (a multiple of kRingK and of the sector, so a position's slot
-// is the same in every lap of the count).
+// Padded passes at a high fan-out (2^9 .. 2^11 digits): the insert and flush work
+// of the region scatter split between warps that run at the same time, with no
+// barrier after the set-up.  Digit d owns a ring of K slots (slot j at
+// ring[j * P + d], a slot holding one tuple; empty slots hold a key of another
+// digit) and one packed word, claimed | flushed << 16: positions claimed and
+// positions flushed, both counted modulo M (a multiple of K and of the sector, so
+// a position's slot is the same in every lap of the count).
 //   * An insert warp streams its own blocks of the chunk.  A tuple reads its
-//     digit's word once (acquire) and, while claimed - flushed < kRingK, claims
-//     position w with one CAS of the word and stores itself in slot w mod kRingK
-//     (key and rid in one 8-byte store); with the ring full it is written from
-//     the run's far end, as in the region scatter.
+//     digit's word once (acquire) and, while claimed - flushed < K, claims
+//     position w with one CAS of the word and stores itself in slot w mod K; with
+//     the ring full it is written from the run's far end, as in the region
+//     scatter.  A 4-byte tuple is one 8-byte store; an 8-byte tuple stores its
+//     rid, then its key with release semantics (a flush lane reads the key with
+//     acquire, so a key it sees comes with its rid).
 //   * A flush lane owns a set of digits (consecutive digits across a warp's lanes,
-//     so its slot accesses do not conflict).  Once the four claimed positions at
-//     the flushed count all hold tuples, it writes them as one 32-byte sector at
-//     the run's next row, empties the slots, then adds the sector to the flushed
-//     half with a release add (inserts read the word with acquire, so a slot is
-//     refilled only after it was emptied).  Only that lane writes the flushed half.
+//     so its slot accesses do not conflict).  Once the claimed positions of one
+//     sector at the flushed count all hold tuples, it writes them as one 32-byte
+//     sector at the run's next row, empties the slots, then adds the sector to
+//     the flushed half with a release add (inserts read the word with acquire, so
+//     a slot is refilled only after it was emptied).  Only that lane writes the
+//     flushed half.
 //   * When every insert warp is done (release / acquire on a counter) the flush
 //     lanes write what is left of each ring, then padding, into the run's gap.
 // One packed word instead of two cursors saves an insert one shared load: the
@@ -943,16 +946,27 @@ static hj_status launch_region(hj_ctx *c, unsigned grid, const void *in, uint64_
 // the context's test setting) sets the timeout bit of the sticky fault word and
 // returns; insert warps never wait, so the CTA still ends.
 constexpr int kRingThreads = 1024;
-constexpr int kRingFlushWarps = 4;                 // 4 of 32 warps flush (2 fall behind, 8 slow the inserts)
-constexpr uint32_t kRingK = 12;                    // three sectors per digit
-constexpr uint32_t kRingMod = 65532;               // 12 * 5461: positions modulo this, in 16 bits
 constexpr uint32_t kRingMaxClaim = 64;             // CAS attempts before the far-end path
 constexpr uint64_t kRingMaxPasses = 1ull << 22;    // flush passes before the timeout bit
 constexpr int kRingVec = 4;                        // 16-byte vectors per lane in flight
 
-template <int LOG2P> struct RingShape {
+template <int W, int LOG2P> struct RingShape {
     static constexpr uint32_t P = 1u << LOG2P;
-    static constexpr size_t kSmem = (size_t)kRingK * P * 8 + (size_t)P * 12 + 16;
+    static constexpr uint32_t SV = (uint32_t)Sector<W>::kTuples;
+    static constexpr size_t kSlot = 2 * W;
+    static constexpr size_t kBudget = 227u * 1024u - 1024u;  // dynamic shared memory
+    // slots per digit: whole sectors in what the ring may use (12 for 4-byte tuples
+    // at 2^11 digits, 6 for 8-byte ones), at most 64
+    static constexpr uint32_t K0 = (uint32_t)((kBudget - (size_t)P * 12 - 16) / ((size_t)P * kSlot)) / SV * SV;
+    static constexpr uint32_t K = K0 > 64 ? 64 : K0;
+    static constexpr uint32_t M = 65535u / K * K;  // positions modulo M: whole laps, in 16 bits
+    static constexpr size_t kSmem = (size_t)K * P * kSlot + (size_t)P * 12 + 16;
+    // flush warps of the 32 (measured): 4 for 4-byte tuples (2 fall behind, 6 or 8
+    // slow the inserts); 8-byte tuples flush a sector per two tuples, twice as
+    // often: 8 at 2^10 and 2^11 digits, 6 at 2^9
+    static constexpr int FW = W == 4 ? 4 : (LOG2P == 9 ? 6 : 8);
+    static_assert(K >= 2 * SV, "a ring holds at least two sectors");
+    static_assert(M % SV == 0, "the flushed count wraps on a sector");
 };
 
 __device__ __forceinline__ uint32_t ld_acquire_cta(const uint32_t *p) {
@@ -960,20 +974,33 @@ __device__ __forceinline__ uint32_t ld_acquire_cta(const uint32_t *p) {
     asm volatile("ld.acquire.cta.shared.u32 %0, [%1];" : "=r"(v) : "r"((uint32_t)__cvta_generic_to_shared(p)) : "memory");
     return v;
 }
+__device__ __forceinline__ unsigned long long ld_acquire_cta_u64(const unsigned long long *p) {
+    unsigned long long v;
+    asm volatile("ld.acquire.cta.shared.u64 %0, [%1];" : "=l"(v) : "r"((uint32_t)__cvta_generic_to_shared(p)) : "memory");
+    return v;
+}
+__device__ __forceinline__ void st_release_cta_u64(unsigned long long *p, unsigned long long v) {
+    asm volatile("st.release.cta.shared.u64 [%0], %1;" ::"r"((uint32_t)__cvta_generic_to_shared(p)), "l"(v) : "memory");
+}
 __device__ __forceinline__ void red_release_add_cta(uint32_t *p, uint32_t v) {
     asm volatile("red.release.cta.shared::cta.add.u32 [%0], %1;" ::"r"((uint32_t)__cvta_generic_to_shared(p)), "r"(v)
                  : "memory");
 }
 
-template <int LOG2P>
+template <int W, int LOG2P>
 __global__ void __launch_bounds__(kRingThreads, 1) scatter_ring_kernel(
     const void *in, uint64_t n_total, const uint64_t *seg_off, uint64_t nseg, const unsigned long long *cb,
     uint64_t chunk, int shift, const unsigned long long *Hs, void *out, uint64_t sent_k0, uint64_t sent_k1,
     const void *const *seg_ptrs, unsigned long long *fault, uint64_t max_passes) {
-    constexpr uint32_t P = 1u << LOG2P, K = kRingK, SV = 4, M = kRingMod;
-    constexpr unsigned NI = kRingThreads / 32 - kRingFlushWarps, NFL = kRingFlushWarps * 32;
+    using U = typename Tup<W>::U;
+    using Vec = typename Tup<W>::Vec;
+    using RS = RingShape<W, LOG2P>;
+    using Slot = typename SortSlot<W>::T;  // 8 bytes (key | rid << 32) or 16 (key, rid)
+    constexpr uint32_t P = RS::P, K = RS::K, SV = RS::SV, M = RS::M;
+    constexpr uint32_t PV = (uint32_t)Tup<W>::kPerVec;
+    constexpr unsigned NI = kRingThreads / 32 - RS::FW, NFL = RS::FW * 32;
     extern __shared__ __align__(16) unsigned char smem[];
-    unsigned long long *ring = (unsigned long long *)smem;  // K * P, slot j of digit d at ring[j * P + d]
+    Slot *ring = (Slot *)smem;                              // K * P, slot j of digit d at ring[j * P + d]
     uint32_t *word = (uint32_t *)(ring + (size_t)K * P);   // P: claimed | flushed << 16 (mod M)
     uint32_t *nxt = word + P;                               // P: next output row of the run
     uint32_t *tail = nxt + P;                               // P: rows at and above hold far-end tuples
@@ -988,28 +1015,31 @@ __global__ void __launch_bounds__(kRingThreads, 1) scatter_ring_kernel(
     const ChunkPos cp = chunk_pos(seg_off, nseg, cb, chunk, g);
     const uint64_t row = cb[cp.s] * P;
     const uint64_t obase = (seg_off[0] + Hs[row]) / SV * SV;
-    unsigned long long *outp = (unsigned long long *)out + obase;
+    Slot *outp = (Slot *)out + obase;
     const void *src = seg_ptrs ? seg_ptrs[cp.s] : in;
     const uint64_t ioff = seg_ptrs ? seg_off[cp.s] : 0;
-    const uint4 *vsrc = (const uint4 *)src + (cp.lo - ioff) / 2;  // chunks start on whole vectors
+    const Vec *vsrc = (const Vec *)src + (cp.lo - ioff) / PV;  // chunks start on whole vectors
     const uint32_t nrows = (uint32_t)(cp.hi - cp.lo);
-    const uint32_t dk0 = (uint32_t)(key_hash<4>((uint32_t)sent_k0) >> shift) & (P - 1u);
-    auto empty_of = [&](uint32_t d) -> uint32_t { return d != dk0 ? (uint32_t)sent_k0 : (uint32_t)sent_k1; };
+    const uint32_t dk0 = (uint32_t)(key_hash<W>((U)sent_k0) >> shift) & (P - 1u);
+    auto empty_key = [&](uint32_t d) -> U { return d != dk0 ? (U)sent_k0 : (U)sent_k1; };
+    auto empty_slot = [&](uint32_t d) -> Slot {
+        if constexpr (W == 4) return (unsigned long long)empty_key(d);
+        else return make_ulonglong2(empty_key(d), 0ull);
+    };
     for (uint32_t d = threadIdx.x; d < P; d += kRingThreads) {
         const uint64_t i = row + (uint64_t)d * cp.nch + cp.cidx;  // the run of (this chunk, d)
         nxt[d] = (uint32_t)(seg_off[0] + Hs[i] - obase);
         tail[d] = (uint32_t)(seg_off[0] + Hs[i + 1] - obase);
         word[d] = 0;
     }
-    for (uint32_t i = threadIdx.x; i < K * P; i += kRingThreads) ring[i] = empty_of(i & (P - 1u));
+    for (uint32_t i = threadIdx.x; i < K * P; i += kRingThreads) ring[i] = empty_slot(i & (P - 1u));
     if (threadIdx.x == 0) *s_done = 0;
     __syncthreads();
     const unsigned warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
 
     if (warp < NI) {
-        auto put = [&](uint32_t k, uint32_t rid) {
-            const unsigned long long sl = (unsigned long long)k | ((unsigned long long)rid << 32);
-            const uint32_t d = (uint32_t)(key_hash<4>(k) >> shift) & (P - 1u);
+        auto put = [&](U k, U rid) {
+            const uint32_t d = (uint32_t)(key_hash<W>(k) >> shift) & (P - 1u);
             for (uint32_t it = 0; it < kRingMaxClaim; ++it) {
                 const uint32_t v = ld_acquire_cta(&word[d]);
                 const uint32_t w = v & 0xFFFFu, f = v >> 16;
@@ -1017,24 +1047,37 @@ __global__ void __launch_bounds__(kRingThreads, 1) scatter_ring_kernel(
                 if (used >= K) break;
                 const uint32_t w1 = w + 1u == M ? 0u : w + 1u;
                 if (atomicCAS(&word[d], v, (v & 0xFFFF0000u) | w1) == v) {
-                    ring[(size_t)(w % K) * P + d] = sl;
+                    Slot *s = &ring[(size_t)(w % K) * P + d];
+                    if constexpr (W == 4) {
+                        *s = (unsigned long long)k | ((unsigned long long)rid << 32);
+                    } else {
+                        s->y = rid;
+                        st_release_cta_u64(&s->x, k);
+                    }
                     return;
                 }
             }
+            Slot sl;
+            if constexpr (W == 4) sl = (unsigned long long)k | ((unsigned long long)rid << 32);
+            else sl = make_ulonglong2(k, rid);
             outp[atomicSub(&tail[d], 1u) - 1u] = sl;
         };
-        const uint32_t nvec = (nrows + 1u) / 2u;
+        const uint32_t nvec = (nrows + PV - 1u) / PV;
         for (uint32_t b = warp * (32u * kRingVec); b < nvec; b += NI * 32u * kRingVec) {
-            uint4 x[kRingVec];
+            Vec x[kRingVec];
 #pragma unroll
             for (int j = 0; j < kRingVec; ++j) {
                 const uint32_t v = b + (uint32_t)j * 32u + lane;
                 if (v < nvec) {
-                    if (2u * v + 1u < nrows) {
-                        x[j] = ld_stream(vsrc + v);
+                    if constexpr (W == 4) {
+                        if (2u * v + 1u < nrows) {
+                            x[j] = ld_stream(vsrc + v);
+                        } else {  // the last tuple alone: nothing past the array end is read
+                            const uint2 y = ((const uint2 *)vsrc)[2u * v];
+                            x[j] = make_uint4(y.x, y.y, 0u, 0u);
+                        }
                     } else {
-                        const uint2 y = ((const uint2 *)vsrc)[2u * v];
-                        x[j] = make_uint4(y.x, y.y, 0u, 0u);
+                        x[j] = ld_stream(vsrc + v);
                     }
                 }
             }
@@ -1042,8 +1085,12 @@ __global__ void __launch_bounds__(kRingThreads, 1) scatter_ring_kernel(
             for (int j = 0; j < kRingVec; ++j) {
                 const uint32_t v = b + (uint32_t)j * 32u + lane;
                 if (v < nvec) {
-                    put(x[j].x, x[j].y);
-                    if (2u * v + 1u < nrows) put(x[j].z, x[j].w);
+                    if constexpr (W == 4) {
+                        put(x[j].x, x[j].y);
+                        if (2u * v + 1u < nrows) put(x[j].z, x[j].w);
+                    } else {
+                        put(x[j].x, x[j].y);
+                    }
                 }
             }
         }
@@ -1064,19 +1111,33 @@ __global__ void __launch_bounds__(kRingThreads, 1) scatter_ring_kernel(
             const uint32_t w = v & 0xFFFFu, f = v >> 16;
             const uint32_t used = w >= f ? w - f : w + M - f;
             if (used < SV) continue;
-            const uint32_t s0 = f % K, ek = empty_of(d);
-            unsigned long long t[SV];
+            const uint32_t s0 = f % K;
+            const U ek = empty_key(d);
+            unsigned long long t[4];  // the sector: 4 x (key | rid << 32) or 2 x (key, rid)
             bool full = true;
 #pragma unroll
             for (uint32_t q = 0; q < SV; ++q) {
-                t[q] = *(volatile unsigned long long *)&ring[(size_t)(s0 + q) * P + d];
-                full &= (uint32_t)t[q] != ek;
+                Slot *s = &ring[(size_t)(s0 + q) * P + d];
+                if constexpr (W == 4) {
+                    t[q] = *(volatile unsigned long long *)s;
+                    full &= (uint32_t)t[q] != ek;
+                } else {
+                    t[2 * q] = ld_acquire_cta_u64(&s->x);
+                    full &= t[2 * q] != ek;
+                }
             }
             if (!full) continue;  // a claimed slot is not written yet
+            if constexpr (W == 8) {
+#pragma unroll
+                for (uint32_t q = 0; q < SV; ++q) t[2 * q + 1] = *(volatile unsigned long long *)&ring[(size_t)(s0 + q) * P + d].y;
+            }
             const uint32_t o = nxt[d];
             st_sector(outp + o, t);
 #pragma unroll
-            for (uint32_t q = 0; q < SV; ++q) ring[(size_t)(s0 + q) * P + d] = ek;
+            for (uint32_t q = 0; q < SV; ++q) {
+                if constexpr (W == 4) ring[(size_t)(s0 + q) * P + d] = (unsigned long long)ek;
+                else ring[(size_t)(s0 + q) * P + d].x = ek;
+            }
             nxt[d] = o + SV;
             // the slots are empty before the flushed count says so (release)
             red_release_add_cta(&word[d], (f + SV == M ? SV - M : SV) << 16);
@@ -1094,7 +1155,7 @@ __global__ void __launch_bounds__(kRingThreads, 1) scatter_ring_kernel(
         const uint32_t v = word[d], w = v & 0xFFFFu, f = v >> 16;
         const uint32_t used = w >= f ? w - f : w + M - f;
         const uint32_t hd = nxt[d], tl = tail[d];
-        const unsigned long long pad = empty_of(d);
+        const Slot pad = empty_slot(d);
         for (uint32_t r = hd; r < tl; ++r) {
             const uint32_t q = r - hd;
             outp[r] = q < used ? ring[(size_t)((f + q) % K) * P + d] : pad;
@@ -1102,17 +1163,30 @@ __global__ void __launch_bounds__(kRingThreads, 1) scatter_ring_kernel(
     }
 }
 
-template <int LOG2P>
+template <int W, int LOG2P>
 static hj_status launch_ring(hj_ctx *c, unsigned grid, const void *in, uint64_t n_total, const uint64_t *seg_off,
                              uint64_t nseg, const unsigned long long *cb, uint64_t chunk, int shift,
                              const unsigned long long *Hs, void *out, uint64_t k0, uint64_t k1,
                              const void *const *seg_ptrs) {
-    auto kern = scatter_ring_kernel<LOG2P>;
+    auto kern = scatter_ring_kernel<W, LOG2P>;
     HJ_TRY(allow_max_smem(c, (const void *)kern));
     const uint64_t passes = c->wait_limit ? std::min<uint64_t>(c->wait_limit, kRingMaxPasses) : kRingMaxPasses;
-    HJ_LAUNCH(c, "partition_scatter", kern, grid, kRingThreads, RingShape<LOG2P>::kSmem, in, n_total, seg_off, nseg,
-              cb, chunk, shift, Hs, out, k0, k1, seg_ptrs, &c->d_ctr->fault, passes);
+    constexpr size_t smem = RingShape<W, LOG2P>::kSmem;
+    HJ_LAUNCH(c, "partition_scatter", kern, grid, kRingThreads, smem, in, n_total, seg_off,
+              nseg, cb, chunk, shift, Hs, out, k0, k1, seg_ptrs, &c->d_ctr->fault, passes);
     return HJ_OK;
+}
+
+// Which padded-pass scatter runs at a fan-out: the ring where it measured faster
+// than the region kernel (per launch at 2^23 x 2^27 uniform 4-byte tuples and the
+// 2^22 x 2^26 Zipf 8-byte workload: 4-byte 0.34 / 0.35 ms against 0.40 / 0.40 at
+// 2^11 / 2^10 digits, a tie at 2^9; 8-byte 0.33 / 0.32 / 0.37 against 0.39 / 0.48
+// / 0.42 at 2^11 / 2^10 / 2^9), unless the context forces one (hj_debug_scatter).
+static bool use_ring(const hj_ctx *c, int width, int bits) {
+    if (bits < 9 || bits > 11) return false;
+    if (c->scatter_kind == HJ_SCATTER_REGION) return false;
+    if (c->scatter_kind == HJ_SCATTER_RING) return true;
+    return width == 8 || bits >= 10;
 }
 
 template <int W>
@@ -1123,14 +1197,22 @@ static hj_status launch_region_bits(hj_ctx *c, int bits, unsigned grid, const vo
 #define HJ_RG(B)                                                                                                 \
     case B:                                                                                                      \
         return launch_region<W, B>(c, grid, in, n_total, seg_off, nseg, cb, chunk, shift, Hs, out, k0, k1, seg_ptrs)
-    if (W == 4 && bits == 11)
-        return launch_ring<11>(c, grid, in, n_total, seg_off, nseg, cb, chunk, shift, Hs, out, k0, k1, seg_ptrs);
+#define HJ_RI(B)                                                                                                 \
+    case B:                                                                                                      \
+        return launch_ring<W, B>(c, grid, in, n_total, seg_off, nseg, cb, chunk, shift, Hs, out, k0, k1, seg_ptrs)
+    if (use_ring(c, W, bits)) {
+        switch (bits) {
+            HJ_RI(9); HJ_RI(10); HJ_RI(11);
+            default: break;
+        }
+    }
     switch (bits) {
         HJ_RG(1); HJ_RG(2); HJ_RG(3); HJ_RG(4); HJ_RG(5); HJ_RG(6);
         HJ_RG(7); HJ_RG(8); HJ_RG(9); HJ_RG(10); HJ_RG(11);
         default: return set_err(c, HJ_E_INVALID, "region scatter takes 1..11 bits, not %d", bits);
     }
 #undef HJ_RG
+#undef HJ_RI
 }
 
 // ------------------------------------------------------------------- driver

@@ -54,6 +54,14 @@ def test_profiling_calls_reject_a_null_context_without_a_gpu(lib):
         assert f(*args) == 1, name  # HJ_E_INVALID
 
 
+def test_debug_hooks_reject_a_null_context_without_a_gpu(lib):
+    for name, args in (("hj_debug_wait_limit", (None, ctypes.c_uint64(5))), ("hj_debug_scatter", (None, 0)),
+                       ("hj_debug_scatter", (None, 2)), ("hj_debug_fail_alloc", (None, ctypes.c_int64(1)))):
+        f = getattr(lib, name)
+        f.restype = ctypes.c_int32
+        assert f(*args) == 1, name  # HJ_E_INVALID
+
+
 def test_server_calls_reject_null_handles_without_a_gpu(lib):
     for name, args in (("hj_server_create", (None, None, None)), ("hj_server_submit", (None, None, None, 0, None)),
                        ("hj_server_poll", (None, 1, None, None)), ("hj_server_destroy", (None,)),

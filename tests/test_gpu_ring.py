@@ -1,10 +1,13 @@
-"""The partition scatter that 4-byte joins take at 2^11 digits -- the plan the tuner
-picks for the 2^24 x 2^28 join -- against the CPU oracle, element by element, on
-inputs that drive each of its paths: rings that overflow to the far end of their
-run (keys crowded into two digits), duplicate build keys, a batch whose group
-partitions on 11 bits (the per-segment input path), and its bounded wait made to
-run out on purpose (a short limit; the kernel returns and the host reports
-HJ_E_TIMEOUT, no GPU fault).  Join results are integers: every comparison is
+"""The ring scatter -- the partition scatter that 4-byte joins take at 2^11 digits
+(the plan the tuner picks for the 2^24 x 2^28 join) and 2^10, and 8-byte joins at
+2^9 .. 2^11 -- against the CPU oracle,
+element by element, on inputs that drive each of its paths: rings that overflow to
+the far end of their run (keys crowded into two digits), duplicate build keys, a
+batch whose group partitions on 11 bits (the per-segment input path), and its
+bounded wait made to run out on purpose (a short limit; the kernel returns and the
+host reports HJ_E_TIMEOUT, no GPU fault).  hj_debug_scatter forces the ring or the
+region scatter, and both kernels are checked at every width and fan-out the ring
+is built for, on ragged sizes and on crowded digits.  Join results are integers: every comparison is
 exact."""
 import numpy as np
 import pytest
@@ -62,13 +65,57 @@ def _check(hjm, ctx, R, S, **kw):
             assert r2.checksum == (c0, c1)
 
 
-def _keys_of_digits(digits, n_keys: int) -> np.ndarray:
-    """Keys among 1..n_keys whose 11-bit pass-one digit is in `digits`, found with
-    the oracle's own partitioner (MurmurHash2 pinned by SMHasher's values)."""
-    keys = np.arange(1, n_keys + 1, dtype=np.uint32)
+def _keys_of_digits(digits, n_keys: int, bits: int = 11, dtype=np.uint32) -> np.ndarray:
+    """Keys among 1..n_keys whose pass-one digit at `bits` is in `digits`, found
+    with the oracle's own partitioner (MurmurHash2 pinned by SMHasher's values)."""
+    keys = np.arange(1, n_keys + 1, dtype=dtype)
     rel = np.stack([keys, keys], 1)
-    out, off = oracle.radix_partition(rel, 11)
+    out, off = oracle.radix_partition(rel, bits)
     return np.concatenate([out[int(off[d]):int(off[d + 1]), 0] for d in digits])
+
+
+def _view(a: np.ndarray) -> torch.Tensor:
+    dt = np.int32 if a.dtype == np.uint32 else np.int64
+    return torch.from_numpy(np.ascontiguousarray(a).view(dt)).to(DEV)
+
+
+RING_FANOUTS = [(4, 9), (4, 10), (4, 11), (8, 9), (8, 10), (8, 11)]
+
+
+@pytest.mark.parametrize("kind", ["region", "ring"])
+@pytest.mark.parametrize("width,bits", RING_FANOUTS)
+def test_both_scatters_at_every_ring_fanout(hjm, width, bits, kind):
+    # ragged sizes spread over every SM's chunk; 4-byte: unique R keys, S over twice
+    # their range; 8-byte: Zipf keys on both sides (duplicate build keys)
+    forced = hjm.HJ_SCATTER_REGION if kind == "region" else hjm.HJ_SCATTER_RING
+    if width == 4:
+        R, S = W.unique_and_uniform(300_007, 2_000_003, 600_014, SEED, DEV, ids=(45, bits))
+    else:
+        R, S = W.zipf_pair(120_011, 900_007, 0.75, 0.5, 1 << 16, SEED, DEV, ids=(45, bits))
+    lib = hjm.load_library()
+    with hjm.Context(0) as c:
+        assert lib.hj_debug_scatter(c.handle, forced) == hjm.HJ_OK
+        _check(hjm, c, R, S, algo=hjm.HJ_ALGO_PHJ, radix_bits=bits, passes=1)
+
+
+@pytest.mark.parametrize("width,bits", RING_FANOUTS)
+def test_ring_with_crowded_digits_at_every_fanout(hjm, width, bits):
+    # every tuple in digit 3 or in the last digit: two rings overflow at once and
+    # most tuples take the far-end path; R holds each key once or twice
+    dt = np.uint32 if width == 4 else np.uint64
+    keys = _keys_of_digits((3, (1 << bits) - 1), 1 << 20, bits, dt)
+    assert len(keys) > 500
+    rng = np.random.default_rng(46 + bits)
+    rk = np.concatenate([keys, keys[: len(keys) // 3]])
+    rk = rk[rng.permutation(len(rk))]
+    R = np.stack([rk, np.arange(len(rk), dtype=dt)], 1)
+    sk = rng.choice(keys, 400_009).astype(dt)
+    sk[::5] = np.setdiff1d(np.arange(1, 200, dtype=dt), keys)[0]  # a key R does not hold
+    S = np.stack([sk, np.arange(len(sk), dtype=dt)], 1)
+    lib = hjm.load_library()
+    with hjm.Context(0) as c:
+        assert lib.hj_debug_scatter(c.handle, hjm.HJ_SCATTER_RING) == hjm.HJ_OK
+        _check(hjm, c, _view(R), _view(S), algo=hjm.HJ_ALGO_PHJ, radix_bits=bits, passes=1)
 
 
 @pytest.mark.parametrize("ns", [200_003, 1_000_001])
