@@ -33,8 +33,8 @@ int join_bits(uint64_t nR) {
 }
 
 __global__ void batch_tasks_kernel(const void *Rp, const uint64_t *roff, const void *Sp, const uint64_t *soff,
-                                   const uint32_t *join_ids, uint64_t ngroup, int bits, uint64_t ek1, int tb,
-                                   PartTask *tasks) {
+                                   const uint32_t *join_ids, uint64_t ngroup, int bits, uint64_t ek1, uint64_t pk1,
+                                   int tb, PartTask *tasks) {
     const uint64_t P = 1ull << bits, n = ngroup * P;
     for (uint64_t i = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; i < n; i += (uint64_t)gridDim.x * blockDim.x) {
         const uint64_t g = i >> bits, p = i & (P - 1);
@@ -49,6 +49,8 @@ __global__ void batch_tasks_kernel(const void *Rp, const uint64_t *roff, const v
         t.b2 = 0;
         t.pad = 0;
         t.ek1 = ek1;
+        t.pk1 = pk1;
+        t.pk2 = 0;
         tasks[i] = t;
     }
 }
@@ -149,7 +151,8 @@ hj_status launch_wave(hj_ctx *c, int W, const JoinSlot *slots, bool agg, bool ch
         const uint64_t n = ng * P;
         const unsigned grid = (unsigned)std::min<uint64_t>((n + 255) / 256, (uint64_t)num_sms(c) * 8);
         HJ_LAUNCH(c, "batch_tasks", batch_tasks_kernel, grid ? grid : 1, 256, 0, Rp->p, roff->as<uint64_t>(), Sp->p,
-                  soff->as<uint64_t>(), g->jid.as<uint32_t>(), ng, g->bits, empty_key2(W, g->bits, 0), (int)tb,
+                  soff->as<uint64_t>(), g->jid.as<uint32_t>(), ng, g->bits, empty_key2(W, g->bits, 0),
+                  pass_pad_key(W, 0, g->bits), (int)tb,
                   w.tasks->as<PartTask>() + task_at);
         task_at += n;
     }

@@ -53,6 +53,10 @@ struct PartTask {
     uint16_t b1, b2;
     uint32_t pad;
     uint64_t ek1;  // second empty-slot marker candidate for (b1, b2)
+    // Keys a padding row of this partition can carry: 0 and each padded pass's
+    // second sentinel (pass_pad_key); a build row with another key is a real tuple
+    // of the partition and needs no hash to be kept.
+    uint64_t pk1, pk2;
 };
 // Output of one join: its pair buffer and its counters.
 struct JoinSlot {
@@ -62,6 +66,9 @@ struct JoinSlot {
     unsigned long long pad;
 };
 uint64_t empty_key2(int width, int b1, int b2);
+// The second padding key of a padded pass over `bits` digits from bit `shift`
+// (the first is 0): the smallest key whose digit differs from 0's.
+uint64_t pass_pad_key(int width, int shift, int bits);
 // Tasks for one join's NP partitions (device array `tasks` of `ntasks` entries
 // plus 8 bytes, ntasks = max_tasks(NP, S rows, slice)): one per slice of at most
 // `slice` S rows of every partition; unused entries are empty.

@@ -1061,7 +1061,6 @@ __global__ void __launch_bounds__(NT, 2048 / NT / 2) partition_join_kernel(
     uint32_t *oversize, int chk, void *stage_base, uint32_t scap) {
     using T = typename Tup<W>::U;
     using Vec = typename Tup<W>::Vec;
-    using Hh = typename HashT<W>::type;
     constexpr int PV = Tup<W>::kPerVec, U = 2, IT = U * PV;
     constexpr uint32_t G = SoaTab<W>::G;
     extern __shared__ __align__(16) unsigned char smem[];
@@ -1148,8 +1147,9 @@ __global__ void __launch_bounds__(NT, 2048 / NT / 2) partition_join_kernel(
                 }
 #pragma unroll
                 for (int e = 0; e < PV; ++e) {
-                    const Hh h = hashw<W>(k[e]);
-                    if (!pf.keep(h)) continue;
+                    // a padding row carries 0 or a pass's second sentinel: only
+                    // such keys are hashed to see whether the row is the partition's
+                    if ((k[e] == T(0) || k[e] == (T)tk.pk1 || k[e] == (T)tk.pk2) && !pf.keep(hashw<W>(k[e]))) continue;
                     bool ok = false;
                     if constexpr (AGG) {
                         ok = at.insert(k[e], chk ? mix_a(r[e]) : 0);
@@ -1345,7 +1345,7 @@ __global__ void __launch_bounds__(NT, 2048 / NT / 2) partition_join_kernel(
 // zero at launch; their order does not matter).
 __global__ void make_tasks_kernel(const void *Rp, const uint64_t *roff, const void *Sp, const uint64_t *soff,
                                   uint64_t NP, uint64_t slice, unsigned long long *next, uint32_t join, int b1,
-                                  int b2, uint64_t ek1, int tb, PartTask *tasks) {
+                                  int b2, uint64_t ek1, uint64_t pk1, uint64_t pk2, int tb, PartTask *tasks) {
     for (uint64_t p = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; p < NP; p += (uint64_t)gridDim.x * blockDim.x) {
         PartTask t;
         t.R = (const char *)Rp + roff[p] * tb;
@@ -1356,6 +1356,8 @@ __global__ void make_tasks_kernel(const void *Rp, const uint64_t *roff, const vo
         t.b2 = (uint16_t)b2;
         t.pad = 0;
         t.ek1 = ek1;
+        t.pk1 = pk1;
+        t.pk2 = pk2;
         const uint64_t s0 = soff[p], ns = soff[p + 1] - s0;
         const uint64_t extra = ns > slice ? (ns + slice - 1) / slice - 1 : 0;
         const uint64_t base = extra ? NP + atomicAdd(next, (unsigned long long)extra) : 0;
@@ -1385,8 +1387,8 @@ hj_status make_tasks(hj_ctx *c, const void *Rp, const uint64_t *roff, const void
     // counter just past the array starts at zero
     HJ_CUDA(c, cudaMemsetAsync(tasks, 0, ntasks * sizeof(PartTask) + 8, c->stream));
     HJ_LAUNCH(c, "make_tasks", make_tasks_kernel, grid ? grid : 1, 256, 0, Rp, roff, Sp, soff, NP, slice,
-              (unsigned long long *)(tasks + ntasks), join, b1, b2, empty_key2(width, b1, b2), (int)tuple_bytes(width),
-              tasks);
+              (unsigned long long *)(tasks + ntasks), join, b1, b2, empty_key2(width, b1, b2),
+              pass_pad_key(width, 0, b1), b2 ? pass_pad_key(width, b1, b2) : 0ull, (int)tuple_bytes(width), tasks);
     return HJ_OK;
 }
 

@@ -1252,6 +1252,12 @@ uint64_t partition_out_rows(hj_ctx *c, int width, uint64_t n_total, uint64_t nse
 }
 
 // Two sentinel keys for a pass: 0, and the first key whose digit differs from 0's.
+static void sentinel_keys(int width, int shift, int bits, uint64_t *k0, uint64_t *k1);
+uint64_t pass_pad_key(int width, int shift, int bits) {
+    uint64_t k0, k1;
+    sentinel_keys(width, shift, bits, &k0, &k1);
+    return k1;
+}
 static void sentinel_keys(int width, int shift, int bits, uint64_t *k0, uint64_t *k1) {
     auto dg = [&](uint64_t k) {
         uint64_t h = width == 4 ? (uint64_t)murmur2_u32((uint32_t)k) : murmur2_u64(k);
