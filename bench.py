@@ -43,6 +43,10 @@ WORKLOADS = {
         nr=1 << 23, ns=1 << 27, dom=1 << 24, algo=2,
         desc="PHJ radix-partitioned join, |R|=2^23, |S|=2^27 (uint32 key, uint32 rid); the 2^24 x 2^28 join at "
              "half size (profiling case); R keys a permutation of 1..2^23, S keys uniform over [1, 2^24]"),
+    "phj_16m_16m": dict(
+        nr=1 << 24, ns=1 << 24, dom=1 << 24, algo=2,
+        desc="the paper's default join size, |R| = |S| = 2^24 (uint32 key, uint32 rid); R keys a seeded "
+             "permutation of 1..2^24, S keys uniform over them (every S tuple matches once); pairs materialised"),
     "batch_4096": dict(
         kind="batch", njoins=4096, nr=0, ns=0, algo=2,
         desc="4096 independent joins, |R| log-uniform in [2^10, 2^22], |S| = 4|R| (uint32 key, uint32 rid); "

@@ -110,11 +110,16 @@ hj_status partition_rel(hj_ctx *c, const hj_rel *in, int b1, int b2, int pad, De
                         uint64_t *rows) {
     const uint64_t n = in->n, tb = tuple_bytes(in->width);
     DevBuf seg(c), A(c), off1(c);
-    HJ_TRY(device_pair(c, 0ull, n, seg));
     const uint64_t rows1 = partition_out_rows(c, in->width, n, 1, b1, pad);
     HJ_TRY(A.alloc(rows1 * tb + 64));
     HJ_TRY(off1.alloc(((1ull << b1) + 1) * 8));
-    HJ_TRY(partition_pass(c, in->width, in->tuples, n, seg.as<uint64_t>(), 1, 0, b1, A.p, off1.as<uint64_t>(), pad));
+    if (pad && b1 <= 11) {  // the first pass is one segment: the fused form
+        HJ_TRY(partition_pass1(c, in->width, in->tuples, n, b1, A.p, off1.as<uint64_t>()));
+    } else {
+        HJ_TRY(device_pair(c, 0ull, n, seg));
+        HJ_TRY(partition_pass(c, in->width, in->tuples, n, seg.as<uint64_t>(), 1, 0, b1, A.p, off1.as<uint64_t>(),
+                              pad));
+    }
     if (b2 == 0) {
         tuples.reset();
         offsets.reset();

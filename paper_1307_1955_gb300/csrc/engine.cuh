@@ -113,6 +113,9 @@ hj_status oversize_fallback(hj_ctx *c, int W, bool agg, bool chk, const PartTask
 hj_status partition_pass(hj_ctx *c, int width, const void *in, uint64_t n_total, const uint64_t *seg_off,
                          uint64_t nseg, int shift, int bits, void *out, uint64_t *part_off, int pad,
                          const void *const *seg_ptrs = nullptr);
+// One padded pass over a single segment of n rows at 2^bits <= 2^11 digits:
+// partition_pass's output with two launches (histogram, scatter).
+hj_status partition_pass1(hj_ctx *c, int width, const void *in, uint64_t n, int bits, void *out, uint64_t *part_off);
 uint64_t partition_out_rows(hj_ctx *c, int width, uint64_t n_total, uint64_t nseg, int bits, int pad);
 // Exclusive scan of n uint32 counts into n + 1 uint64 offsets (out[n] = total).
 hj_status scan_counts(hj_ctx *c, const uint32_t *in, uint64_t n, unsigned long long *out);

@@ -244,6 +244,133 @@ __global__ void extract_offsets_kernel(const uint64_t *seg_off, uint64_t nseg, c
     }
 }
 
+// ------------------------------------------------- run positions of a chunk
+// Where a padded scatter CTA writes.  General form: the pass's segments, chunks and
+// the exclusive scan Hs of the counts in (segment, digit, chunk) order.  Single-
+// segment form (H1 set; the first pass of a join): rows [0, n1) in nch1 chunks;
+// H1[g * P + d] is chunk g's padded count of digit d and base1[g * P + d] the row
+// of its run among digit d's runs (taken with one atomic add on the digit's total
+// T1[d] when the histogram was made, so runs of a digit follow in the order the
+// chunks finished counting: the order of tuples inside a partition is free).
+struct RunGeom {
+    const uint64_t *seg_off;
+    uint64_t nseg;
+    const unsigned long long *cb, *Hs;
+    const uint32_t *H1, *base1, *T1;
+    uint64_t n1, nch1;
+    uint64_t *part_off;  // single-segment form: partition offsets, written by chunk 0
+};
+
+// Chunk position and run bounds of scatter CTA g: run_lo[d] / run_hi[d] are the
+// rows of its digit-d run relative to the returned output base.  False when g has
+// no chunk (or, general form, the pass's output does not start on a sector).  All
+// NT threads of the CTA call it (the single-segment form scans the digit totals).
+template <uint32_t P, int NT>
+__device__ __forceinline__ bool chunk_runs(const RunGeom &rg, uint64_t chunk, uint64_t g, uint32_t SV, ChunkPos *cp,
+                                           uint64_t *obase, uint32_t *run_lo, uint32_t *run_hi,
+                                           unsigned long long *fault) {
+    if (!rg.H1) {
+        if (g >= rg.cb[rg.nseg]) return false;
+        // runs start on whole sectors only if the pass's first output row does (the
+        // padded counts are whole sectors): otherwise the sector stores would be
+        // misaligned, so refuse the input
+        if (rg.seg_off[0] % SV) {
+            if (threadIdx.x == 0) atomicOr(fault, (unsigned long long)kStatusBadInput);
+            return false;
+        }
+        *cp = chunk_pos(rg.seg_off, rg.nseg, rg.cb, chunk, g);
+        const uint64_t row = rg.cb[cp->s] * P;
+        *obase = (rg.seg_off[0] + rg.Hs[row]) / SV * SV;
+        for (uint32_t d = threadIdx.x; d < P; d += NT) {
+            // the run of (this chunk, d) is [Hs[i], Hs[i + 1]): the scan is in
+            // (digit, chunk) order, so the next entry starts the next run of the pass
+            const uint64_t i = row + (uint64_t)d * cp->nch + cp->cidx;
+            run_lo[d] = (uint32_t)(rg.seg_off[0] + rg.Hs[i] - *obase);
+            run_hi[d] = (uint32_t)(rg.seg_off[0] + rg.Hs[i + 1] - *obase);
+        }
+        return true;
+    }
+    if (g >= rg.nch1) return false;
+    cp->s = 0;
+    cp->cidx = g;
+    cp->nch = rg.nch1;
+    cp->lo = g * chunk;
+    cp->hi = min(cp->lo + chunk, rg.n1);
+    *obase = 0;
+    // digit d's partition starts at the sum of the padded totals of digits < d
+    __shared__ unsigned long long sc[33];
+    constexpr uint32_t PER = (P + NT - 1) / NT;  // digits per thread, consecutive
+    unsigned long long v[PER], sum = 0;
+#pragma unroll
+    for (uint32_t q = 0; q < PER; ++q) {
+        const uint32_t d = threadIdx.x * PER + q;
+        v[q] = d < P ? rg.T1[d] : 0u;
+        sum += v[q];
+    }
+    unsigned long long tot;
+    unsigned long long at = block_exclusive_scan<unsigned long long>(sum, sc, &tot);
+#pragma unroll
+    for (uint32_t q = 0; q < PER; ++q) {
+        const uint32_t d = threadIdx.x * PER + q;
+        if (d < P) {
+            const uint64_t i = g * P + d;
+            run_lo[d] = (uint32_t)(at + rg.base1[i]);
+            run_hi[d] = run_lo[d] + rg.H1[i];
+            if (g == 0) rg.part_off[d] = at;
+        }
+        at += v[q];
+    }
+    if (g == 0 && threadIdx.x == 0) rg.part_off[P] = tot;
+    return true;
+}
+
+// Histogram of the single-segment form: chunk g of rows [0, n) counts its digits
+// (pass one: the low `bits` bits of the hash), rounds each count up to whole
+// sectors, writes it to H1[g * P + d] and takes the rows of its run among the
+// digit's runs with one atomic add on the digit's total T1[d] (zero beforehand).
+template <int W>
+__global__ void __launch_bounds__(kHistThreads) hist1_kernel(const void *in, uint64_t n, uint64_t chunk, int bits,
+                                                             uint32_t *H1, uint32_t *base1, uint32_t *T1) {
+    using Vec = typename Tup<W>::Vec;
+    constexpr int PV = Tup<W>::kPerVec, SV = Sector<W>::kTuples;
+    extern __shared__ uint32_t hist[];
+    const uint32_t P = 1u << bits;
+    const uint64_t g = blockIdx.x, lo = g * chunk, hi = min(lo + chunk, n);
+    for (uint32_t d = threadIdx.x; d < P; d += blockDim.x) hist[d] = 0;
+    __syncthreads();
+    // chunks start on whole vectors; a 4-byte relation's odd last row is read alone
+    const Vec *vp = (const Vec *)in + lo / PV;
+    const uint32_t nv = (uint32_t)((hi - lo) / PV);
+    for (uint32_t v0 = 0; v0 < nv; v0 += blockDim.x * kHistUnroll) {
+        Vec x[kHistUnroll];
+#pragma unroll
+        for (int u = 0; u < kHistUnroll; ++u) {
+            const uint32_t v = v0 + (uint32_t)u * blockDim.x + threadIdx.x;
+            if (v < nv) x[u] = ld_stream(vp + v);
+        }
+#pragma unroll
+        for (int u = 0; u < kHistUnroll; ++u) {
+            const uint32_t v = v0 + (uint32_t)u * blockDim.x + threadIdx.x;
+            if (v < nv) {
+                atomicAdd(&hist[digit_of(key_hash<W>(x[u].x), 0, bits)], 1u);
+                if constexpr (W == 4) atomicAdd(&hist[digit_of(key_hash<W>(x[u].z), 0, bits)], 1u);
+            }
+        }
+    }
+    if constexpr (W == 4) {
+        if (threadIdx.x == 0 && (hi - lo) % 2) {
+            const uint32_t k = ((const uint32_t *)in)[2 * (hi - 1)];
+            atomicAdd(&hist[digit_of(key_hash<W>(k), 0, bits)], 1u);
+        }
+    }
+    __syncthreads();
+    for (uint32_t d = threadIdx.x; d < P; d += blockDim.x) {
+        const uint32_t c = (hist[d] + SV - 1) / SV * SV;
+        H1[g * P + d] = c;
+        base1[g * P + d] = c ? atomicAdd(&T1[d], c) : 0u;
+    }
+}
+
 // ----------------------------------------------------------------- scatter
 // One CTA per chunk.  Tile by tile (the next tile's vectors are loaded before the
 // current one is processed):
@@ -774,9 +901,8 @@ template <int W, int LOG2P> struct RegionShape {
 
 template <int W, int LOG2P>
 __global__ void __launch_bounds__(kRegionThreads, 1) scatter_region_kernel(
-    const void *in, uint64_t n_total, const uint64_t *seg_off, uint64_t nseg, const unsigned long long *cb,
-    uint64_t chunk, int shift, const unsigned long long *Hs, void *out, uint64_t sent_k0, uint64_t sent_k1,
-    const void *const *seg_ptrs, unsigned long long *fault) {
+    const void *in, uint64_t n_total, RunGeom rg, uint64_t chunk, int shift, void *out, uint64_t sent_k0,
+    uint64_t sent_k1, const void *const *seg_ptrs, unsigned long long *fault) {
     using U = typename Tup<W>::U;
     using Vec = typename Tup<W>::Vec;
     using RS = RegionShape<W, LOG2P>;
@@ -791,33 +917,17 @@ __global__ void __launch_bounds__(kRegionThreads, 1) scatter_region_kernel(
     uint32_t *tail = head + P;                       // P: rows at and above belong to overflow tuples
 
     const uint64_t g = blockIdx.x;
-    if (g >= cb[nseg]) return;
-    // runs start on whole sectors only if the pass's first output row does (the
-    // padded counts are whole sectors): otherwise the sector stores below would be
-    // misaligned, so refuse the input
-    if (seg_off[0] % SV) {
-        if (threadIdx.x == 0) atomicOr(fault, (unsigned long long)kStatusBadInput);
-        return;
-    }
-    const ChunkPos cp = chunk_pos(seg_off, nseg, cb, chunk, g);
-    const uint64_t row = cb[cp.s] * P;
-    const uint64_t seg_start = seg_off[0] + Hs[row];
-    const uint64_t obase = seg_start / SV * SV;
+    ChunkPos cp;
+    uint64_t obase;
+    if (!chunk_runs<P, NT>(rg, chunk, g, SV, &cp, &obase, head, tail, fault)) return;
     Slot *outp = (Slot *)out + obase;
     // this chunk's tuples: rows [lo, hi) of src; lo is a whole number of vectors
     // (chunks, segments and arrays start on 16 bytes)
     const void *src = seg_ptrs ? seg_ptrs[cp.s] : in;
-    const uint64_t ioff = seg_ptrs ? seg_off[cp.s] : 0;
+    const uint64_t ioff = seg_ptrs ? rg.seg_off[cp.s] : 0;
     const Vec *vsrc = (const Vec *)src + (cp.lo - ioff) / PV;
     const uint32_t nrows = (uint32_t)(cp.hi - cp.lo);
-    for (uint32_t d = threadIdx.x; d < P; d += NT) {
-        // the run of (this chunk, d) is [Hs[i], Hs[i + 1]): the scan is in (digit,
-        // chunk) order, so the next entry starts the next run of the pass
-        const uint64_t i = row + (uint64_t)d * cp.nch + cp.cidx;
-        head[d] = (uint32_t)(seg_off[0] + Hs[i] - obase);
-        tail[d] = (uint32_t)(seg_off[0] + Hs[i + 1] - obase);
-        fill[d] = 0;
-    }
+    for (uint32_t d = threadIdx.x; d < P; d += NT) fill[d] = 0;
     // vector j of the tile [t0, lim) for this thread; a last vector holding one
     // tuple of a 4-byte relation is read with an 8-byte load (nothing past the
     // array end)
@@ -904,15 +1014,14 @@ __global__ void __launch_bounds__(kRegionThreads, 1) scatter_region_kernel(
 }
 
 template <int W, int LOG2P>
-static hj_status launch_region(hj_ctx *c, unsigned grid, const void *in, uint64_t n_total, const uint64_t *seg_off,
-                               uint64_t nseg, const unsigned long long *cb, uint64_t chunk, int shift,
-                               const unsigned long long *Hs, void *out, uint64_t k0, uint64_t k1,
+static hj_status launch_region(hj_ctx *c, unsigned grid, const void *in, uint64_t n_total, const RunGeom &rg,
+                               uint64_t chunk, int shift, void *out, uint64_t k0, uint64_t k1,
                                const void *const *seg_ptrs) {
     auto kern = scatter_region_kernel<W, LOG2P>;
     const size_t smem = RegionShape<W, LOG2P>::kSmem;
     HJ_TRY(allow_max_smem(c, (const void *)kern));
-    HJ_LAUNCH(c, "partition_scatter", kern, grid, kRegionThreads, smem, in, n_total, seg_off, nseg, cb, chunk, shift,
-              Hs, out, k0, k1, seg_ptrs, &c->d_ctr->fault);
+    HJ_LAUNCH(c, "partition_scatter", kern, grid, kRegionThreads, smem, in, n_total, rg, chunk, shift, out, k0, k1,
+              seg_ptrs, &c->d_ctr->fault);
     return HJ_OK;
 }
 
@@ -989,9 +1098,8 @@ __device__ __forceinline__ void red_release_add_cta(uint32_t *p, uint32_t v) {
 
 template <int W, int LOG2P>
 __global__ void __launch_bounds__(kRingThreads, 1) scatter_ring_kernel(
-    const void *in, uint64_t n_total, const uint64_t *seg_off, uint64_t nseg, const unsigned long long *cb,
-    uint64_t chunk, int shift, const unsigned long long *Hs, void *out, uint64_t sent_k0, uint64_t sent_k1,
-    const void *const *seg_ptrs, unsigned long long *fault, uint64_t max_passes) {
+    const void *in, uint64_t n_total, RunGeom rg, uint64_t chunk, int shift, void *out, uint64_t sent_k0,
+    uint64_t sent_k1, const void *const *seg_ptrs, unsigned long long *fault, uint64_t max_passes) {
     using U = typename Tup<W>::U;
     using Vec = typename Tup<W>::Vec;
     using RS = RingShape<W, LOG2P>;
@@ -1007,17 +1115,12 @@ __global__ void __launch_bounds__(kRingThreads, 1) scatter_ring_kernel(
     uint32_t *s_done = tail + P;                            // insert warps finished
 
     const uint64_t g = blockIdx.x;
-    if (g >= cb[nseg]) return;
-    if (seg_off[0] % SV) {  // runs would not start on whole sectors (see the region scatter)
-        if (threadIdx.x == 0) atomicOr(fault, (unsigned long long)kStatusBadInput);
-        return;
-    }
-    const ChunkPos cp = chunk_pos(seg_off, nseg, cb, chunk, g);
-    const uint64_t row = cb[cp.s] * P;
-    const uint64_t obase = (seg_off[0] + Hs[row]) / SV * SV;
+    ChunkPos cp;
+    uint64_t obase;
+    if (!chunk_runs<P, kRingThreads>(rg, chunk, g, SV, &cp, &obase, nxt, tail, fault)) return;
     Slot *outp = (Slot *)out + obase;
     const void *src = seg_ptrs ? seg_ptrs[cp.s] : in;
-    const uint64_t ioff = seg_ptrs ? seg_off[cp.s] : 0;
+    const uint64_t ioff = seg_ptrs ? rg.seg_off[cp.s] : 0;
     const Vec *vsrc = (const Vec *)src + (cp.lo - ioff) / PV;  // chunks start on whole vectors
     const uint32_t nrows = (uint32_t)(cp.hi - cp.lo);
     const uint32_t dk0 = (uint32_t)(key_hash<W>((U)sent_k0) >> shift) & (P - 1u);
@@ -1026,12 +1129,7 @@ __global__ void __launch_bounds__(kRingThreads, 1) scatter_ring_kernel(
         if constexpr (W == 4) return (unsigned long long)empty_key(d);
         else return make_ulonglong2(empty_key(d), 0ull);
     };
-    for (uint32_t d = threadIdx.x; d < P; d += kRingThreads) {
-        const uint64_t i = row + (uint64_t)d * cp.nch + cp.cidx;  // the run of (this chunk, d)
-        nxt[d] = (uint32_t)(seg_off[0] + Hs[i] - obase);
-        tail[d] = (uint32_t)(seg_off[0] + Hs[i + 1] - obase);
-        word[d] = 0;
-    }
+    for (uint32_t d = threadIdx.x; d < P; d += kRingThreads) word[d] = 0;
     for (uint32_t i = threadIdx.x; i < K * P; i += kRingThreads) ring[i] = empty_slot(i & (P - 1u));
     if (threadIdx.x == 0) *s_done = 0;
     __syncthreads();
@@ -1164,16 +1262,15 @@ __global__ void __launch_bounds__(kRingThreads, 1) scatter_ring_kernel(
 }
 
 template <int W, int LOG2P>
-static hj_status launch_ring(hj_ctx *c, unsigned grid, const void *in, uint64_t n_total, const uint64_t *seg_off,
-                             uint64_t nseg, const unsigned long long *cb, uint64_t chunk, int shift,
-                             const unsigned long long *Hs, void *out, uint64_t k0, uint64_t k1,
+static hj_status launch_ring(hj_ctx *c, unsigned grid, const void *in, uint64_t n_total, const RunGeom &rg,
+                             uint64_t chunk, int shift, void *out, uint64_t k0, uint64_t k1,
                              const void *const *seg_ptrs) {
     auto kern = scatter_ring_kernel<W, LOG2P>;
     HJ_TRY(allow_max_smem(c, (const void *)kern));
     const uint64_t passes = c->wait_limit ? std::min<uint64_t>(c->wait_limit, kRingMaxPasses) : kRingMaxPasses;
     constexpr size_t smem = RingShape<W, LOG2P>::kSmem;
-    HJ_LAUNCH(c, "partition_scatter", kern, grid, kRingThreads, smem, in, n_total, seg_off,
-              nseg, cb, chunk, shift, Hs, out, k0, k1, seg_ptrs, &c->d_ctr->fault, passes);
+    HJ_LAUNCH(c, "partition_scatter", kern, grid, kRingThreads, smem, in, n_total, rg, chunk, shift, out, k0, k1,
+              seg_ptrs, &c->d_ctr->fault, passes);
     return HJ_OK;
 }
 
@@ -1191,15 +1288,14 @@ static bool use_ring(const hj_ctx *c, int width, int bits) {
 
 template <int W>
 static hj_status launch_region_bits(hj_ctx *c, int bits, unsigned grid, const void *in, uint64_t n_total,
-                                    const uint64_t *seg_off, uint64_t nseg, const unsigned long long *cb,
-                                    uint64_t chunk, int shift, const unsigned long long *Hs, void *out, uint64_t k0,
+                                    const RunGeom &rg, uint64_t chunk, int shift, void *out, uint64_t k0,
                                     uint64_t k1, const void *const *seg_ptrs) {
 #define HJ_RG(B)                                                                                                 \
     case B:                                                                                                      \
-        return launch_region<W, B>(c, grid, in, n_total, seg_off, nseg, cb, chunk, shift, Hs, out, k0, k1, seg_ptrs)
+        return launch_region<W, B>(c, grid, in, n_total, rg, chunk, shift, out, k0, k1, seg_ptrs)
 #define HJ_RI(B)                                                                                                 \
     case B:                                                                                                      \
-        return launch_ring<W, B>(c, grid, in, n_total, seg_off, nseg, cb, chunk, shift, Hs, out, k0, k1, seg_ptrs)
+        return launch_ring<W, B>(c, grid, in, n_total, rg, chunk, shift, out, k0, k1, seg_ptrs)
     if (use_ring(c, W, bits)) {
         switch (bits) {
             HJ_RI(9); HJ_RI(10); HJ_RI(11);
@@ -1319,12 +1415,13 @@ hj_status partition_pass(hj_ctx *c, int width, const void *in, uint64_t n_total,
     } while (0)
     const size_t tma_smem = width == 4 ? scatter_tma_smem_bytes<4>((uint32_t)P) : scatter_tma_smem_bytes<8>((uint32_t)P);
     if (cfg.tma && pad) {
+        const RunGeom rg{seg_off, nseg, cb, Hs, nullptr, nullptr, nullptr, 0, 0, nullptr};
         if (width == 4)
-            HJ_TRY(launch_region_bits<4>(c, bits, (unsigned)max_chunks, in, n_total, seg_off, nseg, cb, chunk, shift,
-                                         Hs, out, k0, k1, seg_ptrs));
+            HJ_TRY(launch_region_bits<4>(c, bits, (unsigned)max_chunks, in, n_total, rg, chunk, shift, out, k0, k1,
+                                         seg_ptrs));
         else
-            HJ_TRY(launch_region_bits<8>(c, bits, (unsigned)max_chunks, in, n_total, seg_off, nseg, cb, chunk, shift,
-                                         Hs, out, k0, k1, seg_ptrs));
+            HJ_TRY(launch_region_bits<8>(c, bits, (unsigned)max_chunks, in, n_total, rg, chunk, shift, out, k0, k1,
+                                         seg_ptrs));
     } else if (cfg.tma) {
         if (width == 4) {
             HJ_TRY(allow_max_smem(c, (const void *)scatter_tma_kernel<4>));
@@ -1343,6 +1440,43 @@ hj_status partition_pass(hj_ctx *c, int width, const void *in, uint64_t n_total,
         if (cfg.nt == 512) HJ_SC(8, 512, 4); else HJ_SC(8, 1024, 2);
     }
 #undef HJ_SC
+    return HJ_OK;
+}
+
+// One padded pass over a single segment of n rows at 2^bits <= 2^11 digits (the
+// first pass of a join): hist1_kernel and the scatter, whose CTAs place their runs
+// from the digit totals themselves -- two launches and a memset in place of the
+// general pass's chunk, scan and offset launches.  Same output contract as
+// partition_pass with pad: 2^bits partitions, each run padded to whole sectors,
+// part_off[2^bits + 1].
+hj_status partition_pass1(hj_ctx *c, int width, const void *in, uint64_t n, int bits, void *out, uint64_t *part_off) {
+    if (bits < 1 || bits > 11) return set_err(c, HJ_E_INVALID, "single-segment pass bits %d outside [1, 11]", bits);
+    const uint64_t P = 1ull << bits;
+    if (n == 0) {
+        HJ_CUDA(c, cudaMemsetAsync(part_off, 0, (P + 1) * 8, c->stream));
+        return HJ_OK;
+    }
+    const uint64_t chunk = pass_chunk(c, width, bits, n);
+    const uint64_t nch = (n + chunk - 1) / chunk;
+    DevBuf H1(c), base1(c), T1(c);
+    HJ_TRY(H1.alloc(nch * P * 4));
+    HJ_TRY(base1.alloc(nch * P * 4));
+    HJ_TRY(T1.alloc(P * 4));
+    HJ_CUDA(c, cudaMemsetAsync(T1.p, 0, P * 4, c->stream));
+    if (width == 4)
+        HJ_LAUNCH(c, "partition_hist", hist1_kernel<4>, (unsigned)nch, kHistThreads, P * 4, in, n, chunk, bits,
+                  H1.as<uint32_t>(), base1.as<uint32_t>(), T1.as<uint32_t>());
+    else
+        HJ_LAUNCH(c, "partition_hist", hist1_kernel<8>, (unsigned)nch, kHistThreads, P * 4, in, n, chunk, bits,
+                  H1.as<uint32_t>(), base1.as<uint32_t>(), T1.as<uint32_t>());
+    uint64_t k0, k1;
+    sentinel_keys(width, 0, bits, &k0, &k1);
+    const RunGeom rg{nullptr, 1, nullptr, nullptr, H1.as<uint32_t>(), base1.as<uint32_t>(), T1.as<uint32_t>(), n,
+                     nch, part_off};
+    if (width == 4)
+        HJ_TRY(launch_region_bits<4>(c, bits, (unsigned)nch, in, n, rg, chunk, 0, out, k0, k1, nullptr));
+    else
+        HJ_TRY(launch_region_bits<8>(c, bits, (unsigned)nch, in, n, rg, chunk, 0, out, k0, k1, nullptr));
     return HJ_OK;
 }
 
