@@ -277,12 +277,14 @@ hj_status join_phj(hj_ctx *c, const hj_rel *R, const hj_rel *S, const hj_opts &o
     uint64_t r_rows = 0, s_rows = 0;
     HJ_TRY(partition_rel(c, R, b1, b2, 1, Rp, roff, &r_rows));
     HJ_TRY(partition_rel(c, S, b1, b2, 1, Sp, soff, &s_rows));
-    const uint64_t slice = task_slice_rows(R->width, S->n, NP), ntasks = max_tasks(NP, s_rows, slice);
+    const uint64_t tail = tail_split_from(c, R->width, is_agg(o.mode), NP, NP ? (R->n + NP - 1) / NP : 0);
+    const uint64_t slice = task_slice_rows(R->width, S->n, NP),
+                   ntasks = max_tasks(NP, s_rows, slice) + (NP - tail);
     HJ_TRY(oversize.alloc(ntasks * 4));
     HJ_TRY(tasks.alloc(ntasks * sizeof(PartTask) + 8));
     HJ_TRY(slot.alloc(sizeof(JoinSlot)));
     HJ_TRY(make_tasks(c, Rp.p, roff.as<uint64_t>(), Sp.p, soff.as<uint64_t>(), NP, 0, b1, b2, R->width, slice, ntasks,
-                      tasks.as<PartTask>()));
+                      tasks.as<PartTask>(), tail));
     const uint64_t warps = partition_join_warps(c);
     uint64_t cap = mat ? first_capacity(o, S->n, warps) : 0;
     for (int attempt = 0; attempt < 2; ++attempt) {

@@ -74,9 +74,15 @@ uint64_t pass_pad_key(int width, int shift, int bits);
 // `slice` S rows of every partition; unused entries are empty.
 uint64_t task_slice_rows(int width, uint64_t n_s, uint64_t NP);
 uint64_t max_tasks(uint64_t NP, uint64_t s_rows, uint64_t slice);
+// Partitions p >= tail_from have their S rows probed in two halves (at most: the
+// slice bound still holds); each such partition may add one task, so ntasks must
+// then hold NP - tail_from more.
 hj_status make_tasks(hj_ctx *c, const void *Rp, const uint64_t *roff, const void *Sp, const uint64_t *soff,
                      uint64_t NP, uint32_t join, int b1, int b2, int width, uint64_t slice, uint64_t ntasks,
-                     PartTask *tasks);
+                     PartTask *tasks, uint64_t tail_from = ~0ull);
+// First partition of the persistent join's last, partly filled round of NP equal
+// tasks (NP when the tasks fill whole rounds).
+uint64_t tail_split_from(hj_ctx *c, int width, int agg, uint64_t NP, uint64_t expect_r);
 
 
 // Per-partition join (Alg. 2's "apply SHJ on each partition pair") with the

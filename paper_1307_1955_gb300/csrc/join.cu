@@ -1344,8 +1344,10 @@ __global__ void __launch_bounds__(NT, 2048 / NT / 2) partition_join_kernel(
 // p; further slices take indices from NP on, handed out by a counter (*next,
 // zero at launch; their order does not matter).
 __global__ void make_tasks_kernel(const void *Rp, const uint64_t *roff, const void *Sp, const uint64_t *soff,
-                                  uint64_t NP, uint64_t slice, unsigned long long *next, uint32_t join, int b1,
-                                  int b2, uint64_t ek1, uint64_t pk1, uint64_t pk2, int tb, PartTask *tasks) {
+                                  uint64_t NP, uint64_t slice, uint64_t tail_from, unsigned long long *next,
+                                  uint32_t join, int b1, int b2, uint64_t ek1, uint64_t pk1, uint64_t pk2, int tb,
+                                  PartTask *tasks) {
+    const uint64_t sv = 32 / (uint64_t)tb;
     for (uint64_t p = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; p < NP; p += (uint64_t)gridDim.x * blockDim.x) {
         PartTask t;
         t.R = (const char *)Rp + roff[p] * tb;
@@ -1359,11 +1361,18 @@ __global__ void make_tasks_kernel(const void *Rp, const uint64_t *roff, const vo
         t.pk1 = pk1;
         t.pk2 = pk2;
         const uint64_t s0 = soff[p], ns = soff[p + 1] - s0;
-        const uint64_t extra = ns > slice ? (ns + slice - 1) / slice - 1 : 0;
+        // the partitions of the persistent join's last, partly filled round are
+        // probed in two halves, so that the round's idle CTAs take the other halves
+        uint64_t sl = slice;
+        if (p >= tail_from && ns >= 2 * sv) {
+            const uint64_t h = ((ns + 1) / 2 + sv - 1) / sv * sv;
+            if (h < sl) sl = h;
+        }
+        const uint64_t extra = ns > sl ? (ns + sl - 1) / sl - 1 : 0;
         const uint64_t base = extra ? NP + atomicAdd(next, (unsigned long long)extra) : 0;
-        for (uint64_t i = 0, at = 0; i == 0 || at < ns; ++i, at += slice) {
+        for (uint64_t i = 0, at = 0; i == 0 || at < ns; ++i, at += sl) {
             t.S = (const char *)Sp + (s0 + at) * tb;
-            t.ns = (uint32_t)(ns - at < slice ? ns - at : slice);
+            t.ns = (uint32_t)(ns - at < sl ? ns - at : sl);
             tasks[i == 0 ? p : base + i - 1] = t;
         }
     }
@@ -1379,14 +1388,19 @@ uint64_t task_slice_rows(int width, uint64_t n_s, uint64_t NP) {
 
 uint64_t max_tasks(uint64_t NP, uint64_t s_rows, uint64_t slice) { return NP + s_rows / slice + 1; }
 
+uint64_t tail_split_from(hj_ctx *c, int width, int agg, uint64_t NP, uint64_t expect_r) {
+    const uint64_t grid = partition_join_ctas(c, width, agg, expect_r), r = grid ? NP % grid : 0;
+    return NP < grid || r == 0 ? NP : NP - r;
+}
+
 hj_status make_tasks(hj_ctx *c, const void *Rp, const uint64_t *roff, const void *Sp, const uint64_t *soff,
                      uint64_t NP, uint32_t join, int b1, int b2, int width, uint64_t slice, uint64_t ntasks,
-                     PartTask *tasks) {
+                     PartTask *tasks, uint64_t tail_from) {
     const unsigned grid = (unsigned)((NP + 255) / 256);
     // unused task slots stay empty (no rows; the join skips them), and the slice
     // counter just past the array starts at zero
     HJ_CUDA(c, cudaMemsetAsync(tasks, 0, ntasks * sizeof(PartTask) + 8, c->stream));
-    HJ_LAUNCH(c, "make_tasks", make_tasks_kernel, grid ? grid : 1, 256, 0, Rp, roff, Sp, soff, NP, slice,
+    HJ_LAUNCH(c, "make_tasks", make_tasks_kernel, grid ? grid : 1, 256, 0, Rp, roff, Sp, soff, NP, slice, tail_from,
               (unsigned long long *)(tasks + ntasks), join, b1, b2, empty_key2(width, b1, b2),
               pass_pad_key(width, 0, b1), b2 ? pass_pad_key(width, b1, b2) : 0ull, (int)tuple_bytes(width), tasks);
     return HJ_OK;
