@@ -22,31 +22,173 @@ struct TableHold {
     ~TableHold() { table_destroy(c, t); }
 };
 
-// Partitions whose table did not fit in shared memory: SHJ with a global table,
-// task by task (host loop over the listed tasks).  Such a partition may hold a
-// heavily repeated key, so pairs come from a key-list table (one entry per
-// distinct key, its rids in one list); count modes use the aggregate table.
+// Partitions whose table did not fit in shared memory (a heavily repeated key, or
+// more build rows than the table holds): per join, the R rows of every such
+// partition and the S rows of every such task are gathered into two compact
+// arrays (rows of another partition -- the padding -- dropped by their hash), and
+// one global table over the gathered R serves all of them: partitions are
+// disjoint in key, so one table per join is the union of the per-partition
+// tables.  Pairs come from a key-list table (one entry per distinct key, its rids
+// in one list; Sec. 3.1's layout), count modes use the aggregate table.  A fixed
+// number of launches per join, however many partitions fall back; a join with a
+// single such partition uses its rows in place, with the partition filter.
+namespace fallback {
+
+struct GatherRange {
+    const void *ptr;
+    uint64_t n;
+    uint32_t p;
+    uint16_t b1, b2;
+};
+
+__global__ void pick_tasks_kernel(const PartTask *tasks, const uint32_t *list, uint64_t n, PartTask *out) {
+    for (uint64_t i = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; i < n; i += (uint64_t)gridDim.x * blockDim.x)
+        out[i] = tasks[list[i]];
+}
+
+// Rows of the listed ranges whose key falls in the range's partition, appended to
+// `out` (cap rows) at positions taken by one atomic add per warp and step.
+template <int W>
+__global__ void __launch_bounds__(256) gather_rows_kernel(const GatherRange *rg, uint64_t nrg, void *out, uint64_t cap,
+                                                          unsigned long long *count, unsigned long long *fault) {
+    using U = typename Tup<W>::U;
+    const unsigned lane = threadIdx.x & 31, lt = (1u << lane) - 1u;
+    U *o = (U *)out;
+    for (uint64_t r = blockIdx.x; r < nrg; r += gridDim.x) {
+        const GatherRange g = rg[r];
+        const PartFilter pf{g.p, (int)g.b1, (int)g.b2, 1};
+        const U *t = (const U *)g.ptr;
+        for (uint64_t i0 = 0; i0 < g.n; i0 += blockDim.x) {
+            const uint64_t i = i0 + threadIdx.x;
+            U k = 0, rid = 0;
+            bool keep = false;
+            if (i < g.n) {
+                k = t[2 * i];
+                rid = t[2 * i + 1];
+                keep = pf.keep(key_hash<W>(k));
+            }
+            const unsigned m = __ballot_sync(0xffffffffu, keep);
+            unsigned long long base = 0;
+            if (lane == 0 && m) base = atomicAdd(count, (unsigned long long)__popc(m));
+            base = __shfl_sync(0xffffffffu, base, 0);
+            if (keep) {
+                const unsigned long long at = base + __popc(m & lt);
+                if (at < cap) {
+                    o[2 * at] = k;
+                    o[2 * at + 1] = rid;
+                } else {  // cannot happen (cap is the ranges' total): reported, never written
+                    atomicOr(fault, (unsigned long long)kStatusBadInput);
+                }
+            }
+        }
+    }
+}
+
+// Gather the rows of `ranges` into a new array; *rows gets the number kept.
+hj_status gather_rows(hj_ctx *c, int W, const std::vector<GatherRange> &ranges, DevBuf &out, uint64_t *rows) {
+    uint64_t cap = 0;
+    for (const GatherRange &g : ranges) cap += g.n;
+    *rows = 0;
+    if (!cap) return HJ_OK;
+    // pieces of at most 2^16 rows, so that a large partition spreads over the SMs
+    constexpr uint64_t kPiece = 1ull << 16;
+    std::vector<GatherRange> pieces;
+    for (const GatherRange &g : ranges)
+        for (uint64_t at = 0; at < g.n; at += kPiece)
+            pieces.push_back(GatherRange{(const char *)g.ptr + at * tuple_bytes(W), std::min(kPiece, g.n - at), g.p,
+                                         g.b1, g.b2});
+    const uint64_t tb = tuple_bytes(W);
+    DevBuf rg(c), cnt(c);
+    HJ_TRY(out.alloc(cap * tb + 64));
+    HJ_TRY(rg.alloc(pieces.size() * sizeof(GatherRange)));
+    HJ_TRY(cnt.alloc(8));
+    HJ_CUDA(c, cudaMemcpyAsync(rg.p, pieces.data(), pieces.size() * sizeof(GatherRange), cudaMemcpyHostToDevice,
+                               c->stream));
+    HJ_CUDA(c, cudaMemsetAsync(cnt.p, 0, 8, c->stream));
+    const unsigned grid = (unsigned)std::min<uint64_t>(pieces.size(), (uint64_t)num_sms(c) * 8);
+    if (W == 4)
+        HJ_LAUNCH(c, "fallback_gather", gather_rows_kernel<4>, grid, 256, 0, rg.as<GatherRange>(),
+                  (uint64_t)pieces.size(), out.p, cap, cnt.as<unsigned long long>(), &c->d_ctr->fault);
+    else
+        HJ_LAUNCH(c, "fallback_gather", gather_rows_kernel<8>, grid, 256, 0, rg.as<GatherRange>(),
+                  (uint64_t)pieces.size(), out.p, cap, cnt.as<unsigned long long>(), &c->d_ctr->fault);
+    HJ_CUDA(c, cudaMemcpyAsync(rows, cnt.p, 8, cudaMemcpyDeviceToHost, c->stream));
+    HJ_CUDA(c, cudaStreamSynchronize(c->stream));
+    return HJ_OK;
+}
+
+}  // namespace fallback
+
 hj_status oversize_fallback(hj_ctx *c, int W, bool agg, bool chk, const PartTask *tasks, const uint32_t *list_dev,
                             uint64_t nov, const std::vector<JoinSlot> &slots_host) {
-    std::vector<uint32_t> list(nov);
-    HJ_CUDA(c, cudaMemcpyAsync(list.data(), list_dev, nov * 4, cudaMemcpyDeviceToHost, c->stream));
-    HJ_CUDA(c, cudaStreamSynchronize(c->stream));
-    for (uint32_t ti : list) {
-        PartTask tk;
-        HJ_CUDA(c, cudaMemcpyAsync(&tk, tasks + ti, sizeof tk, cudaMemcpyDeviceToHost, c->stream));
+    std::vector<PartTask> tk(nov);
+    {
+        DevBuf picked(c);
+        HJ_TRY(picked.alloc(nov * sizeof(PartTask)));
+        const unsigned grid = (unsigned)std::min<uint64_t>((nov + 255) / 256, (uint64_t)num_sms(c) * 8);
+        HJ_LAUNCH(c, "fallback_tasks", fallback::pick_tasks_kernel, grid ? grid : 1, 256, 0, tasks, list_dev, nov,
+                  picked.as<PartTask>());
+        HJ_CUDA(c, cudaMemcpyAsync(tk.data(), picked.p, nov * sizeof(PartTask), cudaMemcpyDeviceToHost, c->stream));
         HJ_CUDA(c, cudaStreamSynchronize(c->stream));
-        const PartFilter pf{tk.p, (int)tk.b1, (int)tk.b2, 1};
-        const JoinSlot &js = slots_host[tk.join];
+    }
+    // the tasks of each join; the R side of a partition once (its S slices share it)
+    std::sort(tk.begin(), tk.end(), [](const PartTask &a, const PartTask &b) {
+        return a.join != b.join ? a.join < b.join : a.R < b.R;
+    });
+    for (size_t i = 0; i < tk.size();) {
+        const uint32_t join = tk[i].join;
+        std::vector<fallback::GatherRange> rr, ss;
+        size_t j = i;
+        for (; j < tk.size() && tk[j].join == join; ++j) {
+            const PartTask &t = tk[j];
+            if (j == i || t.R != tk[j - 1].R) rr.push_back(fallback::GatherRange{t.R, t.nr, t.p, t.b1, t.b2});
+            ss.push_back(fallback::GatherRange{t.S, t.ns, t.p, t.b1, t.b2});
+        }
+        i = j;
+        if (join >= slots_host.size()) return set_err(c, HJ_E_CUDA, "fallback task of unknown join %u", join);
+        const JoinSlot &js = slots_host[join];
+        DevBuf Rg(c), Sg(c);
+        const void *Rt, *St;
+        uint64_t nr = 0, ns = 0;
+        PartFilter pf{0, 0, 0, 0};
+        if (rr.size() == 1) {
+            // one partition: its rows in place, padding dropped by the partition
+            // filter; its S slices too when they are one gapless run (a slice whose
+            // own build fitted has been probed already and must not be again)
+            const uint64_t tb = tuple_bytes(W);
+            std::sort(ss.begin(), ss.end(), [](const fallback::GatherRange &a, const fallback::GatherRange &b) {
+                return (const char *)a.ptr < (const char *)b.ptr;
+            });
+            bool run = true;
+            for (size_t q = 1; q < ss.size(); ++q)
+                run &= (const char *)ss[q].ptr == (const char *)ss[q - 1].ptr + ss[q - 1].n * tb;
+            Rt = rr[0].ptr;
+            nr = rr[0].n;
+            pf = PartFilter{rr[0].p, (int)rr[0].b1, (int)rr[0].b2, 1};
+            if (run) {
+                St = ss[0].ptr;
+                for (const auto &g : ss) ns += g.n;
+            } else {
+                HJ_TRY(fallback::gather_rows(c, W, ss, Sg, &ns));
+                St = Sg.p;
+            }
+        } else {
+            HJ_TRY(fallback::gather_rows(c, W, rr, Rg, &nr));
+            HJ_TRY(fallback::gather_rows(c, W, ss, Sg, &ns));
+            Rt = Rg.p;
+            St = Sg.p;
+        }
+        if (!nr || !ns) continue;
         TableHold tg{c};
         if (!agg) {
-            HJ_TRY(keylist_build(c, W, tk.R, tk.nr, pf, &tg.t));
-            HJ_TRY(keylist_probe(c, tg.t, tk.S, tk.ns, pf, js.pairs, js.pcap, js.ctr, chk));
+            HJ_TRY(keylist_build(c, W, Rt, nr, pf, &tg.t));
+            HJ_TRY(keylist_probe(c, tg.t, St, ns, pf, js.pairs, js.pcap, js.ctr, chk));
             continue;
         }
-        HJ_TRY(table_create(c, W, agg, tk.nr, &tg.t));
-        HJ_TRY(table_build(c, tg.t, tk.R, 0, tk.nr, tk.nr, pf));
+        HJ_TRY(table_create(c, W, agg, nr, &tg.t));
+        HJ_TRY(table_build(c, tg.t, Rt, 0, nr, nr, pf));
         const RecArea none{nullptr, nullptr, 0};
-        HJ_TRY(table_probe(c, tg.t, tk.S, 0, tk.ns, tk.ns, js.pairs, js.pcap, chk, none, pf, js.ctr, 1));
+        HJ_TRY(table_probe(c, tg.t, St, 0, ns, ns, js.pairs, js.pcap, chk, none, pf, js.ctr, 1));
     }
     return HJ_OK;
 }

@@ -15,7 +15,10 @@
 // a single pair at once; a list of up to kCoopPairs by the whole warp, reading
 // the list with coalesced loads; a longer list (a heavy hitter) is recorded and
 // expanded afterwards by a grid-wide kernel in segments of kSegPairs pairs, so
-// that the millions of pairs of one probe tuple are written by every SM.
+// that the millions of pairs of one probe tuple are written by every SM.  The
+// rows of a warp's step (the lists of its 32 probe tuples) are claimed with one
+// atomic add on the join's count: one global atomic per 32 probes, not per 32
+// pairs.
 // R tuples whose key is all ones (the aggregate table's empty marker) are
 // counted on the table's side and keep their rids at the end of the array.
 #include <algorithm>
@@ -280,13 +283,18 @@ __global__ void __launch_bounds__(256) kl_probe(const void *S, uint64_t ns, cons
                                                 void *pairs, uint64_t pcap, hj_counters *ctr, int chk, PartFilter pf,
                                                 Big *big, unsigned long long *nbig) {
     using U = typename Tup<W>::U;
+    using P = typename PairVec<W>::T;
     constexpr int PV = Tup<W>::kPerVec;
+    constexpr unsigned kUnroll = 4;  // pairs per lane and step of a list walk (loads in flight)
     const unsigned lane = threadIdx.x & 31;
     const uint64_t warp = (blockIdx.x * (uint64_t)blockDim.x + threadIdx.x) >> 5;
     const uint64_t nwarps = ((uint64_t)gridDim.x * blockDim.x) >> 5;
     const uint64_t nv = (ns + PV - 1) / PV;
-    OutState st;
-    const OutCtx oc{pairs, pcap, ctr, 0u, true};
+    P *out = (P *)pairs;
+    auto mk = [](U a, U b) -> P {
+        if constexpr (W == 4) return make_uint2(a, b);
+        else return make_ulonglong2(a, b);
+    };
     unsigned long long c0 = 0, c1 = 0;
     const uint64_t allones = side->agg_cnt;
     for (uint64_t v0 = warp * 32; v0 < nv; v0 += nwarps * 32) {
@@ -312,36 +320,64 @@ __global__ void __launch_bounds__(256) kl_probe(const void *S, uint64_t ns, cons
                 }
             }
             const U s = r[e];
-            // one match
-            const bool one = cnt == 1;
-            const U a = one ? rids[off] : U(0);
-            if (chk && one) {
-                const uint64_t A = mix_a(a), B = mix_b(s);
-                c0 += A * B;
-                c1 += A + B;
-            }
-            warp_append<W>(st, oc, one, a, s);
-            // a heavy hitter: expanded by the grid afterwards
+            // a heavy hitter: expanded by the grid afterwards (it claims its own rows)
             if (cnt > kCoopPairs) {
                 const unsigned long long i = atomicAdd(nbig, 1ull);
                 big[i] = Big{off, cnt, (unsigned long long)s};  // at most one entry per probe tuple
             }
-            // a short list: the whole warp, 32 pairs per step
-            unsigned coop = __ballot_sync(0xffffffffu, cnt > 1 && cnt <= kCoopPairs);
+            // every other list of this step: one claim for the whole warp, each
+            // lane's rows at the exclusive prefix of the lanes' list lengths
+            const uint64_t mine = cnt <= kCoopPairs ? cnt : 0;
+            uint64_t incl = mine;
+#pragma unroll
+            for (int o = 1; o < 32; o <<= 1) {
+                const uint64_t y = __shfl_up_sync(0xffffffffu, incl, o);
+                if (lane >= (unsigned)o) incl += y;
+            }
+            const uint64_t tot = __shfl_sync(0xffffffffu, incl, 31);
+            if (!tot) continue;
+            unsigned long long base = 0;
+            if (lane == 0) base = atomicAdd(&ctr->count, (unsigned long long)tot);
+            base = __shfl_sync(0xffffffffu, base, 0);
+            const uint64_t at = base + incl - mine;
+            // one match: written by its own lane
+            if (mine == 1) {
+                const U a = rids[off];
+                if (at < pcap) out[at] = mk(a, s);
+                if (chk) {
+                    const uint64_t A = mix_a(a), B = mix_b(s);
+                    c0 += A * B;
+                    c1 += A + B;
+                }
+            }
+            // a short list: the whole warp, kUnroll x 32 pairs per step
+            unsigned coop = __ballot_sync(0xffffffffu, mine > 1);
             while (coop) {
                 const int L = __ffs(coop) - 1;
                 coop &= coop - 1;
-                const uint64_t o = __shfl_sync(0xffffffffu, off, L), n = __shfl_sync(0xffffffffu, cnt, L);
+                const uint64_t o = __shfl_sync(0xffffffffu, off, L), n = __shfl_sync(0xffffffffu, mine, L);
+                const uint64_t dst = __shfl_sync(0xffffffffu, at, L);
                 const U ss = __shfl_sync(0xffffffffu, s, L);
-                for (uint64_t j0 = 0; j0 < n; j0 += 32) {
-                    const bool has = j0 + lane < n;
-                    const U ra = has ? rids[o + j0 + lane] : U(0);
-                    if (chk && has) {
-                        const uint64_t A = mix_a(ra), B = mix_b(ss);
-                        c0 += A * B;
-                        c1 += A + B;
+                const uint64_t B = chk ? mix_b(ss) : 0;
+                for (uint64_t j0 = 0; j0 < n; j0 += 32 * kUnroll) {
+                    U ra[kUnroll];
+#pragma unroll
+                    for (unsigned u = 0; u < kUnroll; ++u) {
+                        const uint64_t j = j0 + u * 32 + lane;
+                        ra[u] = j < n ? rids[o + j] : U(0);
                     }
-                    warp_append<W>(st, oc, has, ra, ss);
+#pragma unroll
+                    for (unsigned u = 0; u < kUnroll; ++u) {
+                        const uint64_t j = j0 + u * 32 + lane;
+                        if (j < n) {
+                            if (dst + j < pcap) out[dst + j] = mk(ra[u], ss);
+                            if (chk) {
+                                const uint64_t A = mix_a(ra[u]);
+                                c0 += A * B;
+                                c1 += A + B;
+                            }
+                        }
+                    }
                 }
             }
         }

@@ -127,6 +127,58 @@ def test_phj_zipf_u64_count_full_size(hjm, ctx, theta_s):
     assert cnt > (10 ** 11 if theta_s == 1.0 else 10 ** 9)
 
 
+def _i64(v: int) -> int:
+    return v - (1 << 64) if v >= 1 << 63 else v
+
+
+def _fin_t(x: torch.Tensor) -> torch.Tensor:
+    """SplitMix64 finaliser on int64 tensors (wrapping products, logical shifts);
+    checked against the oracle's mixers below before use."""
+    x = x ^ ((x >> 30) & ((1 << 34) - 1))
+    x = x * _i64(0xBF58476D1CE4E5B9)
+    x = x ^ ((x >> 27) & ((1 << 37) - 1))
+    x = x * _i64(0x94D049BB133111EB)
+    return x ^ ((x >> 31) & ((1 << 33) - 1))
+
+
+def test_phj_zipf_u64_materialised_full_size(hjm, ctx):
+    # The skewed 64-bit workload at theta 0.5 with every pair written: about 4.9e9
+    # (rid_R, rid_S) pairs, 79 GB.  The count and the kernel's checksums against the
+    # oracle's per-key aggregation; then the whole pair buffer, read back in 2 GB
+    # pieces, checksummed on the GPU with torch arithmetic (independent of the join's
+    # kernels) against the same oracle values -- a multiset check of all 4.9e9 pairs
+    # -- and every pair checked to join equal keys.
+    R, S = W.zipf_pair(1 << 22, 1 << 26, 0.75, 0.5, 1 << 20, SEED, DEV, ids=(3, 5))
+    cnt, c0, c1 = oracle.join_aggregate(_np(R), _np(S))
+    assert cnt > 4 * 10 ** 9
+    res = hjm.hj_join(ctx, R, S, algo=hjm.HJ_ALGO_PHJ, mode=hjm.HJ_MATERIALIZE, checksum=True,
+                      out_capacity=cnt)
+    try:
+        assert (res.count, *res.checksum) == (cnt, c0, c1)
+        probe = torch.tensor([0, 1, 12345, (1 << 40) + 7, (1 << 63) - 1], dtype=torch.int64, device=DEV)
+        golden = _i64(0x9E3779B97F4A7C15)
+        assert [v & ((1 << 64) - 1) for v in _fin_t(probe).tolist()] == [oracle.mix_a(v) for v in probe.tolist()]
+        assert [v & ((1 << 64) - 1) for v in _fin_t(probe ^ golden).tolist()] == \
+            [oracle.mix_b(v) for v in probe.tolist()]
+        lib = hjm.load_library()
+        piece = 1 << 27
+        buf = torch.empty((piece, 2), dtype=torch.int64, device=DEV)
+        m64 = (1 << 64) - 1
+        t0 = t1 = 0
+        for at in range(0, cnt, piece):
+            n = min(piece, cnt - at)
+            assert lib.hj_copy(ctx.handle, buf.data_ptr(), res.pairs_ptr + at * 16, n * 16) == hjm.HJ_OK
+            a = _fin_t(buf[:n, 0])
+            b = _fin_t(buf[:n, 1] ^ golden)
+            t0 = (t0 + int((a * b).sum().item())) & m64
+            t1 = (t1 + int(a.sum().item()) + int(b.sum().item())) & m64
+            # every pair joins equal keys (rids are row numbers)
+            assert torch.equal(R[buf[:n, 0], 0], S[buf[:n, 1], 0])
+        assert (t0, t1) == (c0, c1)
+    finally:
+        res.free()
+
+
 @pytest.mark.parametrize("algo", [1, 2])
 def test_join_is_ordered_after_the_kernels_that_made_its_inputs(hjm, algo):
     # A default context orders its work on torch's current stream: a join queued
@@ -222,6 +274,37 @@ def test_oversize_partition_takes_the_global_fallback(hjm, ctx, mode):
         cnt, c0, c1 = oracle.join_aggregate(R, S)
         r = hjm.hj_join(ctx, Rg, Sg, algo=hjm.HJ_ALGO_PHJ, radix_bits=6, mode=1)
         assert (r.count, *r.checksum) == (cnt, c0, c1)
+
+
+@pytest.mark.parametrize("width", [4, 8])
+@pytest.mark.parametrize("mode", [0, 1, 2])
+def test_many_oversize_partitions_fall_back_together(hjm, ctx, width, mode):
+    # 60 keys repeated 2000-4000 times in R, spread over the 256 partitions of an
+    # 8-bit plan, make most of those partitions' tables overflow shared memory; S
+    # holds every heavy key a few times, in skewed amounts (large partitions are
+    # probed in several slices).  The fallback gathers all of them into one table
+    # per join; pairs, count and checksums must equal the oracle's.
+    dt = np.uint32 if width == 4 else np.uint64
+    rng = np.random.default_rng(12 + width)
+    heavy = rng.choice(np.arange(10, 1 << 20), 60, replace=False).astype(dt)
+    reps = rng.integers(2000, 4000, 60)
+    rk = np.concatenate([np.repeat(heavy, reps), rng.integers(1 << 20, 1 << 21, 30000).astype(dt)])
+    rk = rk[rng.permutation(len(rk))]
+    R = np.stack([rk, np.arange(len(rk), dtype=dt)], 1)
+    sk = np.concatenate([np.repeat(heavy, rng.integers(1, 40, 60)), rng.integers(1, 1 << 21, 300000).astype(dt)])
+    sk = sk[rng.permutation(len(sk))]
+    S = np.stack([sk, np.arange(len(sk), dtype=dt) + 3], 1)
+    view = np.int32 if width == 4 else np.int64
+    Rg = torch.from_numpy(np.ascontiguousarray(R).view(view)).to(DEV)
+    Sg = torch.from_numpy(np.ascontiguousarray(S).view(view)).to(DEV)
+    cnt, c0, c1 = oracle.join_aggregate(R, S)
+    r = hjm.hj_join(ctx, Rg, Sg, algo=hjm.HJ_ALGO_PHJ, radix_bits=8, mode=mode, checksum=True)
+    assert r.count == cnt
+    if mode != 0:
+        assert r.checksum == (c0, c1)
+    if mode == 2:
+        want = oracle.sorted_pairs(*oracle.hash_join(R, S))
+        assert np.array_equal(_got(r), want)
 
 
 @pytest.mark.parametrize("algo,bits", [(1, 0), (2, 6)])
