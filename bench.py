@@ -579,6 +579,14 @@ def run_hj(args, wl, ws, rank, local):
     step_s = ms / 1000.0 / args.steps
     join_roof = {"bytes_per_step": join_bytes, "achieved_gbs": join_bytes / step_s / 1e9,
                  "frac": join_bytes / step_s / 1e9 / peak, "frac_vs_g1": join_bytes_g1 / step_s / 1e9 / peak}
+    if bytes_k == 0:
+        # the dominant kernel has no per-launch byte count of its own (the key-list
+        # fallback: its rows are however many partitions overflowed): the whole join
+        # against its algorithmic bytes stands for it
+        roofline = {"bound": "hbm", "kernel": f"whole join (all kernels; dominant: {dom_name})",
+                    "achieved": join_roof["achieved_gbs"], "peak": peak, "unit": "GB/s", "frac": join_roof["frac"],
+                    "peak_kind": peak_kind, "bytes_per_launch": join_bytes, "launches": args.steps,
+                    "avg_launch_ms": ms / args.steps, "traffic": None}
     kernels = {k: {"launches": v[0], "ms": v[1], "share": v[1] / sum(x[1] for x in prof_all.values()),
                    "steps": prof_n}
                for k, v in sorted(prof_all.items(), key=lambda kv: -kv[1][1])}
