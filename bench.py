@@ -99,11 +99,12 @@ WORKLOADS = {
              "one all-to-all of R and one of S, a local hj_join, one all-reduce of count and checksums; strong "
              "scaling (the whole job is one join); pairs materialised, left on the rank that found them"),
     "coproc_16m": dict(
-        kind="coproc", nr=1 << 24, ns=1 << 24, dom=1 << 24, algo=2, shares=24,
+        kind="coproc", nr=1 << 24, ns=1 << 24, dom=1 << 24, algo=2, shares=1000,
         desc="CPU/GPU co-processing of the paper's default join, |R| = |S| = 2^24 (uint32 key, uint32 rid; R keys a "
              "permutation of 1..2^24, S keys uniform over them): the PHJ's join step divided between the GPU and "
              "the host cores (hj_join_coproc) at the cost model's share, and the model (Eq. 1-5) checked against "
-             "measured times at seeded random shares; pairs materialised"),
+             "measured times at 1000 seeded random shares (the paper's validation of its model); pairs "
+             "materialised"),
     "shj_1m": dict(
         nr=1 << 20, ns=1 << 20, dom=1 << 20, algo=1,
         desc="SHJ, |R|=|S|=2^20 (uint32 key, uint32 rid); R keys a permutation of 1..2^20, S keys drawn "
@@ -880,6 +881,20 @@ def run_sharded(args, wl, ws, rank, local):
         dist.destroy_process_group()
 
 
+def deciles(pts):
+    """Mean and max |relative error| of the model's two predictions per tenth of
+    the CPU share range."""
+    out = []
+    for b in range(10):
+        q = [p for p in pts if b / 10 <= p["share"] < (b + 1) / 10 or (b == 9 and p["share"] == 1.0)]
+        if q:
+            out.append({"share": [b / 10, (b + 1) / 10], "n": len(q),
+                        "mean_abs_rel_err": sum(abs(p["rel_err"]) for p in q) / len(q),
+                        "max_abs_rel_err": max(abs(p["rel_err"]) for p in q),
+                        "mean_abs_rel_err_whole_wait": sum(abs(p["rel_err_whole_wait"]) for p in q) / len(q)})
+    return out
+
+
 def run_coproc(args, wl, ws, rank, local):
     """hj_join_coproc on the paper's default join: per-item costs calibrated at CPU
     shares 0 and 1, then the cost model's predicted time (hj_coproc_time, steps
@@ -929,7 +944,7 @@ def run_coproc(args, wl, ws, rank, local):
     # CPU waits all of T1: the second prediction uses that wait
     pts, errs, errs_adj = [], [], []
     for r in shares:
-        meas = med([run(r)[0]["total"] for _ in range(2)])
+        meas = run(r)[0]["total"]
         pred, _, pred_gpu = hj.hj_coproc_time(x, cpu_s, gpu_s, [0.0, r], xfer_s=xf)
         pred_adj = max(pred_gpu, g1 * N + r * N * (xf + c2))
         err, err_adj = (pred - meas) / meas, (pred_adj - meas) / meas
@@ -966,7 +981,9 @@ def run_coproc(args, wl, ws, rank, local):
                       "mean_abs_rel_err": sum(errs) / len(errs), "max_abs_rel_err": max(errs),
                       "mean_abs_rel_err_whole_wait": sum(errs_adj) / len(errs_adj),
                       "max_abs_rel_err_whole_wait": max(errs_adj),
-                      "points": pts,
+                      "points_n": len(pts),
+                      "by_share_decile": deciles(pts),
+                      "points_sample": pts[:: max(1, len(pts) // 24)],
                       "measured_best": min(pts, key=lambda q: q["measured_s"])},
             "roofline": None, "cpu_baseline": None, "e2e": None, "gpu_launches": None, "clocks": clocks,
         }
