@@ -135,6 +135,8 @@ def parse():
     ap.add_argument("--plain-seconds", type=float, default=20.0,
                     help="serving: bound on the one-hj_join-per-request comparison run")
     ap.add_argument("--no-sweep", action="store_true", help="serving: skip the offered-load sweep")
+    ap.add_argument("--serve-workers", type=int, default=4, help="serving: worker threads (streams)")
+    ap.add_argument("--serve-wave-tuples", type=int, default=0, help="serving: tuples per wave (0: the default)")
     ap.add_argument("--scatter", default="auto", choices=["auto", "region", "ring"],
                     help="padded-pass scatter at 2^9..2^11 digits (hj_debug_scatter): auto, or force one kernel")
     return ap.parse_args()
@@ -1078,7 +1080,7 @@ def run_serve(args, wl, ws, rank, local):
         xs = sorted(xs)
         return xs[min(len(xs) - 1, int(math.ceil(q * len(xs))) - 1)]
 
-    with hj.Server(ctx, budget=wl["budget"], workers=3) as srv:
+    with hj.Server(ctx, budget=wl["budget"], workers=args.serve_workers, wave_tuples=args.serve_wave_tuples) as srv:
         # warm-up: the first requests of the stream
         for _ in range(args.warmup):
             for R, S in reqs[:min(K, 64)]:
@@ -1130,7 +1132,8 @@ def run_serve(args, wl, ws, rank, local):
             "config": {"workload": wl["desc"], "requests": n, "distinct_inputs": K,
                        "inputs": f"request i uses the seeded inputs and sizes of request i mod {K} of the stream "
                                  f"(device-resident, generated before the run)",
-                       "tuples": total, "pairs": pairs, "workers": 3, "budget_bytes": wl["budget"],
+                       "tuples": total, "pairs": pairs, "workers": args.serve_workers,
+                       "wave_tuples": args.serve_wave_tuples or "default (2^26)", "budget_bytes": wl["budget"],
                        "parallelism": f"replicas x{ws}", "l2": "inputs far larger than the 129 MB L2; no flush"},
             "saturated": {"tuples_per_s": sat, "span_s": span, "p50_ms": 1000 * pct(lat_sat, 0.5),
                           "p99_ms": 1000 * pct(lat_sat, 0.99), "mismatches": bad_sat},

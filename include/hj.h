@@ -281,7 +281,7 @@ typedef struct hj_server hj_server;
 
 typedef struct hj_server_opts {
     uint64_t budget_bytes; /* HBM admission budget (0: min(120 GiB, 60% of free memory)) */
-    int32_t workers;       /* waves in flight at once, one stream each (0: 3; at most 16) */
+    int32_t workers;       /* waves in flight at once, one stream each (0: 4; at most 16) */
     int32_t max_wave;      /* most requests in one wave (0: 512)                       */
     uint64_t wave_tuples;  /* a wave stops growing past this many tuples of R and S;
                               a request above it runs alone (0: 2^26)                 */
