@@ -75,6 +75,11 @@ __device__ unsigned long long block_scan_u64(unsigned long long v, unsigned long
     return before + x - v;
 }
 
+// Records (or tail chunks) per thread and step of the plan: each thread loads its
+// kPlanPer entries at once, so a list of up to 1024 * kPlanPer entries takes one
+// block scan.
+constexpr int kPlanPer = 4;
+
 __global__ void __launch_bounds__(1024) compact_plan_kernel(const unsigned long long *nrec_p, const ChunkRec *rec,
                                                             uint64_t cap, hj_counters *ctr, uint64_t pcap,
                                                             PlanView pv) {
@@ -93,44 +98,67 @@ __global__ void __launch_bounds__(1024) compact_plan_kernel(const unsigned long 
         if (ci >= tb && ci < tb + nt) pv.tail_used[ci - tb] = rec[i].used;
     }
     __syncthreads();
-    // holes below count, in record order
+    const uint64_t step = (uint64_t)blockDim.x * kPlanPer;
+    // holes below count, in record order (thread t holds records t*kPlanPer ...)
     unsigned long long nd = 0, dp = 0;
-    for (uint64_t b = 0; b < n; b += blockDim.x) {
-        const uint64_t i = b + threadIdx.x;
-        unsigned long long s0 = 0, len = 0;
-        if (i < n) {
-            const ChunkRec r = rec[i];
-            s0 = r.base + r.used;
-            const unsigned long long e = r.base + kChunkPairs < count ? r.base + kChunkPairs : count;
-            len = s0 < e ? e - s0 : 0ull;
+    for (uint64_t b = 0; b < n; b += step) {
+        unsigned long long s0[kPlanPer], len[kPlanPer], f = 0, l = 0;
+#pragma unroll
+        for (int q = 0; q < kPlanPer; ++q) {
+            const uint64_t i = b + (uint64_t)threadIdx.x * kPlanPer + q;
+            s0[q] = len[q] = 0;
+            if (i < n) {
+                const ChunkRec r = rec[i];
+                s0[q] = r.base + r.used;
+                const unsigned long long e = r.base + kChunkPairs < count ? r.base + kChunkPairs : count;
+                len[q] = s0[q] < e ? e - s0[q] : 0ull;
+            }
+            f += len[q] ? 1ull : 0ull;
+            l += len[q];
         }
         unsigned long long tf, tl;
-        const unsigned long long xf = block_scan_u64(len ? 1ull : 0ull, sh, &tf);
-        const unsigned long long xl = block_scan_u64(len, sh, &tl);
-        if (len) {
-            pv.dst_start[nd + xf] = s0;
-            pv.dst_pref[nd + xf] = dp + xl;
+        unsigned long long xf = block_scan_u64(f, sh, &tf);
+        unsigned long long xl = block_scan_u64(l, sh, &tl);
+#pragma unroll
+        for (int q = 0; q < kPlanPer; ++q) {
+            if (len[q]) {
+                pv.dst_start[nd + xf] = s0[q];
+                pv.dst_pref[nd + xf] = dp + xl;
+                ++xf;
+                xl += len[q];
+            }
         }
         nd += tf;
         dp += tl;
     }
     // valid runs of the tail chunks, in address order
     unsigned long long ns = 0, sp = 0;
-    for (uint64_t b = 0; b < nt; b += blockDim.x) {
-        const uint64_t t = b + threadIdx.x;
-        unsigned long long a = 0, len = 0;
-        if (t < nt) {
-            const unsigned long long cb = (tb + t) * kChunkPairs, ce = cb + pv.tail_used[t];
-            a = cb > count ? cb : count;
-            const unsigned long long e = ce < cursor ? ce : cursor;
-            len = a < e ? e - a : 0ull;
+    for (uint64_t b = 0; b < nt; b += step) {
+        unsigned long long a[kPlanPer], len[kPlanPer], f = 0, l = 0;
+#pragma unroll
+        for (int q = 0; q < kPlanPer; ++q) {
+            const uint64_t t = b + (uint64_t)threadIdx.x * kPlanPer + q;
+            a[q] = len[q] = 0;
+            if (t < nt) {
+                const unsigned long long cb = (tb + t) * kChunkPairs, ce = cb + pv.tail_used[t];
+                a[q] = cb > count ? cb : count;
+                const unsigned long long e = ce < cursor ? ce : cursor;
+                len[q] = a[q] < e ? e - a[q] : 0ull;
+            }
+            f += len[q] ? 1ull : 0ull;
+            l += len[q];
         }
         unsigned long long tf, tl;
-        const unsigned long long xf = block_scan_u64(len ? 1ull : 0ull, sh, &tf);
-        const unsigned long long xl = block_scan_u64(len, sh, &tl);
-        if (len) {
-            pv.src_start[ns + xf] = a;
-            pv.src_pref[ns + xf] = sp + xl;
+        unsigned long long xf = block_scan_u64(f, sh, &tf);
+        unsigned long long xl = block_scan_u64(l, sh, &tl);
+#pragma unroll
+        for (int q = 0; q < kPlanPer; ++q) {
+            if (len[q]) {
+                pv.src_start[ns + xf] = a[q];
+                pv.src_pref[ns + xf] = sp + xl;
+                ++xf;
+                xl += len[q];
+            }
         }
         ns += tf;
         sp += tl;
@@ -148,6 +176,9 @@ __global__ void __launch_bounds__(1024) compact_plan_kernel(const unsigned long 
     }
 }
 
+// Pairs moved by a warp per step of its copy loop, per lane.
+constexpr unsigned kMoveUnroll = 4;
+
 template <class P>
 __global__ void compact_move_kernel(P *pairs, PlanView pv) {
     const unsigned lane = threadIdx.x & 31;
@@ -156,19 +187,37 @@ __global__ void compact_move_kernel(P *pairs, PlanView pv) {
     const uint64_t nw = ((uint64_t)gridDim.x * blockDim.x) >> 5;
     for (uint64_t i = w0; i < nd; i += nw) {
         const unsigned long long ds = pv.dst_start[i], m0 = pv.dst_pref[i], m1 = pv.dst_pref[i + 1];
-        // the source run holding move index m0: last t with src_pref[t] <= m0
+        // the source run holding move index m0: the last t with src_pref[t] <= m0
+        // (src_pref is strictly increasing, src_pref[ns] = the total > m0).  Each
+        // round the lanes test 32 evenly spaced pivots strictly inside (lo, hi):
+        // the largest with src_pref <= m0 becomes lo, the smallest above m0 becomes
+        // hi.  Lane 31's pivot lo + floor(32 (hi - lo) / 33) is inside whenever
+        // hi - lo >= 2, so every round shrinks the interval (about 33x).
         uint64_t lo = 0, hi = ns;
-        while (hi - lo > 1) {
-            const uint64_t mid = (lo + hi) / 2;
-            if (pv.src_pref[mid] <= m0) lo = mid;
-            else hi = mid;
+        for (int it = 0; it < 64 && hi - lo > 1; ++it) {
+            const uint64_t piv = lo + ((hi - lo) * (lane + 1)) / 33;
+            const bool in = piv > lo && piv < hi;
+            const bool le = in && pv.src_pref[piv] <= m0;
+            const unsigned ml = __ballot_sync(0xffffffffu, le), mg = __ballot_sync(0xffffffffu, in && !le);
+            const uint64_t nlo = ml ? __shfl_sync(0xffffffffu, piv, 31 - __clz(ml)) : lo;
+            const uint64_t nhi = mg ? __shfl_sync(0xffffffffu, piv, __ffs(mg) - 1) : hi;
+            lo = nlo;
+            hi = nhi;
         }
         unsigned long long m = m0;
         for (uint64_t t = lo; m < m1 && t < ns; ++t) {
             const unsigned long long o = m - pv.src_pref[t], avail = pv.src_pref[t + 1] - m;
             const unsigned long long k = avail < m1 - m ? avail : m1 - m;
             const unsigned long long src = pv.src_start[t] + o, dst = ds + (m - m0);
-            for (unsigned long long j = lane; j < k; j += 32) pairs[dst + j] = pairs[src + j];
+            for (unsigned long long j = lane; j < k; j += 32 * kMoveUnroll) {
+                P v[kMoveUnroll];
+#pragma unroll
+                for (unsigned u = 0; u < kMoveUnroll; ++u)
+                    if (j + 32 * u < k) v[u] = pairs[src + j + 32 * u];
+#pragma unroll
+                for (unsigned u = 0; u < kMoveUnroll; ++u)
+                    if (j + 32 * u < k) pairs[dst + j + 32 * u] = v[u];
+            }
             m += k;
         }
     }
