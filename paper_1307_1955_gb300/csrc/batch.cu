@@ -24,7 +24,7 @@ using namespace hj;
 
 namespace {
 
-constexpr uint32_t kStagePairs = 32768;  // staging rows per CTA
+constexpr uint32_t kStagePairs = 256;  // staging rows per warp (>= 32 x the items of a probe group)
 
 int join_bits(uint64_t nR) {
     int b = 1;
@@ -237,7 +237,7 @@ extern "C" hj_status hj_join_batch(hj_ctx *c, int n, const hj_rel *Rs, const hj_
         if (!cur.empty()) waves.push_back(cur);
     }
     DevBuf ctrs(c), slots(c), dpairs(c), dcaps(c), stage(c);
-    if (!agg) HJ_TRY(stage.alloc(partition_join_ctas(c, W, agg, 8192) * kStagePairs * tb));
+    if (!agg) HJ_TRY(stage.alloc(partition_join_warps(c) * kStagePairs * tb));
     HJ_TRY(ctrs.alloc((uint64_t)n * sizeof(hj_counters)));
     HJ_TRY(slots.alloc((uint64_t)n * sizeof(JoinSlot)));
     HJ_CUDA(c, cudaMemsetAsync(ctrs.p, 0, (uint64_t)n * sizeof(hj_counters), c->stream));

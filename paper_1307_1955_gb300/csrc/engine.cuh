@@ -89,7 +89,8 @@ uint64_t tail_split_from(hj_ctx *c, int width, int agg, uint64_t NP, uint64_t ex
 // table in shared memory; persistent CTAs take tasks from c->d_ctr->work (which
 // must be zero at launch).  Tasks whose table does not fit are appended to
 // `oversize` (task indices) and counted in c->d_ctr->n_oversize.  Pairs go to
-// each task's join slot: with `stage` (a staging area of scap pairs per CTA) by
+// each task's join slot: with `stage` (a staging area of scap pairs per warp, for
+// partition_join_warps(c) warps) by
 // exact claims, otherwise by per-warp chunks recorded in `ra`.
 hj_status partition_join(hj_ctx *c, int width, int agg, const PartTask *tasks, uint64_t ntasks, const JoinSlot *slots,
                          uint64_t expect_r, int checksum, uint32_t *oversize, RecArea ra, void *stage,

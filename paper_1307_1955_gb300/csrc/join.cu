@@ -539,16 +539,13 @@ __device__ __forceinline__ void soa_coop_emit(const SoaTab<W> &t, typename Tup<W
 // How a CTA's warps place the pairs of its partition tasks.
 //
 // ChunkSink: every warp takes whole chunks of the join's pair buffer (emit.cuh);
-// partly used chunks are recorded and compacted by the host afterwards.  Used for
-// a single join: no extra traffic, a small host fix-up at the end.
+// partly used chunks are recorded and compacted on the device afterwards.  Used
+// for a single join: no extra traffic, a small fix-up at the end.
 //
-// StageSink: the CTA appends a task's pairs to its own staging area (global
-// memory, L2-resident) through a shared-memory cursor; when the task is done the
-// CTA claims exactly that many rows of the join's buffer with one atomicAdd and
-// copies them.  Used for batches of joins, where per-warp chunks would leave a
-// partly used chunk per warp per task.  A task whose pairs overflow the staging
-// area places the rest with exact warp-sized claims.  The join's pair count is the
-// claim cursor (ctr->count).
+// WarpStageSink (below): every warp stages its pairs in a private buffer and
+// claims exact rows of the join's buffer per buffer-full.  Used for batches of
+// joins, where per-warp chunks would leave a partly used chunk per warp per join.
+// The join's pair count is the claim cursor (ctr->count).
 template <int W> struct ChunkSink {
     using T = typename Tup<W>::U;
     OutState st;
@@ -664,43 +661,54 @@ template <int W> struct ChunkSink {
     }
 };
 
-struct StageShared {
-    unsigned int cnt, fail;
-    unsigned long long base;
-};
-
-template <int W> struct StageSink {
+// Per-warp staged exact output (batches of joins, whose many joins per launch
+// would leave a partly filled chunk per warp and join): each warp collects its
+// pairs in a private buffer of scap pairs in global memory (a few KB per warp,
+// L2-resident) and, when the buffer fills or the warp moves on to another join,
+// claims exactly that many rows of the join's buffer with one atomic add and
+// copies them out with coalesced stores.  Output is dense as written (no
+// compaction) and the sink needs no CTA barrier.  scap >= 32 x the items of a
+// group, so one flush always makes room.
+template <int W> struct WarpStageSink {
     using T = typename Tup<W>::U;
     using P = typename std::conditional<W == 4, uint2, ulonglong2>::type;
-    P *stage;  // this CTA's staging area
-    uint32_t scap;
-    StageShared *sh;
-    const JoinSlot *slots;
-    unsigned join = 0;
+    P *stage = nullptr;  // this warp's buffer
+    uint32_t scap = 0;
+    const JoinSlot *slots = nullptr;
+    unsigned join = ~0u;
+    uint32_t used = 0;  // warp-uniform
     __device__ __forceinline__ static P mk(T a, T b) {
         if constexpr (W == 4) return make_uint2(a, b);
         else return make_ulonglong2(a, b);
     }
-    // every thread calls it at the start of a task (the counters are reset by
-    // thread 0 before the task's first barrier)
-    __device__ __forceinline__ void begin_task(unsigned j) { join = j; }
+    // all 32 lanes: the staged pairs to exact rows of the join's buffer (pairs past
+    // its capacity are dropped; the count stays exact)
+    __device__ __forceinline__ void flush() {
+        if (!used) return;
+        __syncwarp();  // the buffer's stores are visible to every lane
+        const unsigned lane = threadIdx.x & 31;
+        unsigned long long b = 0;
+        if (lane == 0) b = atomicAdd(&slots[join].ctr->count, (unsigned long long)used);
+        b = __shfl_sync(0xffffffffu, b, 0);
+        P *out = (P *)slots[join].pairs;
+        const unsigned long long pc = slots[join].pcap;
+        for (uint32_t i = lane; i < used; i += 32)
+            if (b + i < pc) out[b + i] = stage[i];
+        __syncwarp();  // read before the buffer is refilled
+        used = 0;
+    }
+    __device__ __forceinline__ void begin_task(unsigned j) {
+        if (j == join) return;
+        flush();
+        join = j;
+    }
     __device__ __forceinline__ void append(bool has, T a, T b) {
         const unsigned mask = __ballot_sync(0xffffffffu, has);
         if (!mask) return;
         const unsigned lane = threadIdx.x & 31, k = __popc(mask), rank = __popc(mask & ((1u << lane) - 1u));
-        unsigned pos = 0;
-        if (lane == 0) pos = atomicAdd(&sh->cnt, k);
-        pos = __shfl_sync(0xffffffffu, pos, 0);
-        if (pos + k <= scap) {
-            if (has) stage[pos + rank] = mk(a, b);
-            return;
-        }
-        // the staging area is full: claim exact rows of the join's buffer
-        if (lane == 0) atomicMin(&sh->fail, pos);
-        unsigned long long g = 0;
-        if (lane == 0) g = atomicAdd(&slots[join].ctr->count, (unsigned long long)k);
-        g = __shfl_sync(0xffffffffu, g, 0);
-        if (has && g + rank < slots[join].pcap) ((P *)slots[join].pairs)[g + rank] = mk(a, b);
+        if (used + k > scap) flush();
+        if (has) stage[used + rank] = mk(a, b);
+        used += k;
     }
     template <int IT>
     __device__ __forceinline__ void append_group(const uint32_t *cnt, const T *first, const T *r) {
@@ -712,47 +720,22 @@ template <int W> struct StageSink {
             tot += __popc(m[i]);
         }
         if (!tot) return;
-        unsigned pos = 0;
-        if (lane == 0) pos = atomicAdd(&sh->cnt, tot);
-        pos = __shfl_sync(0xffffffffu, pos, 0);
-        if (pos + tot <= scap) {
-            unsigned run = 0;
-#pragma unroll
-            for (int i = 0; i < IT; ++i) {
-                if (cnt[i] == 1) stage[pos + run + __popc(m[i] & lt)] = mk(first[i], r[i]);
-                run += __popc(m[i]);
-            }
-            return;
-        }
-        if (lane == 0) atomicMin(&sh->fail, pos);
-        unsigned long long g = 0;
-        if (lane == 0) g = atomicAdd(&slots[join].ctr->count, (unsigned long long)tot);
-        g = __shfl_sync(0xffffffffu, g, 0);
-        unsigned run = 0;
+        if (used + tot > scap) flush();
+        unsigned run = used;
 #pragma unroll
         for (int i = 0; i < IT; ++i) {
-            const unsigned long long q = g + run + __popc(m[i] & lt);
-            if (cnt[i] == 1 && q < slots[join].pcap) ((P *)slots[join].pairs)[q] = mk(first[i], r[i]);
+            if (cnt[i] == 1) stage[run + __popc(m[i] & lt)] = mk(first[i], r[i]);
             run += __popc(m[i]);
         }
+        used += tot;
     }
     template <int IT>
     __device__ __forceinline__ void append_runs(const uint32_t *cnt, const T *first, const T *r) {
         append_group<IT>(cnt, first, r);
     }
     __device__ __forceinline__ hj_counters *ctr() const { return slots[join].ctr; }
-    // all threads: claim the staged pairs' rows and copy them (contains barriers)
-    __device__ __forceinline__ void end_task() {
-        __syncthreads();
-        const unsigned n = sh->cnt < sh->fail ? sh->cnt : sh->fail;
-        if (threadIdx.x == 0) sh->base = n ? atomicAdd(&slots[join].ctr->count, (unsigned long long)n) : 0ull;
-        __syncthreads();
-        const unsigned long long b = sh->base, pc = slots[join].pcap;
-        P *out = (P *)slots[join].pairs;
-        for (unsigned i = threadIdx.x; i < n; i += blockDim.x)
-            if (b + i < pc) out[b + i] = stage[i];
-    }
-    __device__ __forceinline__ void finish() {}
+    __device__ __forceinline__ void end_task() {}
+    __device__ __forceinline__ void finish() { flush(); }
 };
 
 // One group of IT probe items against the table, in phases so that the items'
@@ -861,9 +844,8 @@ __device__ __forceinline__ void probe_fast(const SoaTab<W> &tab, const typename 
     using T = typename Tup<W>::U;
     using Vec = typename Tup<W>::Vec;
     constexpr int PV = Tup<W>::kPerVec, IT = U * PV;
-    // the walk queue serves the chunk sink; the staging sink (batches of joins),
-    // whose appends need more registers, walks each item at once
-    constexpr bool kQueue = std::is_same<Sink, ChunkSink<W>>::value;
+    // runs that go on past a full home bucket are queued and walked 32 at a time
+    constexpr bool kQueue = true;
     const uint32_t gstride = nwarps * 32u * U;
     const unsigned lt = (1u << lane) - 1u;
     uint32_t g = warp * 32u * U;
@@ -1067,7 +1049,6 @@ __global__ void __launch_bounds__(NT, 2048 / NT / 2) partition_join_kernel(
     __shared__ TableSide side;
     __shared__ int s_full;
     __shared__ unsigned long long s_p;
-    __shared__ StageShared s_stage;
     const unsigned lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
 
     Sink sink;
@@ -1075,17 +1056,12 @@ __global__ void __launch_bounds__(NT, 2048 / NT / 2) partition_join_kernel(
         sink.slots = slots;
         sink.ra = ra;
     } else {
-        sink.stage = (typename StageSink<W>::P *)stage_base + (size_t)blockIdx.x * scap;
+        sink.stage = (typename WarpStageSink<W>::P *)stage_base + ((size_t)blockIdx.x * nwarps + warp) * scap;
         sink.scap = scap;
-        sink.sh = &s_stage;
         sink.slots = slots;
     }
     for (;;) {
-        if (threadIdx.x == 0) {
-            s_p = atomicAdd(&work->work, 1ull);
-            s_stage.cnt = 0;
-            s_stage.fail = 0xFFFFFFFFu;
-        }
+        if (threadIdx.x == 0) s_p = atomicAdd(&work->work, 1ull);
         __syncthreads();
         const uint64_t ti = s_p;
         if (ti >= ntasks) break;
@@ -1459,7 +1435,7 @@ hj_status partition_join(hj_ctx *c, int width, int agg, const PartTask *tasks, u
     // the fast probe (no aggregate, no checksum) into the chunk sink adds each
     // warp's walk queue, within what the shape's CTAs per SM can have (two
     // 512-thread CTAs share an SM)
-    const uint64_t qbytes = (!agg && !checksum && !stage) ? (uint64_t)(cfg.nt / 32) * kWalkQ * 2 * width : 0;
+    const uint64_t qbytes = (!agg && !checksum) ? (uint64_t)(cfg.nt / 32) * kWalkQ * 2 * width : 0;
     const uint64_t total_max = cfg.nt == 512 ? (112ull << 10) : (222ull << 10);
     const uint64_t budget = std::min<uint64_t>(cfg.smem_limit + qbytes, total_max) - qbytes;
     uint64_t max_slots = (budget - bitmap_bytes) / slot_bytes / 128 * 128;
@@ -1487,7 +1463,7 @@ hj_status partition_join(hj_ctx *c, int width, int agg, const PartTask *tasks, u
     } while (0)
 #define HJ_PJ_SK(WW)                                            \
     do {                                                        \
-        if (stage) HJ_PJ_F(WW, StageSink);                       \
+        if (stage) HJ_PJ_F(WW, WarpStageSink);                       \
         else HJ_PJ_F(WW, ChunkSink);                             \
     } while (0)
     if (width == 4) {
