@@ -1269,7 +1269,7 @@ def run_outcore(args, wl, ws, rank, local):
 # process of its own so that the previous run's device memory is gone: the batched joins, the served
 # request stream and the skewed 64-bit joins.  Their summaries ride on the default line ("also").
 EXTRAS = (
-    ("batched", ["--workload", "batch_4096", "--steps", "3", "--warmup", "1", "--plain-steps", "1"]),
+    ("batched", ["--workload", "batch_4096", "--steps", "5", "--warmup", "2", "--plain-steps", "1"]),
     ("served", ["--workload", "serve_20000", "--warmup", "1", "--plain-seconds", "8", "--no-sweep"]),
     ("skewed_u64_theta_0.5", ["--workload", "zipf_4m_64m_t05", "--steps", "10", "--warmup", "3", "--no-e2e"]),
     ("skewed_u64_theta_1.0", ["--workload", "zipf_4m_64m_t10", "--steps", "10", "--warmup", "3", "--no-e2e"]),
