@@ -105,6 +105,37 @@ def test_batch_oversize_partition_and_overflow(hjm, ctx):
         res[j].free()
 
 
+@pytest.mark.parametrize("mode", [1, 2])
+def test_batch_many_joins_with_many_oversize_partitions(hjm, ctx, mode):
+    # Four joins whose R holds 3-40 keys repeated 1500-3000 times (several
+    # partitions per join overflow shared memory; one join has a single such
+    # partition), beside a join with none: the fallback groups the overflowing
+    # tasks by join and gathers each join's rows into its own table.
+    rng = np.random.default_rng(31)
+    Rs, Ss, host = [], [], []
+    for j, nheavy in enumerate([40, 3, 1, 25, 0]):
+        heavy = rng.choice(np.arange(10, 1 << 20), max(nheavy, 1), replace=False).astype(np.uint32)[:nheavy]
+        rk = np.concatenate([np.repeat(heavy, rng.integers(1500, 3000, nheavy)),
+                             rng.integers(1 << 20, 1 << 21, 20000).astype(np.uint32)])
+        rk = rk[rng.permutation(len(rk))]
+        sk = np.concatenate([np.repeat(heavy, rng.integers(1, 20, nheavy)),
+                             rng.integers(1, 1 << 21, 100000).astype(np.uint32)])
+        sk = sk[rng.permutation(len(sk))]
+        R = np.stack([rk, np.arange(len(rk), dtype=np.uint32)], 1)
+        S = np.stack([sk, np.arange(len(sk), dtype=np.uint32) + 5], 1)
+        host.append((R, S))
+        Rs.append(torch.from_numpy(np.ascontiguousarray(R).view(np.int32)).to(DEV))
+        Ss.append(torch.from_numpy(np.ascontiguousarray(S).view(np.int32)).to(DEV))
+    res = hjm.hj_join_batch(ctx, Rs, Ss, mode=mode, checksum=True)
+    for j, (R, S) in enumerate(host):
+        cnt, c0, c1 = oracle.join_aggregate(R, S)
+        assert (res[j].count, *res[j].checksum) == (cnt, c0, c1), j
+        if mode == 2:
+            want = oracle.sorted_pairs(*oracle.hash_join(R, S))
+            assert np.array_equal(_sorted(res[j].pairs_numpy()), want), j
+            res[j].free()
+
+
 def test_batch_full_size_counts_and_sampled_pairs(hjm, ctx):
     # The 4096-join batch at full size (|R| log-uniform in [2^10, 2^22], |S| = 4 |R|, about
     # 1.1e10 tuples), in the launch configuration the bench times (pairs materialised,
