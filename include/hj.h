@@ -50,7 +50,10 @@ typedef int32_t hj_status;
 #define HJ_U32 4
 #define HJ_U64 8
 
-/* A relation: n tuples of <key, rid>, both fields `width` bytes (HJ_U32 or HJ_U64). */
+/* A relation: n tuples of <key, rid>, both fields `width` bytes (HJ_U32 or HJ_U64).
+ * The device entry points take relations of fewer than 2^32 - 1 tuples (row offsets
+ * inside a partition pass are 32-bit); hj_join_host_large splits larger host
+ * relations into partition pairs below that size. */
 typedef struct hj_rel {
     const void *tuples;
     uint64_t n;

@@ -205,8 +205,8 @@ hj_status check_rel(hj_ctx *c, const hj_rel *r, const char *name) {
                                            (unsigned long long)r->n);
     if (r->n && ((uintptr_t)r->tuples & 15))
         return set_err(c, HJ_E_INVALID, "%s tuples are not 16-byte aligned", name);
-    if (r->width == HJ_U32 && r->n >= 0xFFFFFFFFull)
-        return set_err(c, HJ_E_INVALID, "%s: 4-byte relations hold fewer than 2^32 - 1 tuples", name);
+    if (r->n >= 0xFFFFFFFFull)  // partition passes keep 32-bit row offsets
+        return set_err(c, HJ_E_INVALID, "%s: a relation holds fewer than 2^32 - 1 tuples", name);
     return HJ_OK;
 }
 

@@ -383,6 +383,17 @@ def test_invalid_arguments(hjm, ctx):
     assert e.value.status == hjm.HJ_E_INVALID
     with pytest.raises(hjm.HJError):
         hjm.hj_join(ctx, R, S, algo=hjm.HJ_ALGO_PHJ, radix_bits=13, passes=1)
+    # 2^32 - 1 rows or more, either width: refused before any device memory is read
+    lib = hjm.load_library()
+    for width in (4, 8):
+        big = hjm.hj_rel(R.data_ptr(), (1 << 32) - 1, width, 0)
+        small = hjm.hj_rel(R.data_ptr(), 10, width, 0)
+        res = hjm.hj_result()
+        o = hjm._opts()
+        assert lib.hj_join(ctx.handle, ctypes.byref(big), ctypes.byref(small), ctypes.byref(o),
+                           ctypes.byref(res)) == hjm.HJ_E_INVALID
+        assert lib.hj_join(ctx.handle, ctypes.byref(small), ctypes.byref(big), ctypes.byref(o),
+                           ctypes.byref(res)) == hjm.HJ_E_INVALID
 
 
 def test_injected_allocation_failure_leaks_nothing(hjm):
