@@ -253,6 +253,10 @@ hj_status partition_rel(hj_ctx *c, const hj_rel *in, int b1, int b2, int pad, De
     const uint64_t n = in->n, tb = tuple_bytes(in->width);
     DevBuf seg(c), A(c), off1(c);
     const uint64_t rows1 = partition_out_rows(c, in->width, n, 1, b1, pad);
+    // run offsets inside a pass are 32-bit: the padded output must stay below 2^32 rows
+    if (rows1 >= 0xFFFFFFFFull || (b2 && partition_out_rows(c, in->width, rows1, 1ull << b1, b2, pad) >= 0xFFFFFFFFull))
+        return set_err(c, HJ_E_UNSUPPORTED, "%llu tuples padded to whole sectors pass 2^32 rows",
+                       (unsigned long long)n);
     HJ_TRY(A.alloc(rows1 * tb + 64));
     HJ_TRY(off1.alloc(((1ull << b1) + 1) * 8));
     if (pad && b1 <= 11) {  // the first pass is one segment: the fused form
