@@ -33,14 +33,17 @@ namespace {
 
 // Effective thread instructions per item of each kernel at the sustained issue
 // rate below: ncu's smsp__inst_executed x 32 / items, scaled so that the model's
-// time equals the kernel's measured time on GB300 (4-byte tuples; the 2^24 x 2^28
-// join at 11 radix bits, 12 bits in one and two passes, and SHJ at 2^20 and 2^24
-// build tuples).  hj_tune measures the real thing on the caller's relations.
-constexpr double kIptHist = 22.0;         // per input tuple (bandwidth-bound)
-constexpr double kIptScatterTma = 132.0;  // per input tuple, fan-out <= 2^11 (TMA-staged kernel)
-constexpr double kIptScatterWide = 293.0; // per input tuple, fan-out 2^12
-constexpr double kIptJoinProbe = 82.0;    // per S tuple, shared-memory table
-constexpr double kIptJoinBuild = 60.0;    // per R tuple, shared-memory table
+// time equals the kernel's measured time on GB300 (4-byte tuples: the 2^24 x 2^28
+// join at 11 radix bits -- scatter 1.302 ms, join 1.019 ms -- and the build-heavy
+// 2^24 x 2^24 join -- join 0.229 ms, which with the first fixes the probe and build
+// costs --, 12 bits in one and two passes, and SHJ at 2^20 and 2^24 build tuples).
+// hj_tune measures the real thing on the caller's relations.
+constexpr double kIptHist = 22.0;            // per input tuple (bandwidth-bound)
+constexpr double kIptScatterRing = 101.0;    // per input tuple, ring scatter (2^10 and 2^11 digits)
+constexpr double kIptScatterRegion = 150.0;  // per input tuple, region scatter (fan-out <= 2^9; measured 131 at 2^8, 171 per pass of 6 + 6 bits)
+constexpr double kIptScatterWide = 293.0;    // per input tuple, fan-out 2^12
+constexpr double kIptJoinProbe = 70.0;       // per S tuple, shared-memory table
+constexpr double kIptJoinBuild = 232.0;      // per R tuple, shared-memory table (latency-bound build)
 constexpr double kIptShjBuild = 40.0;     // per R tuple, global table
 constexpr double kIptShjProbe = 60.0;     // per S tuple, global table
 constexpr double kIssueFraction = 0.55;   // sustained share of the issue slots
@@ -48,7 +51,7 @@ constexpr double kCopyFraction = 0.83;    // share of nominal HBM bandwidth a co
 constexpr double kRandomFraction = 0.2;   // share for 32-byte random sectors (table probes)
 constexpr double kLaunchS = 4e-6;         // per kernel launch
 constexpr double kShjFixedS = 55e-6;      // per SHJ call: table fill, allocations, one host synchronisation
-constexpr double kPhjFixedS = 170e-6;     // per PHJ call: allocations, two host synchronisations
+constexpr double kPhjFixedS = 50e-6;      // per PHJ call: allocations, launch gaps, one host synchronisation
 
 }  // namespace
 
@@ -97,8 +100,10 @@ double predict_seconds(const CostModel &m, int width, bool agg, bool mat, uint64
         const int b1 = passes == 2 ? bits - bits / 2 : bits, b2 = passes == 2 ? bits / 2 : 0;
         for (int p = 0; p < passes; ++p) {
             const int bp = p == 0 ? b1 : b2;
-            const double ipt = bp <= 11 ? kIptScatterTma : kIptScatterWide;
-            s[0] += std::max(t * n / b, n * kIptHist / ir) + 2 * 8 * kLaunchS;
+            const double ipt = bp >= 10 && bp <= 11 ? kIptScatterRing : bp <= 9 ? kIptScatterRegion : kIptScatterWide;
+            // a first pass at <= 2^11 digits is two launches per relation (histogram
+            // and scatter place the runs themselves), any other pass eight
+            s[0] += std::max(t * n / b, n * kIptHist / ir) + (p == 0 && bp <= 11 ? 2 * 2 : 2 * 8) * kLaunchS;
             s[1] += std::max(2.0 * t * n / b, n * ipt / ir);
         }
         // fewer partition pairs than join CTAs leave SMs idle
