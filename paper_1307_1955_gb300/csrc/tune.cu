@@ -40,7 +40,8 @@ namespace {
 // hj_tune measures the real thing on the caller's relations.
 constexpr double kIptHist = 22.0;            // per input tuple (bandwidth-bound)
 constexpr double kIptScatterRing = 101.0;    // per input tuple, ring scatter (2^10 and 2^11 digits)
-constexpr double kIptScatterRegion = 150.0;  // per input tuple, region scatter (fan-out <= 2^9; measured 131 at 2^8, 171 per pass of 6 + 6 bits)
+constexpr double kIptScatterRegion = 131.0;  // per input tuple, region scatter at 2^8 and 2^9 digits
+constexpr double kIptScatterRegionLow = 115.0;  // per input tuple, region scatter at <= 2^7 digits (measured per pass of 6 + 6 bits)
 constexpr double kIptScatterWide = 293.0;    // per input tuple, fan-out 2^12
 constexpr double kIptJoinProbe = 70.0;       // per S tuple, shared-memory table
 constexpr double kIptJoinBuild = 232.0;      // per R tuple, shared-memory table (latency-bound build)
@@ -100,7 +101,10 @@ double predict_seconds(const CostModel &m, int width, bool agg, bool mat, uint64
         const int b1 = passes == 2 ? bits - bits / 2 : bits, b2 = passes == 2 ? bits / 2 : 0;
         for (int p = 0; p < passes; ++p) {
             const int bp = p == 0 ? b1 : b2;
-            const double ipt = bp >= 10 && bp <= 11 ? kIptScatterRing : bp <= 9 ? kIptScatterRegion : kIptScatterWide;
+            const double ipt = bp >= 10 && bp <= 11 ? kIptScatterRing
+                               : bp <= 7               ? kIptScatterRegionLow
+                               : bp <= 9               ? kIptScatterRegion
+                                                       : kIptScatterWide;
             // a first pass at <= 2^11 digits is two launches per relation (histogram
             // and scatter place the runs themselves), any other pass eight
             s[0] += std::max(t * n / b, n * kIptHist / ir) + (p == 0 && bp <= 11 ? 2 * 2 : 2 * 8) * kLaunchS;

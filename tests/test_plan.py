@@ -57,10 +57,16 @@ def test_forced_fields_are_honoured(hjm):
     p = plan(hjm, 1 << 24, 1 << 28, algo=hjm.HJ_ALGO_PHJ, radix_bits=14, passes=2)
     assert (p["algo"], p["radix_bits"], p["passes"]) == (hjm.HJ_ALGO_PHJ, 14, 2)
     assert plan(hjm, 1 << 24, 1 << 28, algo=hjm.HJ_ALGO_SHJ)["algo"] == hjm.HJ_ALGO_SHJ
-    # two passes cost more than one at the same fan-out (twice the partition traffic)
+    # at a fan-out one ring pass reaches, two passes cost more (twice the partition
+    # traffic); at 2^12, where one pass needs the wide scatter, two 2^6 passes of the
+    # region scatter measured slightly faster (5.29 against 5.36 ms), and the model
+    # puts them within 20 % of each other
+    one = plan(hjm, 1 << 24, 1 << 28, algo=hjm.HJ_ALGO_PHJ, radix_bits=11, passes=1)
+    two = plan(hjm, 1 << 24, 1 << 28, algo=hjm.HJ_ALGO_PHJ, radix_bits=11, passes=2)
+    assert two["predicted_ms"] > one["predicted_ms"]
     one = plan(hjm, 1 << 24, 1 << 28, algo=hjm.HJ_ALGO_PHJ, radix_bits=12, passes=1)
     two = plan(hjm, 1 << 24, 1 << 28, algo=hjm.HJ_ALGO_PHJ, radix_bits=12, passes=2)
-    assert two["predicted_ms"] > one["predicted_ms"]
+    assert abs(two["predicted_ms"] - one["predicted_ms"]) < 0.2 * one["predicted_ms"]
 
 
 def test_count_modes_drop_the_output_bytes(hjm):
