@@ -85,10 +85,11 @@ def test_shj_unique_keys_full_size(hjm, ctx):
     assert res.algo == hjm.HJ_ALGO_SHJ
 
 
-@pytest.mark.parametrize("bits,passes", [(1, 1), (5, 1), (8, 1), (11, 1), (12, 1), (2, 2), (9, 2), (14, 2), (21, 2),
-                                         (22, 2)])
+@pytest.mark.parametrize("bits,passes", [(1, 1), (5, 1), (8, 1), (11, 1), (12, 1), (2, 2), (9, 2), (12, 2), (13, 2),
+                                         (14, 2), (21, 2), (22, 2)])
 def test_phj_half_match_scaled(hjm, ctx, bits, passes):
-    # (11 bits in one pass is the plan the tuner picks at full size, and (21, 2) /
+    # (11 bits in one pass is the plan the tuner picks at full size, (12, 2) the
+    # model's plan for twice that build side, and (21, 2) /
     # (22, 2) put 11-bit passes first / in both passes: the ring scatter at its
     # chunk and segment paths.)
     # PHJ on the |R| = 2^24, |S| = 2^28 workload scaled by 2^-8 (ragged sizes):

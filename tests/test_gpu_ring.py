@@ -7,7 +7,8 @@ batch whose group partitions on 11 bits (the per-segment input path), and its
 bounded wait made to run out on purpose (a short limit; the kernel returns and the
 host reports HJ_E_TIMEOUT, no GPU fault).  hj_debug_scatter forces the ring or the
 region scatter, and both kernels are checked at every width and fan-out the ring
-is built for, on ragged sizes and on crowded digits.  Join results are integers: every comparison is
+is built for, on ragged sizes and on crowded digits; the region scatter is also
+checked at the low fan-outs where it keeps up to 256 slots per digit.  Join results are integers: every comparison is
 exact."""
 import numpy as np
 import pytest
@@ -116,6 +117,31 @@ def test_ring_with_crowded_digits_at_every_fanout(hjm, width, bits):
     with hjm.Context(0) as c:
         assert lib.hj_debug_scatter(c.handle, hjm.HJ_SCATTER_RING) == hjm.HJ_OK
         _check(hjm, c, _view(R), _view(S), algo=hjm.HJ_ALGO_PHJ, radix_bits=bits, passes=1)
+
+
+REGION_FANOUTS = [(4, 5), (4, 6), (4, 7), (4, 8), (8, 5), (8, 6), (8, 7)]
+
+
+@pytest.mark.parametrize("crowded", [False, True])
+@pytest.mark.parametrize("width,bits", REGION_FANOUTS)
+def test_region_scatter_at_low_fanouts(hjm, ctx, width, bits, crowded):
+    # the region scatter where its slots per digit are many (up to 256): ragged
+    # uniform keys, whose digits mostly fit their slots, and keys of two digits,
+    # which overflow them on every tile (far-end path); padded passes only run
+    # inside joins, so the join result is what is compared
+    dt = np.uint32 if width == 4 else np.uint64
+    rng = np.random.default_rng(47 + bits + width)
+    if crowded:
+        keys = _keys_of_digits((0, (1 << bits) - 2), 1 << 18, bits, dt)
+        assert len(keys) > 1000
+        rk = rng.permutation(keys)[: min(len(keys), 20_000)]
+        sk = rng.choice(keys, 300_007).astype(dt)
+    else:
+        rk = rng.permutation(np.arange(1, 100_004, dtype=dt))
+        sk = rng.integers(1, 200_008, 600_011).astype(dt)
+    R = np.stack([rk, np.arange(len(rk), dtype=dt)], 1)
+    S = np.stack([sk, np.arange(len(sk), dtype=dt)], 1)
+    _check(hjm, ctx, _view(R), _view(S), algo=hjm.HJ_ALGO_PHJ, radix_bits=bits, passes=1)
 
 
 @pytest.mark.parametrize("ns", [200_003, 1_000_001])
