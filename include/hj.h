@@ -211,16 +211,21 @@ hj_status hj_tune_clear(hj_ctx *ctx);
 hj_status hj_join_host(hj_ctx *ctx, const hj_rel *R_host, const hj_rel *S_host, const hj_opts *opts,
                        void *pairs_host, uint64_t pairs_host_cap, hj_result *out);
 
-/* Join of relations in HOST memory that need not fit the device -- the paper's
- * larger-than-buffer join (App. A): each relation is streamed to the device in
- * chunks, split there on hash bits [20, 20 + bt) (bt <= 8, chosen so that every
- * partition pair of a uniform split fits) and copied back into page-locked host
- * partitions; then every partition pair is gathered onto the device and joined by
- * the PHJ (whose digits use hash bits below 20), its pairs copied into
- * `pairs_host`.  A pair whose S side is too large next to its R partition (skew)
- * is joined in S groups.  The device memory used stays within `device_bytes` (0:
- * 40% of free memory); when everything fits at once this is hj_join_host.  `out`
- * receives count and checksums (out->radix_bits = bt, out->pairs = NULL); the
+/* Join of relations in HOST memory that need not fit the device.  When R,
+ * partitioned, fits `device_bytes` beside two S chunks of at least 2^20 tuples in
+ * flight (and R's partitions fit shared memory after one pass), R is copied and
+ * partitioned once and S streamed past it in chunks, as hj_join_host does
+ * (out->passes = 1, out->radix_bits = the PHJ's bits).  Otherwise the paper's
+ * larger-than-buffer join (App. A; out->passes = 0): each relation is streamed
+ * to the device in chunks, split there on hash bits [20, 20 + bt) (bt <= 8,
+ * chosen so that every partition pair of a uniform split fits) and copied back
+ * into page-locked host partitions; then every partition pair is gathered onto
+ * the device and joined by the PHJ (whose digits use hash bits below 20), its
+ * pairs copied into `pairs_host`.  A pair whose S side is too large next to its R
+ * partition (skew) is joined in S groups.  The device memory used is sized to
+ * `device_bytes` (0: 40% of free memory); when everything fits at once this is
+ * hj_join_host.  `out` receives count and checksums (out->radix_bits = bt for the
+ * split, out->pairs = NULL); the
  * pairs land in `pairs_host` (room for pairs_host_cap pairs; HJ_E_OVERFLOW with
  * the full count if too small).  HJ_E_INVALID if device_bytes is below twice
  * the fixed workspace of one join (64 MiB, plus 2^20 pairs when materialising);
@@ -446,6 +451,19 @@ hj_status hj_debug_wait_limit(hj_ctx *ctx, uint64_t n);
 #define HJ_SCATTER_REGION 1
 #define HJ_SCATTER_RING 2
 hj_status hj_debug_scatter(hj_ctx *ctx, int kind);
+/* Test and measurement hook: hj_join_host_large's plan.  HJ_OUTCORE_AUTO (the
+ * default) keeps R on the device and streams S past it when that fits
+ * device_bytes, else splits both relations (App. A); HJ_OUTCORE_SPLIT always
+ * splits.  Results are identical either way.  HJ_E_INVALID for a NULL context or
+ * another value. */
+#define HJ_OUTCORE_AUTO 0
+#define HJ_OUTCORE_SPLIT 1
+hj_status hj_debug_outcore(hj_ctx *ctx, int mode);
+/* Test hook: the most device bytes the context held at once (its own buffers, as
+ * hj_debug_bytes_in_use counts them) since it was created or since the last call
+ * with reset != 0, which then restarts the count from the bytes held now.  0 for
+ * a NULL context. */
+uint64_t hj_debug_peak_bytes(hj_ctx *ctx, int reset);
 
 #ifdef __cplusplus
 }

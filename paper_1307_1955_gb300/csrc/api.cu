@@ -474,7 +474,7 @@ struct PipeSet {
 };
 
 hj_status join_host_pipelined(hj_ctx *c, const hj_rel *Rh, const hj_rel *Sh, const hj_opts &o, int bits,
-                              void *pairs_host, uint64_t pairs_host_cap, hj_result *res) {
+                              uint64_t chunk_rows, void *pairs_host, uint64_t pairs_host_cap, hj_result *res) {
     const int W = Rh->width;
     const uint64_t tb = tuple_bytes(W), NP = 1ull << bits;
     const bool mat = o.mode == HJ_MATERIALIZE;
@@ -541,7 +541,7 @@ hj_status join_host_pipelined(hj_ctx *c, const hj_rel *Rh, const hj_rel *Sh, con
             ps.computed = c->pipe_ev[i][1];
             ps.drained = c->pipe_ev[i][2];
             ps.h = (hj_counters *)c->pipe_h + i;
-            HJ_TRY(ps.dS.alloc(kHostChunk * tb + 64));
+            HJ_TRY(ps.dS.alloc(chunk_rows * tb + 64));
         }
         // R: copied and partitioned once
         HJ_TRY(dR.alloc(Rh->n * tb + 64));
@@ -549,12 +549,12 @@ hj_status join_host_pipelined(hj_ctx *c, const hj_rel *Rh, const hj_rel *Sh, con
         hj_rel R = *Rh;
         R.tuples = dR.p;
         HJ_TRY(partition_rel(c, &R, bits, 0, 1, Rp, roff, &r_rows));
-        const uint64_t nchunks = (Sh->n + kHostChunk - 1) / kHostChunk;
+        const uint64_t nchunks = (Sh->n + chunk_rows - 1) / chunk_rows;
         const uint64_t warps = partition_join_warps(c);
         for (uint64_t k = 0; k < nchunks; ++k) {
             PipeSet &ps = *sets[k & 1];
             if (ps.chunk != ~0ull && !ps.taken) HJ_TRY(drain(ps));
-            const uint64_t r0 = k * kHostChunk, n = std::min(kHostChunk, Sh->n - r0);
+            const uint64_t r0 = k * chunk_rows, n = std::min(chunk_rows, Sh->n - r0);
             // the set's S buffer is free once chunk k - 2's join is done
             HJ_CUDA(c, cudaStreamWaitEvent(cs, ps.computed, 0));
             HJ_CUDA(c, cudaMemcpyAsync(ps.dS.p, (const char *)Sh->tuples + r0 * tb, n * tb, cudaMemcpyHostToDevice,
@@ -595,7 +595,7 @@ hj_status join_host_pipelined(hj_ctx *c, const hj_rel *Rh, const hj_rel *Sh, con
         HJ_CUDA(c, cudaStreamSynchronize(os));
         // chunks that did not fit their pair buffer: on their own, exact capacity
         for (uint64_t k : redo) {
-            const uint64_t r0 = k * kHostChunk, n = std::min(kHostChunk, Sh->n - r0);
+            const uint64_t r0 = k * chunk_rows, n = std::min(chunk_rows, Sh->n - r0);
             DevBuf dS(c);
             HJ_TRY(dS.alloc(n * tb + 64));
             HJ_CUDA(c, cudaMemcpyAsync(dS.p, (const char *)Sh->tuples + r0 * tb, n * tb, cudaMemcpyHostToDevice,
@@ -812,6 +812,50 @@ hj_status join_coproc(hj_ctx *c, const hj_rel *R, const hj_rel *S, const hj_opts
 
 }  // namespace
 
+namespace hj {
+
+// Device bytes of join_host_pipelined with chunks of `chunk_rows` S rows at `bits`
+// radix bits: R and its padded partitioned copy, two S chunk buffers and (pairs)
+// two pair buffers with one chunk of slack per emitting warp, one chunk's padded
+// partitioned copy, and 64 MiB for counters, histograms, task lists and records.
+uint64_t host_streamed_bytes(hj_ctx *c, int width, bool mat, uint64_t nR, uint64_t chunk_rows, int bits) {
+    const uint64_t tb = tuple_bytes(width);
+    uint64_t b = nR * tb + partition_out_rows(c, width, nR, 1, bits, 1) * tb + ((1ull << bits) + 1) * 8;
+    b += 2 * (chunk_rows * tb + 64);
+    if (mat) b += 2 * (chunk_rows + partition_join_warps(c) * kChunkPairs) * tb;
+    b += partition_out_rows(c, width, chunk_rows, 1, bits, 1) * tb;
+    return b + (64ull << 20);
+}
+
+bool host_streamed_plan(hj_ctx *c, const hj_rel *Rh, const hj_rel *Sh, const hj_opts &o, uint64_t device_bytes,
+                        uint64_t *chunk_rows, int *bits) {
+    if (Rh->n == 0 || Rh->n >= 0xFFFFFFFFull) return false;
+    if (!c->model_ready) {
+        c->model = cost_model_for(c->device);
+        c->model_ready = true;
+    }
+    const bool mat = o.mode == HJ_MATERIALIZE;
+    for (uint64_t ch = kHostChunk; ch >= (1ull << 20); ch >>= 1) {
+        const std::vector<PlanCand> pcs =
+            plan_candidates(c->model, Rh->width, !mat, mat, Rh->n, std::min<uint64_t>(Sh->n, ch), HJ_ALGO_PHJ, 0, 1);
+        if (pcs.empty() || pcs[0].passes != 1) return false;  // R needs two passes: no streamed plan
+        if (host_streamed_bytes(c, Rh->width, mat, Rh->n, ch, pcs[0].bits) <= device_bytes) {
+            *chunk_rows = ch;
+            *bits = pcs[0].bits;
+            return true;
+        }
+    }
+    return false;
+}
+
+hj_status host_streamed_join(hj_ctx *c, const hj_rel *Rh, const hj_rel *Sh, const hj_opts &o, int bits,
+                             uint64_t chunk_rows, void *pairs_host, uint64_t pairs_host_cap, hj_result *res) {
+    *res = hj_result{};
+    return join_host_pipelined(c, Rh, Sh, o, bits, chunk_rows, pairs_host, pairs_host_cap, res);
+}
+
+}  // namespace hj
+
 extern "C" {
 
 hj_status hj_join_coproc(hj_ctx *c, const hj_rel *R, const hj_rel *S, const hj_opts *opts, double cpu_share,
@@ -974,7 +1018,7 @@ hj_status hj_join_host(hj_ctx *c, const hj_rel *Rh, const hj_rel *Sh, const hj_o
         if (pipe && Sh->n >= 2 * kHostChunk && Rh->n < 0xFFFFFFFFull && o.mode >= HJ_COUNT &&
             o.mode <= HJ_MATERIALIZE) {
             *res = hj_result{};
-            return join_host_pipelined(c, Rh, Sh, o, bits, pairs_host, pairs_host_cap, res);
+            return join_host_pipelined(c, Rh, Sh, o, bits, kHostChunk, pairs_host, pairs_host_cap, res);
         }
     }
     DevBuf dR(c), dS(c);

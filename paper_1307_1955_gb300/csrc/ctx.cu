@@ -340,6 +340,22 @@ hj_status hj_debug_fail_alloc(hj_ctx *c, int64_t n) {
 
 uint64_t hj_debug_bytes_in_use(const hj_ctx *c) { return c ? c->in_use : 0; }
 
+/* Test hook: the most device bytes held at once since creation or the last reset;
+ * a reset restarts the count from the bytes held now. */
+uint64_t hj_debug_peak_bytes(hj_ctx *c, int reset) {
+    if (!c) return 0;
+    const uint64_t p = c->peak;
+    if (reset) c->peak = c->in_use;
+    return p;
+}
+
+/* Test and measurement hook: hj_join_host_large's plan (HJ_OUTCORE_*). */
+hj_status hj_debug_outcore(hj_ctx *c, int mode) {
+    if (!c || mode < HJ_OUTCORE_AUTO || mode > HJ_OUTCORE_SPLIT) return HJ_E_INVALID;
+    c->outcore_mode = mode;
+    return HJ_OK;
+}
+
 /* Test hook: limit of the ring scatter's bounded wait (flush passes before its
  * flush warps give up and report HJ_E_TIMEOUT); 0 restores the default. */
 hj_status hj_debug_wait_limit(hj_ctx *c, uint64_t n) {

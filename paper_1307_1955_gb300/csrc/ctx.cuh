@@ -93,6 +93,7 @@ struct hj_ctx {
     int64_t fail_alloc_after = -1;  // fail the N-th allocation from now (0 = next)
     uint64_t wait_limit = 0;        // bounded device waits: passes / polls before giving up (0 = default)
     int scatter_kind = 0;           // HJ_SCATTER_*: padded-pass scatter at 2^9 .. 2^11 digits
+    int outcore_mode = 0;           // HJ_OUTCORE_*: hj_join_host_large's plan
 };
 
 struct hj_table {

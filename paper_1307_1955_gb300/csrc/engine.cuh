@@ -98,6 +98,17 @@ hj_status partition_join(hj_ctx *c, int width, int agg, const PartTask *tasks, u
 uint64_t partition_join_warps(hj_ctx *c);
 uint64_t partition_join_ctas(hj_ctx *c, int width, int agg, uint64_t expect_r);
 
+// ------------------------------------------------------------ api.cu (host joins)
+// hj_join_host_large with R kept on the device: the device bytes of the streamed
+// join (R partitioned once, S in chunks of chunk_rows through two buffer sets),
+// the largest chunk (2^24 .. 2^20 rows) and one-pass radix bits that fit
+// device_bytes (false if none does, or R needs two passes), and the join itself.
+uint64_t host_streamed_bytes(hj_ctx *c, int width, bool mat, uint64_t nR, uint64_t chunk_rows, int bits);
+bool host_streamed_plan(hj_ctx *c, const hj_rel *Rh, const hj_rel *Sh, const hj_opts &o, uint64_t device_bytes,
+                        uint64_t *chunk_rows, int *bits);
+hj_status host_streamed_join(hj_ctx *c, const hj_rel *Rh, const hj_rel *Sh, const hj_opts &o, int bits,
+                             uint64_t chunk_rows, void *pairs_host, uint64_t pairs_host_cap, hj_result *res);
+
 struct PairSink;
 // Tasks listed in `list_dev` (nov task indices) whose table did not fit in shared
 // memory: SHJ with a global table per task, into the task's join slot (slots_host

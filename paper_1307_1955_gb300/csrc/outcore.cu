@@ -3,6 +3,11 @@
 // (App. A: partition each relation chunk by chunk through a bounded buffer, keep
 // the partitions, then join every partition pair).
 //
+// When R alone fits the budget with room for two S chunks in flight, the split is
+// skipped: R is partitioned once on the device and S streamed past it in chunks
+// (host_streamed_join, api.cu), so that each tuple crosses the host link once
+// instead of three times.  Otherwise:
+//
 //   1. partition: each relation is streamed to the device in chunks that fit the
 //      budget; every chunk is split on hash bits [kTopShift, kTopShift + bt) by the
 //      partition pass and copied back whole, with its partition offsets, into a
@@ -216,6 +221,15 @@ extern "C" hj_status hj_join_host_large(hj_ctx *c, const hj_rel *Rh, const hj_re
     // everything fits: one join
     if (join_bytes(Rh->n, Sh->n, tb, mat) <= device_bytes)
         return hj_join_host(c, Rh, Sh, &o, pairs_host, pairs_host_cap, out);
+    // R fits with room to stream S past it: R is partitioned once and kept, S goes
+    // through in chunks (every tuple crosses the link once, where the split below
+    // takes three crossings)
+    {
+        uint64_t sc = 0;
+        int sb = 0;
+        if (c->outcore_mode != HJ_OUTCORE_SPLIT && host_streamed_plan(c, Rh, Sh, o, device_bytes, &sc, &sb))
+            return host_streamed_join(c, Rh, Sh, o, sb, sc, pairs_host, pairs_host_cap, out);
+    }
     // top-level fan-out: partition pairs of a uniform split fit with room for skew
     int bt = 1;
     while (bt < kTopMaxBits && 3 * pipe_bytes(Rh->n >> bt, Sh->n >> bt, tb, mat) / 2 > device_bytes) ++bt;

@@ -20,6 +20,7 @@ HJ_ALGO_AUTO, HJ_ALGO_SHJ, HJ_ALGO_PHJ = 0, 1, 2
 HJ_FLAG_CHECKSUM = 1
 HJ_FLAG_GRAPH = 2
 HJ_SCATTER_AUTO, HJ_SCATTER_REGION, HJ_SCATTER_RING = 0, 1, 2
+HJ_OUTCORE_AUTO, HJ_OUTCORE_SPLIT = 0, 1
 
 _STATUS = {0: "HJ_OK", 1: "HJ_E_INVALID", 2: "HJ_E_NOMEM", 3: "HJ_E_OVERFLOW", 4: "HJ_E_CUDA",
            5: "HJ_E_TIMEOUT", 6: "HJ_E_UNSUPPORTED", 7: "HJ_E_PENDING"}
@@ -118,6 +119,8 @@ def load_library(path: str = LIB_PATH):
         "hj_debug_bytes_in_use": (U64, [V]),
         "hj_debug_wait_limit": (I32, [V, U64]),
         "hj_debug_scatter": (I32, [V, ctypes.c_int]),
+        "hj_debug_outcore": (I32, [V, ctypes.c_int]),
+        "hj_debug_peak_bytes": (U64, [V, ctypes.c_int]),
         "hj_split": (I32, [V, P(hj_rel), ctypes.c_int, V, P(U64)]),
         "hj_join_coproc": (I32, [V, P(hj_rel), P(hj_rel), P(hj_opts), ctypes.c_double, ctypes.c_int, P(hj_result),
                                  P(ctypes.c_double)]),

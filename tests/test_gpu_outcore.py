@@ -37,34 +37,66 @@ def _sorted(p):
     return p[np.lexsort((p[:, 1], p[:, 0]))] if len(p) else p.reshape(0, 2)
 
 
+@pytest.fixture(scope="module")
+def lib(hjm):
+    return hjm.load_library()
+
+
+@pytest.mark.parametrize("split", [False, True])
 @pytest.mark.parametrize("budget_mb", [160, 240, 4096])
-def test_large_join_through_a_small_budget_matches_oracle(hjm, ctx, budget_mb):
+def test_large_join_through_a_small_budget_matches_oracle(hjm, lib, budget_mb, split):
+    # 160 MB: R does not fit beside two S chunks and their pair buffers, so the
+    # relations are split (App. A); 240 MB: R stays on the device and S streams past
+    # it in 2^20-row chunks, unless the split is forced; 4096 MB: one join.  The
+    # device bytes the context holds never pass the budget.
     R, S = W.unique_and_uniform(1 << 20, 1 << 23, 1 << 21, W.DEFAULT_SEED, "cpu", ids=(40,))
     r, s = W.to_numpy_u(R), W.to_numpy_u(S)
     want = oracle.sorted_pairs(*oracle.hash_join(r, s))
     cnt, c0, c1 = oracle.join_aggregate(r, s)
     out = torch.empty((len(want) + 16, 2), dtype=torch.int32)
-    res = hjm.hj_join_host_large(ctx, R, S, out, device_bytes=budget_mb << 20, checksum=True)
-    assert (res.count, *res.checksum) == (cnt, c0, c1)
-    got = out[:res.count].numpy().view(np.uint32).astype(np.uint64)
-    assert np.array_equal(_sorted(got), want)
-    if budget_mb < 4096:
-        assert res.radix_bits >= 1  # the top-level split ran
-    cr = hjm.hj_join_host_large(ctx, R, S, None, device_bytes=budget_mb << 20, mode=hjm.HJ_COUNT_CHECKSUM)
-    assert (cr.count, *cr.checksum) == (cnt, c0, c1)
+    with hjm.Context(0) as c:
+        assert lib.hj_debug_outcore(c.handle, hjm.HJ_OUTCORE_SPLIT if split else hjm.HJ_OUTCORE_AUTO) == hjm.HJ_OK
+        lib.hj_debug_peak_bytes(c.handle, 1)
+        res = hjm.hj_join_host_large(c, R, S, out, device_bytes=budget_mb << 20, checksum=True)
+        peak = lib.hj_debug_peak_bytes(c.handle, 1)
+        assert (res.count, *res.checksum) == (cnt, c0, c1)
+        got = out[:res.count].numpy().view(np.uint32).astype(np.uint64)
+        assert np.array_equal(_sorted(got), want)
+        if budget_mb == 240 and not split:
+            assert res.passes == 1  # R resident, S streamed
+        elif budget_mb < 4096:
+            assert res.passes == 0 and res.radix_bits >= 1  # the top-level split ran
+        assert peak <= budget_mb << 20, (peak, budget_mb)
+        cr = hjm.hj_join_host_large(c, R, S, None, device_bytes=budget_mb << 20, mode=hjm.HJ_COUNT_CHECKSUM)
+        assert (cr.count, *cr.checksum) == (cnt, c0, c1)
+        assert lib.hj_debug_peak_bytes(c.handle, 0) <= budget_mb << 20
 
 
-def test_large_join_skewed_u64_groups_of_s(hjm, ctx):
-    # A hot S key makes one partition's S side far larger than the budget allows next
-    # to its R partition: it is joined in S groups.
-    # (|S| = 2^25 with S theta 1.2: the top key alone is about 6e6 tuples, more than
-    # the 192 MB budget holds next to its R partition.)
+def test_outcore_hook_rejects_bad_modes(hjm, lib):
+    with hjm.Context(0) as c:
+        for m in (-1, 2):
+            assert lib.hj_debug_outcore(c.handle, m) == 1  # HJ_E_INVALID
+    assert lib.hj_debug_outcore(None, 0) == 1
+
+
+@pytest.mark.parametrize("split", [True, False])
+def test_large_join_skewed_u64_groups_of_s(hjm, lib, split):
+    # Split: a hot S key makes one partition's S side far larger than the budget
+    # allows next to its R partition, so it is joined in S groups.  (|S| = 2^25 with
+    # S theta 1.2: the top key alone is about 6e6 tuples, more than the 192 MB budget
+    # holds next to its R partition.)  Not split: R stays on the device and the hot
+    # key's tuples pass in S chunks.
     R, S = W.zipf_pair(1 << 16, 1 << 25, 0.5, 1.2, 1 << 14, W.DEFAULT_SEED, "cpu", ids=(41,))
     r, s = W.to_numpy_u(R), W.to_numpy_u(S)
     cnt, c0, c1 = oracle.join_aggregate(r, s)
-    res = hjm.hj_join_host_large(ctx, R, S, None, device_bytes=192 << 20, mode=hjm.HJ_COUNT_CHECKSUM)
-    assert (res.count, *res.checksum) == (cnt, c0, c1)
-    assert res.radix_bits >= 4
+    with hjm.Context(0) as c:
+        assert lib.hj_debug_outcore(c.handle, hjm.HJ_OUTCORE_SPLIT if split else hjm.HJ_OUTCORE_AUTO) == hjm.HJ_OK
+        res = hjm.hj_join_host_large(c, R, S, None, device_bytes=192 << 20, mode=hjm.HJ_COUNT_CHECKSUM)
+        assert (res.count, *res.checksum) == (cnt, c0, c1)
+        if split:
+            assert res.passes == 0 and res.radix_bits >= 4
+        else:
+            assert res.passes == 1
 
 
 def test_large_join_overflow_reports_the_count(hjm, ctx):
