@@ -2,6 +2,7 @@
 // SHJ / PHJ drivers that sequence the kernels of join.cu and partition.cu.
 #include <algorithm>
 #include <chrono>
+#include <cstddef>
 #include <cmath>
 #include <memory>
 #include <thread>
@@ -119,8 +120,18 @@ hj_status gather_rows(hj_ctx *c, int W, const std::vector<GatherRange> &ranges, 
 
 }  // namespace fallback
 
+FallbackGroup::~FallbackGroup() { table_destroy(c, t); }
+
+hj_status fallback_reprobe(hj_ctx *c, bool chk, const FallbackRedo &redo, const JoinSlot &slot) {
+    for (const auto &g : redo.groups)
+        HJ_TRY(keylist_probe(c, g->t, g->S, g->ns, g->pf, slot.pairs, slot.pcap, slot.ctr, chk));
+    return HJ_OK;
+}
+
 hj_status oversize_fallback(hj_ctx *c, int W, bool agg, bool chk, const PartTask *tasks, const uint32_t *list_dev,
-                            uint64_t nov, const std::vector<JoinSlot> &slots_host) {
+                            uint64_t nov, const std::vector<JoinSlot> &slots_host, FallbackRedo *redo) {
+    hj_counters prev{};
+    if (redo) prev = *c->h_ctr;  // the caller read the counters last
     std::vector<PartTask> tk(nov);
     {
         DevBuf picked(c);
@@ -183,6 +194,24 @@ hj_status oversize_fallback(hj_ctx *c, int W, bool agg, bool chk, const PartTask
         if (!agg) {
             HJ_TRY(keylist_build(c, W, Rt, nr, pf, &tg.t));
             HJ_TRY(keylist_probe(c, tg.t, St, ns, pf, js.pairs, js.pcap, js.ctr, chk));
+            if (redo) {
+                HJ_TRY(read_counters(c));
+                if (!redo->crossed && c->h_ctr->count > js.pcap) {
+                    redo->crossed = true;
+                    redo->from = prev;
+                }
+                prev = *c->h_ctr;
+                if (redo->crossed) {  // this group's pairs are written again after the buffer grows
+                    auto g = std::make_unique<FallbackGroup>(c);
+                    g->t = tg.t;
+                    tg.t = nullptr;
+                    g->Sg.p = Sg.release();
+                    g->S = St;
+                    g->ns = ns;
+                    g->pf = pf;
+                    redo->groups.push_back(std::move(g));
+                }
+            }
             continue;
         }
         HJ_TRY(table_create(c, W, agg, nr, &tg.t));
@@ -404,10 +433,28 @@ hj_status run_partition_join(hj_ctx *c, const hj_rel *R, const hj_rel *S, const 
     if (nov == 0) return HJ_OK;
     // partitions whose table did not fit shared memory: global tables, pairs claimed
     // exactly after the compacted ones (counted even past the capacity)
+    const hj_counters before = *c->h_ctr;
     std::vector<JoinSlot> slots_host{JoinSlot{pairs, pcap, c->d_ctr, 0}};
-    HJ_TRY(oversize_fallback(c, W, agg, chk, tasks, oversize, nov, slots_host));
+    // (pairs whose partition join fitted its buffer: the fallback keeps what it
+    // needs to write the pairs that pass the buffer again)
+    const bool keep = mat && before.cursor <= pcap && before.count <= pcap;
+    FallbackRedo redo;
+    HJ_TRY(oversize_fallback(c, W, agg, chk, tasks, oversize, nov, slots_host, keep ? &redo : nullptr));
     HJ_TRY(read_counters(c));
     if (c->h_ctr->status & kStatusTableFull) return set_err(c, HJ_E_CUDA, "hash table unexpectedly full");
+    if (keep && redo.crossed && c->h_ctr->count > pcap) {
+        // only fallback pairs passed the buffer (heavy keys in oversize partitions):
+        // the buffer grows to the exact count, keeping every pair written before the
+        // first group that passed it, and that group and the later ones probe again
+        // from the counters they started from (no partition join, no table rebuilt)
+        HJ_TRY(sink->grow(c->h_ctr->count, redo.from.count));
+        HJ_CUDA(c, cudaMemcpyAsync(c->d_ctr, &redo.from, offsetof(hj_counters, work), cudaMemcpyHostToDevice,
+                                   c->stream));
+        HJ_CUDA(c, cudaStreamSynchronize(c->stream));  // (`redo` lives on this stack)
+        HJ_TRY(fallback_reprobe(c, chk, redo, JoinSlot{sink->pairs.p, sink->pcap, c->d_ctr, 0}));
+        HJ_TRY(read_counters(c));
+        if (c->h_ctr->status & kStatusTableFull) return set_err(c, HJ_E_CUDA, "hash table unexpectedly full");
+    }
     return HJ_OK;
 }
 

@@ -114,8 +114,29 @@ struct PairSink;
 // memory: SHJ with a global table per task, into the task's join slot (slots_host
 // mirrors the device slots).  Pairs are claimed exactly at the slot's count, after
 // the pairs already there.
+// With `redo` (one join writing pairs into the context's counters), the counters
+// are read after each task group's probe; from the first group whose pairs passed
+// the slot's capacity on, each group's key-list table and S rows are kept in
+// `redo`, with the counters from before that group, so that fallback_reprobe can
+// write those groups' pairs again into a larger buffer without rebuilding.
+struct FallbackGroup {
+    hj_ctx *c;
+    hj_table *t = nullptr;
+    DevBuf Sg;                  // gathered S rows (empty when S is probed in place)
+    const void *S = nullptr;
+    uint64_t ns = 0;
+    PartFilter pf{0, 0, 0, 0};
+    explicit FallbackGroup(hj_ctx *ctx) : c(ctx), Sg(ctx) {}
+    ~FallbackGroup();
+};
+struct FallbackRedo {
+    bool crossed = false;
+    hj_counters from{};  // counters before the first group that passed the capacity
+    std::vector<std::unique_ptr<FallbackGroup>> groups;
+};
 hj_status oversize_fallback(hj_ctx *c, int W, bool agg, bool chk, const PartTask *tasks, const uint32_t *list_dev,
-                            uint64_t nov, const std::vector<JoinSlot> &slots_host);
+                            uint64_t nov, const std::vector<JoinSlot> &slots_host, FallbackRedo *redo = nullptr);
+hj_status fallback_reprobe(hj_ctx *c, bool chk, const FallbackRedo &redo, const JoinSlot &slot);
 
 // ------------------------------------------------------------ partition.cu
 // One radix-partition pass over nseg independent segments of `in` (segment s is
@@ -150,6 +171,7 @@ struct PairSink {
     std::vector<uint64_t> caps;
     PairSink(hj_ctx *ctx, int w) : c(ctx), width(w), pairs(ctx) {}
     hj_status reset(uint64_t cap_pairs);                 // (re)allocate the buffer, drop records
+    hj_status grow(uint64_t cap_pairs, uint64_t keep);  // larger buffer holding the first `keep` pairs
     hj_status new_area(uint64_t warps, RecArea *ra);     // record area for one launch
     // Device-planned compaction of the single record area, stream-ordered after the
     // join: no host round trip.  Does nothing when the cursor ran past the capacity.

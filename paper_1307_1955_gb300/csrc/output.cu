@@ -230,6 +230,17 @@ hj_status PairSink::reset(uint64_t cap_pairs) {
     return pairs.alloc(pcap * 2ull * width);
 }
 
+hj_status PairSink::grow(uint64_t cap_pairs, uint64_t keep) {
+    DevBuf nb(c);
+    HJ_TRY(nb.alloc(cap_pairs * 2ull * width));
+    if (keep)
+        HJ_CUDA(c, cudaMemcpyAsync(nb.p, pairs.p, keep * 2ull * width, cudaMemcpyDeviceToDevice, c->stream));
+    pairs.reset();
+    pairs.p = nb.release();
+    pcap = cap_pairs;
+    return HJ_OK;
+}
+
 hj_status PairSink::new_area(uint64_t warps, RecArea *ra) {
     auto b = std::make_unique<DevBuf>(c);
     HJ_TRY(b->alloc(area_bytes(warps)));

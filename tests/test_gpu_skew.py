@@ -63,6 +63,34 @@ def test_heavy_hitter_phj(hjm, ctx, s):
     _check(hjm, ctx, R, S, want, agg, algo=hjm.HJ_ALGO_PHJ, radix_bits=10, passes=2)
 
 
+@pytest.mark.parametrize("width", [4, 8])
+def test_heavy_key_pairs_past_the_first_capacity(hjm, ctx, width):
+    # One key held 40000 times by R and 200 times by S: its partition goes to the
+    # key-list fallback, whose 8e6 pairs pass the first pair buffer (|S| plus a chunk
+    # per warp) while the partition join's own pairs fit.  The buffer then grows to
+    # the exact count and only the fallback runs again (its capacity is the count).
+    dt = np.uint32 if width == 4 else np.uint64
+    rng = np.random.default_rng(66 + width)
+    heavy = 7
+    rk = np.concatenate([np.full(40_000, heavy), rng.permutation(np.arange(100, 20_100))]).astype(dt)
+    rk = rk[rng.permutation(len(rk))]
+    sk = np.concatenate([np.full(200, heavy), rng.integers(100, 40_100, 100_003)]).astype(dt)
+    sk = sk[rng.permutation(len(sk))]
+    R = np.stack([rk, np.arange(len(rk), dtype=dt)], 1)
+    S = np.stack([sk, np.arange(len(sk), dtype=dt)], 1)
+    view = np.int32 if width == 4 else np.int64
+    Rg = torch.from_numpy(R.view(view)).to(DEV)
+    Sg = torch.from_numpy(S.view(view)).to(DEV)
+    want, agg = _want(Rg, Sg)
+    assert agg[0] > 8_000_000
+    res = hjm.hj_join(ctx, Rg, Sg, checksum=True, algo=hjm.HJ_ALGO_PHJ, radix_bits=6)
+    assert (res.count, *res.checksum) == agg
+    assert res.pairs_cap == res.count  # grown to the exact count, not re-run whole
+    p = res.pairs_numpy().astype(np.uint64)
+    res.free()
+    assert np.array_equal(oracle.sorted_pairs(p[:, 0], p[:, 1]), want)
+
+
 @pytest.mark.parametrize("s", [0.10, 0.25])
 def test_heavy_hitter_shj_and_build_probe(hjm, ctx, s):
     # SHJ: the pair table's build meets a run of repeated keys and the join takes a
