@@ -183,10 +183,16 @@ hj_status scan_entries(hj_ctx *c, Src src, Dst dst, uint64_t n, uint64_t *total_
 // one atomic per copy on one address would serialise the build).
 __device__ __forceinline__ unsigned lanes_lt() { return (1u << (threadIdx.x & 31)) - 1u; }
 
-// Step 1: every kept key in the table (CAS on the key), its count added.
+constexpr uint64_t kGuessWalk = 64;
+
+// Step 1: every kept key in the table (CAS on the key), its count added.  Each
+// key the CAS inserts counts in *nkeys; once they pass key_limit (a table sized
+// for fewer distinct keys than rows, half full) the warps stop and the host
+// builds again at full size.
 template <int W>
 __global__ void __launch_bounds__(256) kl_count(const void *R, uint64_t n, AggSlot<W> *slots, uint64_t cap,
-                                                TableSide *side, hj_counters *ctr, PartFilter pf) {
+                                                TableSide *side, hj_counters *ctr, PartFilter pf,
+                                                unsigned long long *nkeys, uint64_t key_limit) {
     using U = typename Tup<W>::U;
     constexpr int PV = Tup<W>::kPerVec;
     const unsigned lane = threadIdx.x & 31;
@@ -194,9 +200,14 @@ __global__ void __launch_bounds__(256) kl_count(const void *R, uint64_t n, AggSl
     const uint64_t nwarps = ((uint64_t)gridDim.x * blockDim.x) >> 5;
     const uint64_t nv = (n + PV - 1) / PV;
     for (uint64_t v0 = warp * 32; v0 < nv; v0 += nwarps * 32) {  // warp-uniform: every lane takes part
+        unsigned long long seen = 0;
+        if (lane == 0) seen = *(volatile unsigned long long *)nkeys;
+        if (__shfl_sync(0xffffffffu, seen, 0) > key_limit) break;  // (warp-uniform)
         const uint64_t v = v0 + lane;
         U k[2] = {0, 0}, r[2] = {0, 0};
         if (v < nv) kl_load<W>(R, v, n, k, r);
+        const bool guess = key_limit != ~0ull;
+        unsigned fresh = 0;  // keys this lane inserted (counted per warp, first table only)
 #pragma unroll
         for (int e = 0; e < PV; ++e) {
             const uint64_t h = key_hash<W>(k[e]);
@@ -208,18 +219,30 @@ __global__ void __launch_bounds__(256) kl_count(const void *R, uint64_t n, AggSl
                 atomicAdd(&side->agg_cnt, (unsigned long long)m);
                 continue;
             }
+            // a first, smaller table: nothing more once it is given up, and a walk of
+            // at most kGuessWalk slots (at load <= 1/2 a longer one gives it up too)
+            if (guess && *(volatile unsigned long long *)nkeys > key_limit) continue;
+            const uint64_t walk = guess && cap > kGuessWalk ? kGuessWalk : cap;
             uint64_t b = bucket_of<W>(h, cap);
             bool done = false;
-            for (uint64_t it = 0; it < cap && !done; ++it) {
+            for (uint64_t it = 0; it < walk && !done; ++it) {
                 const U old = cas_key<W>((U *)&slots[b].key, Tup<W>::kAllOnes, k[e]);
                 if (old == Tup<W>::kAllOnes || old == k[e]) {
                     add_cnt(&slots[b].cnt, (decltype(slots[b].cnt))m);
+                    fresh += old == Tup<W>::kAllOnes;
                     done = true;
                 } else if (++b == cap) {
                     b = 0;
                 }
             }
-            if (!done) atomicOr(&ctr->status, (unsigned long long)kStatusTableFull);
+            if (!done) {
+                if (guess) atomicAdd(nkeys, (unsigned long long)cap);  // past the limit: built again at full size
+                else atomicOr(&ctr->status, (unsigned long long)kStatusTableFull);
+            }
+        }
+        if (guess) {  // (the warp is converged again here)
+            const unsigned tot = __reduce_add_sync(0xffffffffu, fresh);
+            if (lane == 0 && tot) atomicAdd(nkeys, (unsigned long long)tot);
         }
     }
 }
@@ -439,27 +462,48 @@ __global__ void __launch_bounds__(256) kl_expand(const Big *big, const unsigned 
 
 }  // namespace
 
+// First table of a key-list build over more than kKeyGuessMin rows: sized for
+// rows / kKeyGuessDiv distinct keys.  A relation whose repeated keys sent it here
+// holds far fewer distinct keys than rows, and the scan of step 2 reads the
+// whole table; one with more distinct keys stops early and is built again at
+// full size.
+constexpr uint64_t kKeyGuessMin = 1ull << 16;
+constexpr uint64_t kKeyGuessDiv = 32;
+
 hj_status keylist_build(hj_ctx *c, int width, const void *R, uint64_t n, PartFilter pf, hj_table **out) {
     *out = nullptr;
-    DevBuf rids(c);
+    DevBuf rids(c), nkeys(c);
+    HJ_TRY(nkeys.alloc(8));
     hj_table *t = nullptr;
-    HJ_TRY(table_create(c, width, 1, n, &t));
     struct Guard {
         hj_ctx *c;
         hj_table *t;
         ~Guard() {
             if (t) table_destroy(c, t);
         }
-    } g{c, t};
-    {
+    } g{c, nullptr};
+    for (uint64_t keys = n > kKeyGuessMin ? std::max(kKeyGuessMin, n / kKeyGuessDiv) : n;;) {
+        HJ_TRY(table_create(c, width, 1, keys, &t));
+        g.t = t;
+        const uint64_t limit = keys < n ? t->cap / 2 : ~0ull;
+        HJ_CUDA(c, cudaMemsetAsync(nkeys.p, 0, 8, c->stream));
         const uint64_t nv = (n + 1) / (width == 4 ? 2 : 1);
         const unsigned grid = (unsigned)std::min<uint64_t>((nv + 255) / 256 + 1, (uint64_t)num_sms(c) * 8);
         if (width == 4)
             HJ_LAUNCH(c, "keylist_count", kl_count<4>, grid, 256, 0, R, n, (AggSlot<4> *)t->slots, t->cap,
-                      (TableSide *)t->side, c->d_ctr, pf);
+                      (TableSide *)t->side, c->d_ctr, pf, nkeys.as<unsigned long long>(), limit);
         else
             HJ_LAUNCH(c, "keylist_count", kl_count<8>, grid, 256, 0, R, n, (AggSlot<8> *)t->slots, t->cap,
-                      (TableSide *)t->side, c->d_ctr, pf);
+                      (TableSide *)t->side, c->d_ctr, pf, nkeys.as<unsigned long long>(), limit);
+        if (keys >= n) break;
+        uint64_t got = 0;
+        HJ_CUDA(c, cudaMemcpyAsync(&got, nkeys.p, 8, cudaMemcpyDeviceToHost, c->stream));
+        HJ_CUDA(c, cudaStreamSynchronize(c->stream));
+        if (got <= limit) break;
+        // more distinct keys than the first table holds: full size
+        table_destroy(c, t);
+        g.t = t = nullptr;
+        keys = n;
     }
     if (width == 4) HJ_TRY(scan_entries(c, AggCnt4{(AggSlot<4> *)t->slots}, AggCnt4{(AggSlot<4> *)t->slots}, t->cap, nullptr));
     else HJ_TRY(scan_entries(c, AggCnt8{(AggSlot<8> *)t->slots}, AggCnt8{(AggSlot<8> *)t->slots}, t->cap, nullptr));

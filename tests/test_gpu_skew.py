@@ -64,6 +64,27 @@ def test_heavy_hitter_phj(hjm, ctx, s):
 
 
 @pytest.mark.parametrize("width", [4, 8])
+@pytest.mark.parametrize("heavy", [0, 100_000])
+def test_keylist_first_table_is_given_up_or_kept(hjm, ctx, width, heavy):
+    # One radix bit: both partitions (about 2^18 R rows each) go to the key-list
+    # fallback, whose first table is sized for a 32nd as many distinct keys as rows.
+    # Distinct keys fill it past half: it is given up and built again at full size.
+    # With 100000 copies of one key the distinct keys fit and it is kept.
+    dt = np.uint32 if width == 4 else np.uint64
+    rng = np.random.default_rng(75 + width)
+    nr = 1 << 19
+    rk = np.concatenate([np.full(heavy, 7), np.arange(100, 100 + nr - heavy)]).astype(dt)
+    rk = rk[rng.permutation(len(rk))]
+    sk = np.concatenate([np.full(5, 7), rng.integers(100, 100 + 2 * nr, (1 << 20) - 5)]).astype(dt)
+    sk = sk[rng.permutation(len(sk))]
+    view = np.int32 if width == 4 else np.int64
+    Rg = torch.from_numpy(np.stack([rk, np.arange(nr, dtype=dt)], 1).view(view)).to(DEV)
+    Sg = torch.from_numpy(np.stack([sk, np.arange(len(sk), dtype=dt)], 1).view(view)).to(DEV)
+    want, agg = _want(Rg, Sg)
+    _check(hjm, ctx, Rg, Sg, want, agg, algo=hjm.HJ_ALGO_PHJ, radix_bits=1)
+
+
+@pytest.mark.parametrize("width", [4, 8])
 def test_heavy_key_pairs_past_the_first_capacity(hjm, ctx, width):
     # One key held 40000 times by R and 200 times by S: its partition goes to the
     # key-list fallback, whose 8e6 pairs pass the first pair buffer (|S| plus a chunk
