@@ -184,30 +184,78 @@ hj_status scan_entries(hj_ctx *c, Src src, Dst dst, uint64_t n, uint64_t *total_
 __device__ __forceinline__ unsigned lanes_lt() { return (1u << (threadIdx.x & 31)) - 1u; }
 
 constexpr uint64_t kGuessWalk = 64;
+// Keys that fill several lanes of a warp group (the heavy hitters that make a
+// partition need a key-list table) are also gathered per tile of a CTA: up to
+// kHot of them in shared memory, each then taking one global atomic per tile
+// instead of one per warp group.
+constexpr int kHot = 8;
 
-// Step 1: every kept key in the table (CAS on the key), its count added.  Each
-// key the CAS inserts counts in *nkeys; once they pass key_limit (a table sized
-// for fewer distinct keys than rows, half full) the warps stop and the host
-// builds again at full size.
+// Entry of key k among the tile's gathered keys (a free one taken), or -1.
+template <int W> __device__ __forceinline__ int hot_entry(typename Tup<W>::U *hk, typename Tup<W>::U k) {
+    using U = typename Tup<W>::U;
+#pragma unroll 1
+    for (int j = 0; j < kHot; ++j) {
+        const U cur = ((volatile U *)hk)[j];
+        if (cur == k) return j;
+        if (cur == Tup<W>::kAllOnes) {
+            const U old = cas_key<W>(&hk[j], Tup<W>::kAllOnes, k);
+            if (old == Tup<W>::kAllOnes || old == k) return j;
+        }
+    }
+    return -1;
+}
+
+// Adds m to key k's count, inserting the key (CAS on the key); returns 1 if this
+// call inserted it.  A walk that ends without a slot gives up a first table
+// (guess: *nkeys is pushed past any limit) or flags a full one.
+template <int W>
+__device__ __forceinline__ unsigned kl_add(AggSlot<W> *slots, uint64_t cap, typename Tup<W>::U k, uint64_t h,
+                                           unsigned m, bool guess, unsigned long long *nkeys, hj_counters *ctr) {
+    using U = typename Tup<W>::U;
+    const uint64_t walk = guess && cap > kGuessWalk ? kGuessWalk : cap;
+    uint64_t b = bucket_of<W>(h, cap);
+    for (uint64_t it = 0; it < walk; ++it) {
+        const U old = cas_key<W>((U *)&slots[b].key, Tup<W>::kAllOnes, k);
+        if (old == Tup<W>::kAllOnes || old == k) {
+            add_cnt(&slots[b].cnt, (decltype(slots[b].cnt))m);
+            return old == Tup<W>::kAllOnes;
+        }
+        if (++b == cap) b = 0;
+    }
+    if (guess) atomicAdd(nkeys, (unsigned long long)cap);
+    else atomicOr(&ctr->status, (unsigned long long)kStatusTableFull);
+    return 0;
+}
+
+// Step 1: every kept key in the table, its count added.  Each key inserted counts
+// in *nkeys; with a first table sized for fewer distinct keys than rows
+// (key_limit = half its slots) the CTAs stop once they pass the limit, walks end
+// after kGuessWalk slots (at load <= 1/2 a longer one gives the table up too),
+// and the host builds again at full size.
 template <int W>
 __global__ void __launch_bounds__(256) kl_count(const void *R, uint64_t n, AggSlot<W> *slots, uint64_t cap,
                                                 TableSide *side, hj_counters *ctr, PartFilter pf,
                                                 unsigned long long *nkeys, uint64_t key_limit) {
     using U = typename Tup<W>::U;
     constexpr int PV = Tup<W>::kPerVec;
+    __shared__ U hk[kHot];        // the tile's gathered keys (all ones: free)
+    __shared__ unsigned hc[kHot];  // and their counts
+    __shared__ int stop;
     const unsigned lane = threadIdx.x & 31;
-    const uint64_t warp = (blockIdx.x * (uint64_t)blockDim.x + threadIdx.x) >> 5;
-    const uint64_t nwarps = ((uint64_t)gridDim.x * blockDim.x) >> 5;
+    const bool guess = key_limit != ~0ull;
     const uint64_t nv = (n + PV - 1) / PV;
-    for (uint64_t v0 = warp * 32; v0 < nv; v0 += nwarps * 32) {  // warp-uniform: every lane takes part
-        unsigned long long seen = 0;
-        if (lane == 0) seen = *(volatile unsigned long long *)nkeys;
-        if (__shfl_sync(0xffffffffu, seen, 0) > key_limit) break;  // (warp-uniform)
-        const uint64_t v = v0 + lane;
+    const uint64_t tiles = (nv + blockDim.x - 1) / blockDim.x;
+    if (threadIdx.x < kHot) {
+        hk[threadIdx.x] = Tup<W>::kAllOnes;
+        hc[threadIdx.x] = 0;
+    }
+    if (threadIdx.x == 0) stop = 0;
+    __syncthreads();
+    for (uint64_t tile = blockIdx.x; tile < tiles; tile += gridDim.x) {  // block-uniform
+        const uint64_t v = tile * blockDim.x + threadIdx.x;
         U k[2] = {0, 0}, r[2] = {0, 0};
         if (v < nv) kl_load<W>(R, v, n, k, r);
-        const bool guess = key_limit != ~0ull;
-        unsigned fresh = 0;  // keys this lane inserted (counted per warp, first table only)
+        unsigned fresh = 0;  // keys this lane inserted (first table only)
 #pragma unroll
         for (int e = 0; e < PV; ++e) {
             const uint64_t h = key_hash<W>(k[e]);
@@ -219,49 +267,62 @@ __global__ void __launch_bounds__(256) kl_count(const void *R, uint64_t n, AggSl
                 atomicAdd(&side->agg_cnt, (unsigned long long)m);
                 continue;
             }
-            // a first, smaller table: nothing more once it is given up, and a walk of
-            // at most kGuessWalk slots (at load <= 1/2 a longer one gives it up too)
-            if (guess && *(volatile unsigned long long *)nkeys > key_limit) continue;
-            const uint64_t walk = guess && cap > kGuessWalk ? kGuessWalk : cap;
-            uint64_t b = bucket_of<W>(h, cap);
-            bool done = false;
-            for (uint64_t it = 0; it < walk && !done; ++it) {
-                const U old = cas_key<W>((U *)&slots[b].key, Tup<W>::kAllOnes, k[e]);
-                if (old == Tup<W>::kAllOnes || old == k[e]) {
-                    add_cnt(&slots[b].cnt, (decltype(slots[b].cnt))m);
-                    fresh += old == Tup<W>::kAllOnes;
-                    done = true;
-                } else if (++b == cap) {
-                    b = 0;
+            if (guess && *(volatile unsigned long long *)nkeys > key_limit) continue;  // given up
+            if (m > 1) {
+                const int j = hot_entry<W>(hk, k[e]);
+                if (j >= 0) {
+                    atomicAdd(&hc[j], m);
+                    continue;
                 }
             }
-            if (!done) {
-                if (guess) atomicAdd(nkeys, (unsigned long long)cap);  // past the limit: built again at full size
-                else atomicOr(&ctr->status, (unsigned long long)kStatusTableFull);
-            }
+            fresh += kl_add<W>(slots, cap, k[e], h, m, guess, nkeys, ctr);
         }
         if (guess) {  // (the warp is converged again here)
             const unsigned tot = __reduce_add_sync(0xffffffffu, fresh);
             if (lane == 0 && tot) atomicAdd(nkeys, (unsigned long long)tot);
         }
+        __syncthreads();
+        if (threadIdx.x < kHot) {  // the gathered keys: one add each
+            const U hkey = hk[threadIdx.x];
+            if (hkey != Tup<W>::kAllOnes) {
+                if (kl_add<W>(slots, cap, hkey, key_hash<W>(hkey), hc[threadIdx.x], guess, nkeys, ctr) && guess)
+                    atomicAdd(nkeys, 1ull);
+                hk[threadIdx.x] = Tup<W>::kAllOnes;
+                hc[threadIdx.x] = 0;
+            }
+        }
+        if (threadIdx.x == 0) stop = guess && *(volatile unsigned long long *)nkeys > key_limit;
+        __syncthreads();
+        if (stop) break;
     }
 }
 
-// Step 3: every kept R tuple's rid into its key's list.
+// Step 3: every kept R tuple's rid into its key's list: a warp group's places
+// [at, at + popc(g)) claimed by its leader on the key's fill position, a gathered
+// key's places claimed once per tile.
 template <int W>
 __global__ void __launch_bounds__(256) kl_scatter(const void *R, uint64_t n, AggSlot<W> *slots, uint64_t cap,
                                                   TableSide *side, typename Tup<W>::U *rids, hj_counters *ctr,
                                                   PartFilter pf) {
     using U = typename Tup<W>::U;
     constexpr int PV = Tup<W>::kPerVec;
+    __shared__ U hk[kHot];
+    __shared__ unsigned hc[kHot];
+    __shared__ unsigned long long hb[kHot];  // first place of a gathered key's tuples (~0: none)
     const unsigned lane = threadIdx.x & 31;
-    const uint64_t warp = (blockIdx.x * (uint64_t)blockDim.x + threadIdx.x) >> 5;
-    const uint64_t nwarps = ((uint64_t)gridDim.x * blockDim.x) >> 5;
     const uint64_t nv = (n + PV - 1) / PV;
-    for (uint64_t v0 = warp * 32; v0 < nv; v0 += nwarps * 32) {
-        const uint64_t v = v0 + lane;
+    const uint64_t tiles = (nv + blockDim.x - 1) / blockDim.x;
+    if (threadIdx.x < kHot) {
+        hk[threadIdx.x] = Tup<W>::kAllOnes;
+        hc[threadIdx.x] = 0;
+    }
+    __syncthreads();
+    for (uint64_t tile = blockIdx.x; tile < tiles; tile += gridDim.x) {  // block-uniform
+        const uint64_t v = tile * blockDim.x + threadIdx.x;
         U k[2] = {0, 0}, r[2] = {0, 0};
         if (v < nv) kl_load<W>(R, v, n, k, r);
+        int hj[2] = {-1, -1};      // gathered entry of item e
+        unsigned hr[2] = {0, 0};   // and its place among the entry's tuples
 #pragma unroll
         for (int e = 0; e < PV; ++e) {
             const uint64_t h = key_hash<W>(k[e]);
@@ -269,33 +330,70 @@ __global__ void __launch_bounds__(256) kl_scatter(const void *R, uint64_t n, Agg
             const unsigned g = __match_any_sync(0xffffffffu, k[e]) & __ballot_sync(0xffffffffu, ok);
             const int leader = g ? __ffs(g) - 1 : 0;
             // the leader claims the group's places: [at, at + popc(g)) of the key's
-            // list, or of the all-ones keys' list counted down from the array's end
+            // list, or of the all-ones keys' list counted down from the array's end,
+            // or of the key's gathered tuples in this tile
             uint64_t at = 0;
             bool fail = false;
+            int j = -1;
             if (ok && lane == (unsigned)leader) {
                 const uint64_t m = __popc(g);
                 if (k[e] == Tup<W>::kAllOnes) {
                     at = atomicAdd(&side->n_allones, (unsigned long long)m);
                 } else {
-                    const uint64_t b = kl_find<W>(slots, cap, k[e], h);
-                    if (b == cap) {  // cannot happen: step 1 inserted every kept key
-                        fail = true;
-                    } else if constexpr (W == 4) {
-                        unsigned *half = (unsigned *)&slots[b].suma;  // [0] offset, [1] fill position
-                        at = half[0] + atomicAdd(&half[1], (unsigned)m);
+                    if (m > 1) j = hot_entry<W>(hk, k[e]);
+                    if (j >= 0) {
+                        at = atomicAdd(&hc[j], (unsigned)m);
                     } else {
-                        at = slots[b].suma + atomicAdd(&slots[b].pad, (unsigned long long)m);
+                        const uint64_t b = kl_find<W>(slots, cap, k[e], h);
+                        if (b == cap) {  // cannot happen: step 1 inserted every kept key
+                            fail = true;
+                        } else if constexpr (W == 4) {
+                            unsigned *half = (unsigned *)&slots[b].suma;  // [0] offset, [1] fill position
+                            at = half[0] + atomicAdd(&half[1], (unsigned)m);
+                        } else {
+                            at = slots[b].suma + atomicAdd(&slots[b].pad, (unsigned long long)m);
+                        }
                     }
                 }
                 if (fail) atomicOr(&ctr->status, (unsigned long long)kStatusTableFull);
             }
             at = __shfl_sync(0xffffffffu, at, leader);
             fail = __shfl_sync(0xffffffffu, fail, leader);
+            j = __shfl_sync(0xffffffffu, j, leader);
             if (!ok || fail) continue;
             const uint64_t rank = __popc(g & lanes_lt());
-            if (k[e] == Tup<W>::kAllOnes) rids[n - 1 - (at + rank)] = r[e];
-            else rids[at + rank] = r[e];
+            if (j >= 0) {
+                hj[e] = j;
+                hr[e] = (unsigned)(at + rank);
+            } else if (k[e] == Tup<W>::kAllOnes) {
+                rids[n - 1 - (at + rank)] = r[e];
+            } else {
+                rids[at + rank] = r[e];
+            }
         }
+        __syncthreads();
+        if (threadIdx.x < kHot) {  // the gathered keys: their places in one claim each
+            const U hkey = hk[threadIdx.x];
+            if (hkey != Tup<W>::kAllOnes) {
+                const uint64_t b = kl_find<W>(slots, cap, hkey, key_hash<W>(hkey));
+                const unsigned m = hc[threadIdx.x];
+                if (b == cap) {
+                    atomicOr(&ctr->status, (unsigned long long)kStatusTableFull);
+                    hb[threadIdx.x] = ~0ull;
+                } else if constexpr (W == 4) {
+                    unsigned *half = (unsigned *)&slots[b].suma;
+                    hb[threadIdx.x] = half[0] + atomicAdd(&half[1], m);
+                } else {
+                    hb[threadIdx.x] = slots[b].suma + atomicAdd(&slots[b].pad, (unsigned long long)m);
+                }
+                hk[threadIdx.x] = Tup<W>::kAllOnes;
+                hc[threadIdx.x] = 0;
+            }
+        }
+        __syncthreads();
+#pragma unroll
+        for (int e = 0; e < PV; ++e)
+            if (hj[e] >= 0 && hb[hj[e]] != ~0ull) rids[hb[hj[e]] + hr[e]] = r[e];
     }
 }
 
