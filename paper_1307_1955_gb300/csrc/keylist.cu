@@ -35,7 +35,7 @@ namespace {
 constexpr unsigned kScanThreads = 1024;
 constexpr uint64_t kScanBlock = 2 * kScanThreads;  // entries per scan block
 constexpr uint64_t kCoopPairs = 4096;              // longest list one warp emits
-constexpr uint64_t kSegPairs = 1ull << 16;         // pairs per expansion segment
+constexpr uint64_t kSegPairs = 1ull << 13;         // pairs per expansion segment (one CTA's)
 
 template <int W>
 __device__ __forceinline__ void kl_load(const void *base, uint64_t v, uint64_t n_total, typename Tup<W>::U *k,
@@ -536,6 +536,7 @@ __global__ void __launch_bounds__(256) kl_expand(const Big *big, const unsigned 
         const unsigned long long base = s_base;
         const U s = (U)b.s;
         const uint64_t B = chk ? mix_b(s) : 0;
+#pragma unroll 4
         for (uint64_t i = threadIdx.x; i < len; i += blockDim.x) {
             const U a = rids[b.off + j0 + i];
             if (base + i < pcap) {
