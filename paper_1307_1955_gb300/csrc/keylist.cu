@@ -446,37 +446,55 @@ __global__ void __launch_bounds__(256) kl_probe(const void *S, uint64_t ns, cons
                 const unsigned long long i = atomicAdd(nbig, 1ull);
                 big[i] = Big{off, cnt, (unsigned long long)s};  // at most one entry per probe tuple
             }
-            // every other list of this step: one claim for the whole warp, each
-            // lane's rows at the exclusive prefix of the lanes' list lengths
+            // every other list of this step: one claim for the whole warp.  Lists
+            // of fewer than 32 pairs first, flattened: pair p of their concatenation
+            // (in lane order) is written by lane p mod 32 at base + p, its list found
+            // by a search over the lanes' prefix sums; then each longer list by the
+            // whole warp in turn, at base + (small pairs) + the prefix of the longer
+            // lists before it.
             const uint64_t mine = cnt <= kCoopPairs ? cnt : 0;
-            uint64_t incl = mine;
+            const uint64_t small = mine < 32 ? mine : 0, mid = mine - small;
+            uint64_t incl = small | (mid << 32);  // (small sums stay below 2^10, mid sums below 2^18)
 #pragma unroll
             for (int o = 1; o < 32; o <<= 1) {
                 const uint64_t y = __shfl_up_sync(0xffffffffu, incl, o);
                 if (lane >= (unsigned)o) incl += y;
             }
-            const uint64_t tot = __shfl_sync(0xffffffffu, incl, 31);
+            const uint64_t last = __shfl_sync(0xffffffffu, incl, 31);
+            const uint64_t tot_s = last & 0xffffffffu, tot = tot_s + (last >> 32);
             if (!tot) continue;
             unsigned long long base = 0;
             if (lane == 0) base = atomicAdd(&ctr->count, (unsigned long long)tot);
             base = __shfl_sync(0xffffffffu, base, 0);
-            const uint64_t at = base + incl - mine;
-            // one match: written by its own lane
-            if (mine == 1) {
-                const U a = rids[off];
-                if (at < pcap) out[at] = mk(a, s);
-                if (chk) {
-                    const uint64_t A = mix_a(a), B = mix_b(s);
-                    c0 += A * B;
-                    c1 += A + B;
+            const uint64_t incl_s = incl & 0xffffffffu, incl_m = incl >> 32;
+            for (uint64_t p0 = 0; p0 < tot_s; p0 += 32) {
+                const uint64_t p = p0 + lane;
+                unsigned L = 0;  // first lane whose inclusive prefix passes p
+#pragma unroll
+                for (unsigned b = 16; b >= 1; b >>= 1) {
+                    const uint64_t x = __shfl_sync(0xffffffffu, incl_s, L + b - 1);
+                    if (x <= p) L += b;
+                }
+                const uint64_t first = __shfl_sync(0xffffffffu, incl_s - small, L & 31);
+                const uint64_t o = __shfl_sync(0xffffffffu, off, L & 31);
+                const U ss = __shfl_sync(0xffffffffu, s, L & 31);
+                if (p < tot_s) {
+                    const U a = rids[o + (p - first)];
+                    if (base + p < pcap) out[base + p] = mk(a, ss);
+                    if (chk) {
+                        const uint64_t A = mix_a(a), B = mix_b(ss);
+                        c0 += A * B;
+                        c1 += A + B;
+                    }
                 }
             }
-            // a short list: the whole warp, kUnroll x 32 pairs per step
-            unsigned coop = __ballot_sync(0xffffffffu, mine > 1);
+            const uint64_t at = base + tot_s + incl_m - mid;
+            // a longer list: the whole warp, kUnroll x 32 pairs per step
+            unsigned coop = __ballot_sync(0xffffffffu, mid > 0);
             while (coop) {
                 const int L = __ffs(coop) - 1;
                 coop &= coop - 1;
-                const uint64_t o = __shfl_sync(0xffffffffu, off, L), n = __shfl_sync(0xffffffffu, mine, L);
+                const uint64_t o = __shfl_sync(0xffffffffu, off, L), n = __shfl_sync(0xffffffffu, mid, L);
                 const uint64_t dst = __shfl_sync(0xffffffffu, at, L);
                 const U ss = __shfl_sync(0xffffffffu, s, L);
                 const uint64_t B = chk ? mix_b(ss) : 0;
