@@ -434,11 +434,15 @@ hj_status hj_debug_fail_alloc(hj_ctx *ctx, int64_t n);
 uint64_t hj_debug_bytes_in_use(const hj_ctx *ctx);
 /* Test hook for the bounded device waits (the paper has no counterpart): the
  * ring partition scatter (2^9 .. 2^11 digits) runs flush warps that wait
- * on the CTA's insert warps; after n passes (default 2^22; n = 0 restores it) they
- * give up, set a sticky fault bit and return, and the call that reads the
+ * on the CTA's insert warps; after n passes (default 2^22; n = 0 restores both
+ * defaults) they give up, set a sticky fault bit and return.  The TMA-staged
+ * scatter of unpadded passes (hj_partition and the host-memory split, fan-out
+ * <= 2^11) polls the mbarrier of each staged tile at most n - 1 times (default
+ * 2^26; so n = 1 gives up at the first wait): a CTA that gives up sets the same
+ * bit, waits for its copy in flight to land and returns.  The call that reads the
  * counters next returns HJ_E_TIMEOUT (its results are then undefined).  The fault
- * is reported once; later calls on the context run normally.  Only the limit
- * changes: no GPU fault is involved.  HJ_E_INVALID for a NULL context. */
+ * is reported once; later calls on the context run normally.  Only the limits
+ * change: no GPU fault is involved.  HJ_E_INVALID for a NULL context. */
 hj_status hj_debug_wait_limit(hj_ctx *ctx, uint64_t n);
 /* Test and measurement hook: which kernel scatters a padded partition pass at
  * 2^9 .. 2^11 digits.  HJ_SCATTER_AUTO (the default) takes the ring scatter where

@@ -356,8 +356,9 @@ hj_status hj_debug_outcore(hj_ctx *c, int mode) {
     return HJ_OK;
 }
 
-/* Test hook: limit of the ring scatter's bounded wait (flush passes before its
- * flush warps give up and report HJ_E_TIMEOUT); 0 restores the default. */
+/* Test hook: limits of the bounded waits (ring scatter flush passes, n; TMA-staged
+ * scatter mbarrier polls, n - 1) before a kernel gives up and the call reports
+ * HJ_E_TIMEOUT; 0 restores the defaults. */
 hj_status hj_debug_wait_limit(hj_ctx *c, uint64_t n) {
     if (!c) return HJ_E_INVALID;
     c->wait_limit = n;

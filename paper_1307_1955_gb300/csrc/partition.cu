@@ -1427,16 +1427,20 @@ hj_status partition_pass(hj_ctx *c, int width, const void *in, uint64_t n_total,
             HJ_TRY(launch_region_bits<8>(c, bits, (unsigned)max_chunks, in, n_total, rg, chunk, shift, out, k0, k1,
                                          seg_ptrs));
     } else if (cfg.tma) {
+        // mbarrier polls per tile: the default, or n - 1 under a test limit of n (so
+        // that n = 1 gives up at the first wait, however long the hardware suspends
+        // a polling thread)
+        const uint32_t polls = c->wait_limit ? (uint32_t)std::min<uint64_t>(c->wait_limit - 1, kWaitLimit) : kWaitLimit;
         if (width == 4) {
             HJ_TRY(allow_max_smem(c, (const void *)scatter_tma_kernel<4>));
             HJ_LAUNCH(c, "partition_scatter", scatter_tma_kernel<4>, (unsigned)max_chunks, kTmaThreads, tma_smem, in,
                       n_total, seg_off, nseg, cb, chunk, shift, bits, Hs, out, pad, k0, k1, &c->d_ctr->fault, seg_ptrs,
-                      kWaitLimit);
+                      polls);
         } else {
             HJ_TRY(allow_max_smem(c, (const void *)scatter_tma_kernel<8>));
             HJ_LAUNCH(c, "partition_scatter", scatter_tma_kernel<8>, (unsigned)max_chunks, kTmaThreads, tma_smem, in,
                       n_total, seg_off, nseg, cb, chunk, shift, bits, Hs, out, pad, k0, k1, &c->d_ctr->fault, seg_ptrs,
-                      kWaitLimit);
+                      polls);
         }
     } else if (width == 4) {
         if (cfg.nt == 512) HJ_SC(4, 512, 8); else HJ_SC(4, 1024, 2);

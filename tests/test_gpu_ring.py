@@ -194,6 +194,38 @@ def test_batch_group_on_eleven_bits(hjm, ctx):
         assert np.array_equal(_sorted_got(res[j]), want), j
 
 
+@pytest.mark.parametrize("width", [4, 8])
+def test_tma_wait_runs_out_and_the_context_recovers(hjm, width):
+    # A limit of one: the TMA-staged scatter of an unpadded pass (hj_partition)
+    # polls its first tile's mbarrier zero times, gives up, waits for the copy in
+    # flight to land and returns.  hj_partition reports HJ_E_TIMEOUT and releases its
+    # buffers; with the default limit the next partition on the context is the
+    # oracle's, element by element.
+    lib = hjm.load_library()
+    n = (1 << 20) + 7
+    if width == 4:
+        rel, _ = W.unique_and_uniform(n, 0, 1, SEED, DEV, ids=(48,))
+    else:
+        rel, _ = W.zipf_pair(n, 0, 0.75, 0.5, 1 << 16, SEED, DEV, ids=(48,))
+    with hjm.Context(0) as c:
+        base = lib.hj_debug_bytes_in_use(c.handle)
+        assert lib.hj_debug_wait_limit(c.handle, 1) == hjm.HJ_OK
+        with pytest.raises(hjm.HJError) as e:
+            hjm.hj_partition(c, rel, 8)
+        assert e.value.status == hjm.HJ_E_TIMEOUT
+        assert lib.hj_debug_bytes_in_use(c.handle) == base
+        assert lib.hj_debug_wait_limit(c.handle, 0) == hjm.HJ_OK
+        got, goff = hjm.hj_partition(c, rel, 8)
+        want, woff = oracle.radix_partition(W.to_numpy_u(rel), 8)
+        assert np.array_equal(goff, woff)  # partition boundaries exact, the same rows in each
+        for p in range(len(woff) - 1):
+            a, b = int(woff[p]), int(woff[p + 1])
+            x = got[a:b][np.lexsort((got[a:b, 1], got[a:b, 0]))]
+            y = want[a:b][np.lexsort((want[a:b, 1], want[a:b, 0]))]
+            assert np.array_equal(x, y), p
+        assert lib.hj_debug_bytes_in_use(c.handle) == base
+
+
 def test_bounded_wait_runs_out_and_the_context_recovers(hjm):
     # A limit of one flush pass: the flush warps give up while the insert warps are
     # still streaming, set the fault bit and return (insert warps never wait, so
