@@ -985,11 +985,12 @@ template <int W> struct AggSoa {
             v[0] = x.x; v[1] = x.y;
         }
     }
-    // Add one build tuple of key k (a = A(rid), used with checksums).  The slot
-    // of k is the first slot of its run that holds k, else the first empty one,
-    // claimed by CAS: slots only ever go from empty to a key, so two inserts of
-    // the same key always meet in one slot.  False if every bucket is full.
-    __device__ __forceinline__ bool insert(T k, uint64_t a) const {
+    // Add m build tuples of key k (a = the sum of their A(rid), used with
+    // checksums).  The slot of k is the first slot of its run that holds k, else
+    // the first empty one, claimed by CAS: slots only ever go from empty to a key,
+    // so two inserts of the same key always meet in one slot.  False if every
+    // bucket is full.
+    __device__ __forceinline__ bool insert(T k, uint32_t m, uint64_t a) const {
         uint32_t b = part_bucket<W>(k, nb);
         for (uint32_t it = 0; it < nb; ++it) {
             volatile T *kb = keys + b * G;
@@ -1008,7 +1009,7 @@ template <int W> struct AggSoa {
                     hit = emp;
                 }
                 if (hit < 0) break;  // full bucket without k
-                atomicAdd(&cnt[b * G + hit], 1u);
+                atomicAdd(&cnt[b * G + hit], m);
                 if (suma) atomicAdd(&suma[b * G + hit], (unsigned long long)a);
                 return true;
             }
@@ -1113,6 +1114,45 @@ __global__ void __launch_bounds__(NT, 2048 / NT / 2) partition_join_kernel(
             }
             __syncthreads();
             // build over R_p
+            if constexpr (AGG) {
+                // lanes of a warp holding the same key insert once, their count and
+                // A(rid) sum together (a repeated key's slot takes one atomic per warp
+                // group instead of one per tuple); the loop is warp-uniform
+                for (uint32_t v0 = threadIdx.x & ~31u; v0 < nrv; v0 += blockDim.x) {
+                    const uint32_t v = v0 + lane;
+                    T k[2] = {0, 0}, r[2] = {0, 0};
+                    if (v < nrv) {
+                        const Vec x = ld_stream(Rv + v);
+                        if constexpr (W == 4) {
+                            k[0] = x.x; r[0] = x.y; k[1] = x.z; r[1] = x.w;
+                        } else {
+                            k[0] = x.x; r[0] = x.y;
+                        }
+                    }
+#pragma unroll
+                    for (int e = 0; e < PV; ++e) {
+                        // a padding row carries 0 or a pass's second sentinel: only
+                        // such keys are hashed to see whether the row is the partition's
+                        const bool in = v < nrv && !((k[e] == T(0) || k[e] == (T)tk.pk1 || k[e] == (T)tk.pk2) &&
+                                                     !pf.keep(hashw<W>(k[e])));
+                        const unsigned g = __match_any_sync(0xffffffffu, k[e]) & __ballot_sync(0xffffffffu, in);
+                        const uint64_t a = chk && in ? mix_a(r[e]) : 0;
+                        uint64_t asum = a;
+                        if (chk && __any_sync(0xffffffffu, in && __popc(g) > 1)) {
+                            // the group's sum of A(rid): every lane's value, kept by
+                            // the lanes of its group (whole-warp shuffles)
+                            asum = 0;
+#pragma unroll 8
+                            for (int q = 0; q < 32; ++q) {
+                                const uint64_t y = __shfl_sync(0xffffffffu, a, q);
+                                if ((g >> q) & 1u) asum += y;
+                            }
+                        }
+                        if (!in || (g & ((1u << lane) - 1u))) continue;  // the group's lowest lane inserts
+                        if (!at.insert(k[e], (uint32_t)__popc(g), asum)) s_full = 1;
+                    }
+                }
+            } else
             for (uint32_t v = threadIdx.x; v < nrv; v += blockDim.x) {
                 const Vec x = ld_stream(Rv + v);
                 T k[2], r[2];
@@ -1127,9 +1167,7 @@ __global__ void __launch_bounds__(NT, 2048 / NT / 2) partition_join_kernel(
                     // such keys are hashed to see whether the row is the partition's
                     if ((k[e] == T(0) || k[e] == (T)tk.pk1 || k[e] == (T)tk.pk2) && !pf.keep(hashw<W>(k[e]))) continue;
                     bool ok = false;
-                    if constexpr (AGG) {
-                        ok = at.insert(k[e], chk ? mix_a(r[e]) : 0);
-                    } else {
+                    {
                         T *kv = (T *)smem;
                         uint32_t bkt = part_bucket<W>(k[e], tab.nb);
                         // a walk past kMaxSmemWalk buckets means a heavily repeated
