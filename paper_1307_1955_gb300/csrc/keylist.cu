@@ -7,18 +7,24 @@
 // distinct key one entry whose rid list holds all of its build tuples' rids.
 // Here that is the aggregate table (one slot per distinct key with its count)
 // plus one array of rids:
-//   1. insert every kept key of R into the aggregate table with its count;
+//   1. insert every kept key of R into the aggregate table with its count (the
+//      first table sized for a 32nd as many distinct keys as rows, built again at
+//      full size if it passes half full);
 //   2. an exclusive scan of the counts gives each key the offset of its rid list;
 //   3. a second pass over R places every rid in its key's list (a per-key fill
 //      position claimed by atomicAdd; the order inside a list is free).
+// In steps 1 and 3 the lanes of a warp holding one key act as one, and keys that
+// fill several lanes are also gathered per CTA tile in shared memory: a heavy
+// hitter's count and fill position take one global atomic per tile.
 // A probe finds its key's one slot and emits the key's rid list with its own rid:
-// a single pair at once; a list of up to kCoopPairs by the whole warp, reading
-// the list with coalesced loads; a longer list (a heavy hitter) is recorded and
-// expanded afterwards by a grid-wide kernel in segments of kSegPairs pairs, so
-// that the millions of pairs of one probe tuple are written by every SM.  The
-// rows of a warp's step (the lists of its 32 probe tuples) are claimed with one
-// atomic add on the join's count: one global atomic per 32 probes, not per 32
-// pairs.
+// lists of fewer than 32 pairs flattened across the warp (pair p of their
+// concatenation written by lane p mod 32); a list of up to kCoopPairs by the
+// whole warp, reading the list with coalesced loads; a longer list (a heavy
+// hitter) is recorded and expanded afterwards by a grid-wide kernel in segments
+// of kSegPairs pairs, so that the millions of pairs of one probe tuple are
+// written by every SM.  The rows of a warp's step (the lists of its 32 probe
+// tuples) are claimed with one atomic add on the join's count: one global atomic
+// per 32 probes, not per 32 pairs.
 // R tuples whose key is all ones (the aggregate table's empty marker) are
 // counted on the table's side and keep their rids at the end of the array.
 #include <algorithm>
